@@ -1,0 +1,152 @@
+/*
+ * eri.h -- C ABI of the GB300 McMurchie-Davidson 4-centre ERI library.
+ *
+ * The library evaluates batches of contracted Cartesian shellsets (ab|cd)
+ * (Eq. def-abcd of arXiv 2506.12501, contracted as in Section 2.1) of one
+ * angular-momentum class at a time, by the MD sequence of Eq. md-2body:
+ *   [0]^(m) (Eq. 0m, Boys function Eq. boys)
+ *     -> [r]^(0) (Eq. r-rr) -> [p|q] (Eq. pq-from-r)
+ *     -> [p|cd] (Eq. ket-from-hermite, ket contracted first)
+ *     -> [ab|cd] (Eq. bra-from-hermite, bra contracted),
+ * with Cartesian transforms E built by Eqs. E2rr1/E2rr2/E2-000.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every array argument is DEVICE memory owned by the caller, except where
+ *   a comment says "host".  The library never frees caller memory.
+ * - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *   NULL = legacy default stream).  Pointers must stay valid until the work
+ *   queued on the stream has completed (for plans: until eri_plan_destroy).
+ * - Return value: ERI_OK (0) or a negative error code; eri_error_string()
+ *   describes it.  Argument errors are detected on the host before any
+ *   launch and leave outputs untouched.  ERI_ECUDA reports a failed CUDA
+ *   call (launch or allocation).
+ * - The library allocates only internal workspace (pair tables, class
+ *   tables, the Boys table), cached per device and reused between calls;
+ *   eri_finalize() releases it.  Calls on different streams of one device
+ *   must not overlap in time (they share that workspace).
+ * - Shells: angular momentum 0 <= l <= ERI_LMAX, contraction degree
+ *   1 <= K <= ERI_KMAX.  Contraction coefficients are used verbatim (no
+ *   normalisation is applied by the library).
+ * - Cartesian components of a shell are ordered x^l first, then
+ *   lexicographically (xx, xy, xz, yy, yz, zz for l = 2); a pair index is
+ *   ab = a*nc(lb) + b with nc(l) = (l+1)(l+2)/2.
+ */
+#ifndef ERI_H
+#define ERI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ERI_LMAX 3
+#define ERI_KMAX 8
+
+enum {
+    ERI_OK = 0,
+    ERI_EINVAL = -1,   /* bad argument: l or K out of range, NULL pointer, sizes */
+    ERI_ECLASS = -2,   /* a pair's shell angular momenta disagree with the class */
+    ERI_ECUDA = -3,    /* a CUDA call failed */
+    ERI_ETIMEOUT = -4, /* a bounded device-side wait ran out (plan execution) */
+    ERI_ENOMEM = -5,   /* workspace allocation failed */
+    ERI_EPLAN = -6     /* plan misuse (wrong buffers for the plan's mode) */
+};
+
+/* Precision of the Hermite-to-Cartesian transforms. */
+enum {
+    ERI_PREC_FP64 = 0,  /* everything in FP64 */
+    ERI_PREC_SPLIT = 1  /* transforms in FP32 hi+lo split products with FP64
+                           accumulation; Boys, R and prefactors stay FP64 */
+};
+
+typedef struct {
+    int32_t la, lb, lc, ld;
+} eri_class_t;
+
+/* A basis set: shells on atoms, primitives back to back (all DEVICE). */
+typedef struct {
+    const double* centres;     /* [natom][3] bohr */
+    const int32_t* shell_atom; /* [nshell] atom of each shell */
+    const int32_t* shell_l;    /* [nshell] angular momentum */
+    const int32_t* shell_K;    /* [nshell] contraction degree */
+    const int32_t* shell_off;  /* [nshell] first primitive of the shell */
+    const double* exps;        /* [nprim] exponents (> 0) */
+    const double* coefs;       /* [nprim] contraction coefficients */
+    int32_t natom, nshell, nprim;
+} eri_basis_t;
+
+/*
+ * eri_boys -- the Boys function F_m(T) = int_0^1 y^{2m} exp(-T y^2) dy
+ * (Eq. boys), evaluated as the integral kernels do: Taylor interpolation of
+ * F_mmax on a tabulated grid, then downward recursion
+ *     F_m = (2T F_{m+1} + exp(-T)) / (2m+1);
+ * for T beyond the grid the large-T form F_0 = (1/2) sqrt(pi/T) with the
+ * upward recursion (Section 3.2.1).
+ *   T: [n] arguments (T >= 0, finite); F: [n][mmax+1] results, F[i*(mmax+1)+m].
+ *   0 <= mmax <= ERI_BOYS_MMAX.  n == 0 is a no-op.
+ */
+#define ERI_BOYS_MMAX 20
+int eri_boys(int mmax, const double* T, int64_t n, double* F, void* stream);
+
+/*
+ * eri_batch -- contracted Cartesian shellsets (ab|cd) of class `cls` for a
+ * batch (Section 3.1: bra shell-pair list x ket shell-pair list).
+ *   bra_pairs: [nbra][2] shell indices (a, b) with l = (la, lb);
+ *   ket_pairs: [nket][2] shell indices (c, d) with l = (lc, ld);
+ *   quartets:  NULL => every (bra, ket) combination ("product form");
+ *              else [nq][2] (bra index, ket index) ("list form").
+ *   out: [out_len] doubles, written (not accumulated).  Layout, with
+ *        nab = nc(la) nc(lb), ncd = nc(lc) nc(ld):
+ *        product form  out[ij + nbra*(ab + nab*(cd + ncd*kl))]
+ *                      (the [ij,ab,cd,kl] column-major layout of Section 3.1),
+ *                      out_len >= nbra*nket*nab*ncd;
+ *        list form     out[q + nq*(ab*ncd + cd)], out_len >= nq*nab*ncd.
+ *   precision: ERI_PREC_FP64 or ERI_PREC_SPLIT.
+ * A shell whose l disagrees with `cls` makes the kernel skip that pair's
+ * quartets (their outputs are left as zeros) and is reported by
+ * eri_last_status() as ERI_ECLASS after the stream has been synchronised.
+ * nbra == 0, nket == 0 or nq == 0 is a no-op.
+ */
+int eri_batch(eri_class_t cls, const eri_basis_t* basis,
+              const int32_t* bra_pairs, int64_t nbra,
+              const int32_t* ket_pairs, int64_t nket,
+              const int64_t* quartets, int64_t nq,
+              double* out, int64_t out_len, int precision, void* stream);
+
+/*
+ * eri_batch_grad -- adjoint of eri_batch: accumulates the derivatives of
+ *   E = sum_{quartets} sum_{abcd} W_abcd (ab|cd)
+ * with respect to the atom centres and the primitive exponents (the
+ * contraction coefficients are held fixed), by differentiating each
+ * primitive Gaussian (Section 2.1) and recomputing the forward Hermite
+ * intermediates.
+ *   W: same layout and length as eri_batch's `out` for the same arguments;
+ *   grad_centres: [natom][3], ACCUMULATED (+=);
+ *   grad_exps:    [nprim],    ACCUMULATED (+=).
+ * Either gradient pointer may be NULL to skip that part.
+ */
+int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
+                   const int32_t* bra_pairs, int64_t nbra,
+                   const int32_t* ket_pairs, int64_t nket,
+                   const int64_t* quartets, int64_t nq,
+                   const double* W, int64_t w_len,
+                   double* grad_centres, double* grad_exps, void* stream);
+
+/*
+ * eri_last_status -- synchronises `stream` and returns ERI_OK or the first
+ * error a kernel recorded since the previous call (then clears it).
+ */
+int eri_last_status(void* stream);
+
+/* Human-readable text for an error code (static storage). */
+const char* eri_error_string(int code);
+
+/* Release every cached workspace of the current device. */
+int eri_finalize(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ERI_H */

@@ -1,0 +1,22 @@
+"""GB300-native McMurchie-Davidson 4-centre ERI library (arXiv 2506.12501).
+
+The compute path is the CUDA library ``libmderi.so`` (C ABI in
+``include/eri.h``); this package is its thin Python binding.
+"""
+from .binding import (  # noqa: F401
+    DeviceBasis,
+    EriError,
+    ERI_OK, ERI_EINVAL, ERI_ECLASS, ERI_ECUDA, ERI_ETIMEOUT, ERI_ENOMEM, ERI_EPLAN,
+    ERI_PREC_FP64, ERI_PREC_SPLIT, ERI_LMAX, ERI_KMAX, ERI_BOYS_MMAX,
+    EXPORTS,
+    eri_boys,
+    eri_batch,
+    eri_batch_grad,
+    eri_last_status,
+    eri_finalize,
+    error_string,
+    lib,
+    nc,
+    out_len,
+)
+from .autograd import ERIFunction, eri  # noqa: F401,E402

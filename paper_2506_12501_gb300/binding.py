@@ -1,0 +1,174 @@
+"""ctypes binding of ``libmderi.so`` (include/eri.h).
+
+Argument marshalling only: tensors are passed as raw device pointers and the
+current torch CUDA stream as the ``stream`` argument; every integral is
+computed by the library's kernels.  There is no CPU fallback: if the
+library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+ERI_OK, ERI_EINVAL, ERI_ECLASS, ERI_ECUDA, ERI_ETIMEOUT, ERI_ENOMEM, ERI_EPLAN = 0, -1, -2, -3, -4, -5, -6
+ERI_PREC_FP64, ERI_PREC_SPLIT = 0, 1
+ERI_LMAX, ERI_KMAX, ERI_BOYS_MMAX = 3, 8, 20
+
+_lock = threading.Lock()
+_lib = None
+
+
+class EriError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} (code {code})")
+
+
+class eri_class_t(ctypes.Structure):
+    _fields_ = [("la", ctypes.c_int32), ("lb", ctypes.c_int32), ("lc", ctypes.c_int32), ("ld", ctypes.c_int32)]
+
+
+class eri_basis_t(ctypes.Structure):
+    _fields_ = [("centres", ctypes.c_void_p), ("shell_atom", ctypes.c_void_p), ("shell_l", ctypes.c_void_p),
+                ("shell_K", ctypes.c_void_p), ("shell_off", ctypes.c_void_p), ("exps", ctypes.c_void_p),
+                ("coefs", ctypes.c_void_p), ("natom", ctypes.c_int32), ("nshell", ctypes.c_int32),
+                ("nprim", ctypes.c_int32)]
+
+
+EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize"]
+
+
+def lib() -> ctypes.CDLL:
+    """Load the library, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            L.eri_boys.argtypes = [I, P, I64, P, P]
+            L.eri_batch.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P, I64, I, P]
+            L.eri_batch_grad.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P, I64,
+                                         P, P, P]
+            L.eri_last_status.argtypes = [P]
+            L.eri_error_string.argtypes = [I]
+            L.eri_error_string.restype = ctypes.c_char_p
+            L.eri_finalize.argtypes = []
+            for f in ("eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_finalize"):
+                getattr(L, f).restype = I
+            _lib = L
+        return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().eri_error_string(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != ERI_OK:
+        raise EriError(code, where)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def nc(l: int) -> int:
+    return (l + 1) * (l + 2) // 2
+
+
+class DeviceBasis:
+    """A basis (see synth.Basis) copied to the current CUDA device."""
+
+    def __init__(self, basis, device=None):
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        f64 = dict(dtype=torch.float64, device=dev)
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.centres = torch.as_tensor(basis["centres"], **f64).reshape(-1, 3).contiguous()
+        self.shell_atom = torch.as_tensor(basis["shell_atom"], **i32).contiguous()
+        self.shell_l = torch.as_tensor(basis["shell_l"], **i32).contiguous()
+        self.shell_K = torch.as_tensor(basis["shell_K"], **i32).contiguous()
+        self.shell_off = torch.as_tensor(basis["shell_off"], **i32).contiguous()
+        self.exps = torch.as_tensor(basis["exps"], **f64).contiguous()
+        self.coefs = torch.as_tensor(basis["coefs"], **f64).contiguous()
+
+    def struct(self, centres=None, exps=None) -> eri_basis_t:
+        c = self.centres if centres is None else centres
+        e = self.exps if exps is None else exps
+        return eri_basis_t(_ptr(c), _ptr(self.shell_atom), _ptr(self.shell_l), _ptr(self.shell_K),
+                           _ptr(self.shell_off), _ptr(e), _ptr(self.coefs), c.shape[0],
+                           self.shell_l.shape[0], e.shape[0])
+
+
+def eri_boys(mmax: int, T: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """F_m(T), m = 0..mmax, shape (n, mmax+1), by the library's Boys kernel."""
+    T = T.contiguous()
+    if out is None:
+        out = torch.empty((T.numel(), mmax + 1), dtype=torch.float64, device=T.device)
+    _check(lib().eri_boys(mmax, _ptr(T), T.numel(), _ptr(out), _stream(stream)), "eri_boys")
+    return out
+
+
+def out_len(cls, nbra: int, nket: int, nq: int | None) -> int:
+    la, lb, lc, ld = cls
+    nqq = nq if nq is not None else nbra * nket
+    return nqq * nc(la) * nc(lb) * nc(lc) * nc(ld)
+
+
+def eri_batch(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pairs: torch.Tensor,
+              quartets: torch.Tensor | None = None, out: torch.Tensor | None = None,
+              precision: int = ERI_PREC_FP64, stream=None, centres=None, exps=None) -> torch.Tensor:
+    """Contracted Cartesian shellsets of class ``cls`` (see include/eri.h for the layout)."""
+    nbra, nket = bra_pairs.shape[0], ket_pairs.shape[0]
+    nq = quartets.shape[0] if quartets is not None else None
+    n = out_len(cls, nbra, nket, nq)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=bra_pairs.device)
+    if n == 0:  # an empty quartet list has no device pointer; nothing to compute
+        return out
+    b = basis.struct(centres, exps)
+    code = lib().eri_batch(eri_class_t(*cls), ctypes.byref(b), _ptr(bra_pairs), nbra, _ptr(ket_pairs), nket,
+                           _ptr(quartets), nq if nq is not None else 0, _ptr(out), out.numel(), precision,
+                           _stream(stream))
+    _check(code, "eri_batch")
+    return out
+
+
+def eri_batch_grad(cls, basis: DeviceBasis, bra_pairs, ket_pairs, quartets, W: torch.Tensor,
+                   grad_centres: torch.Tensor | None = None, grad_exps: torch.Tensor | None = None,
+                   stream=None, centres=None, exps=None):
+    """Accumulate d(sum W (ab|cd))/d(centres, exponents) into the given tensors."""
+    nbra, nket = bra_pairs.shape[0], ket_pairs.shape[0]
+    nq = quartets.shape[0] if quartets is not None else None
+    if out_len(cls, nbra, nket, nq) == 0:
+        return grad_centres, grad_exps
+    b = basis.struct(centres, exps)
+    code = lib().eri_batch_grad(eri_class_t(*cls), ctypes.byref(b), _ptr(bra_pairs), nbra, _ptr(ket_pairs), nket,
+                                _ptr(quartets), nq if nq is not None else 0, _ptr(W.contiguous()), W.numel(),
+                                _ptr(grad_centres), _ptr(grad_exps), _stream(stream))
+    _check(code, "eri_batch_grad")
+    return grad_centres, grad_exps
+
+
+def eri_last_status(stream=None) -> int:
+    return lib().eri_last_status(_stream(stream))
+
+
+def eri_finalize() -> int:
+    return lib().eri_finalize()

@@ -1,0 +1,103 @@
+// eri_device.cuh -- device building blocks shared by the forward and adjoint
+// kernels: the Boys function and the auxiliary integrals [r]^(0).
+#pragma once
+
+#include "eri_internal.h"
+
+namespace eri {
+
+// 1/(2n+1), n = 0..31 (exact to the last bit of a double division)
+__constant__ double c_inv_odd[32] = {
+    1.0 / 1,  1.0 / 3,  1.0 / 5,  1.0 / 7,  1.0 / 9,  1.0 / 11, 1.0 / 13, 1.0 / 15, 1.0 / 17, 1.0 / 19, 1.0 / 21,
+    1.0 / 23, 1.0 / 25, 1.0 / 27, 1.0 / 29, 1.0 / 31, 1.0 / 33, 1.0 / 35, 1.0 / 37, 1.0 / 39, 1.0 / 41, 1.0 / 43,
+    1.0 / 45, 1.0 / 47, 1.0 / 49, 1.0 / 51, 1.0 / 53, 1.0 / 55, 1.0 / 57, 1.0 / 59, 1.0 / 61, 1.0 / 63};
+
+// 2 pi^(5/2), the constant of Eq. 0m
+constexpr double kTwoPi52 = 34.986836655249725693;
+// sqrt(pi)/2
+constexpr double kHalfSqrtPi = 0.88622692545275801365;
+
+// Boys function F_0..F_L at T (Eq. boys), written to F[0..L].
+// T < kBoysTmax: F_L by its Taylor expansion about the nearest grid point
+//   F_L(T0 + d) = sum_{k<7} F_{L+k}(T0) (-d)^k / k!     (|d| <= 1/64)
+// (table rows hold F_{L+k}(T0)/k! and exp(-T0)), exp(-T) = exp(-T0) exp(-d)
+// with exp(-d) by its own degree-6 Taylor polynomial, then the downward
+// recursion F_n = (2T F_{n+1} + exp(-T)) / (2n+1).
+// T >= kBoysTmax: F_0 = (1/2) sqrt(pi/T) (erf(sqrt T) = 1 to double
+// precision) and the upward recursion F_{n+1} = (2n+1) F_n / (2T), the
+// exp(-T) term being below double precision there (Section 3.2.1).
+// FP64 cost: 6 + 7 + 2L (+1) below the grid end.
+__device__ __forceinline__ void boys_eval(int L, double T, const double* __restrict__ tab, double* F)
+{
+    if (T < kBoysTmax) {
+        const float Tf = (float)T;
+        int j = __float2int_rn(Tf * (float)kBoysInvStep);
+        j = j < 0 ? 0 : (j > kBoysGrid - 1 ? kBoysGrid - 1 : j);
+        const double T0 = (double)((float)j * (float)kBoysStep);  // exact
+        const double md = T0 - T;                                  // -d
+        const double2* row = reinterpret_cast<const double2*>(tab + (size_t)j * 8);
+        const double2 r01 = __ldg(row), r23 = __ldg(row + 1), r45 = __ldg(row + 2), r67 = __ldg(row + 3);
+        double f = r67.x;
+        f = fma(f, md, r45.y);
+        f = fma(f, md, r45.x);
+        f = fma(f, md, r23.y);
+        f = fma(f, md, r23.x);
+        f = fma(f, md, r01.y);
+        f = fma(f, md, r01.x);
+        double e = 1.0 / 720.0;
+        e = fma(e, md, 1.0 / 120.0);
+        e = fma(e, md, 1.0 / 24.0);
+        e = fma(e, md, 1.0 / 6.0);
+        e = fma(e, md, 0.5);
+        e = fma(e, md, 1.0);
+        e = fma(e, md, 1.0);
+        const double eT = r67.y * e;
+        F[L] = f;
+        const double twoT = T + T;
+        for (int n = L - 1; n >= 0; --n) {
+            f = fma(twoT, f, eT) * c_inv_odd[n];
+            F[n] = f;
+        }
+    } else {
+        const double rt = rsqrt(T);
+        const double inv2T = 0.5 * rt * rt;
+        double f = kHalfSqrtPi * rt;
+        F[0] = f;
+        for (int n = 0; n < L; ++n) {
+            f = f * ((double)(2.0f * (float)n + 1.0f) * inv2T);
+            F[n + 1] = f;
+        }
+    }
+}
+
+// Auxiliary integrals of one primitive quartet (Eqs. 0m and r-rr):
+//   R[e] = [r_e]^(0) for every Hermite function e of order <= L (tetrahedral
+//   numbering), given
+//   base[n] = [0]^(n) = pref (-2 rho)^n F_n(T), n = 0..L,
+//   X = P - Q.
+// The table `st` gives for each e >= 1 the axis i and the sources e-1_i and
+// e-2_i.  Level by level, n = L-1 down to 0, all entries of order 1..L-n
+// are rewritten in place from the level-(n+1) values (highest order first,
+// so every source is read before it is overwritten).
+// FP64 cost: one multiply per entry, plus one FMA where the coefficient
+// e_i - 1 is nonzero.
+template <typename RPtr>
+__device__ __forceinline__ void r_recursion(int L, const double* base, double X, double Y, double Z,
+                                            const RStep* __restrict__ st, RPtr R)
+{
+    R[0] = base[L];
+    for (int n = L - 1; n >= 0; --n) {
+        const int N = L - n;
+        const int top = (N + 1) * (N + 2) * (N + 3) / 6;  // Nh(N)
+        for (int e = top - 1; e >= 1; --e) {
+            const RStep s = st[e];
+            const double x = s.axis == 0 ? X : (s.axis == 1 ? Y : Z);
+            double v = x * R[s.src1];
+            if (s.coef) v = fma(s.coefd, R[s.src2], v);
+            R[e] = v;
+        }
+        R[0] = base[n];
+    }
+}
+
+}  // namespace eri

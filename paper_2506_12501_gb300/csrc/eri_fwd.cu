@@ -1,0 +1,751 @@
+// eri_fwd.cu -- forward ERI batches: eri_boys and eri_batch.
+//
+// Per class and batch (Section 3.1: bra pair list x ket pair list):
+//  1. prepass_kernel   validates indices, angular momenta and contraction
+//                      degrees and finds the largest K on each centre;
+//  2. pair_kernel      per primitive pair: zeta_p, P, 2pi^(5/2)/zeta_p or
+//                      1/zeta_q, and the products E^x E^y E^z of the
+//                      Hermite expansion coefficients (Eqs. E2rr1/E2rr2/
+//                      E2-000) for every nonzero (Cartesian pair, Hermite)
+//                      term, with c_a c_b folded in and, on the ket, the
+//                      sign (-1)^{l_q} of Eq. pq-from-r;
+//  3. fwd_kernel       per tile of quartets, staged through shared memory:
+//       A. [r]^(0) for every primitive quartet of the tile (Boys function,
+//          Eq. 0m, Eq. r-rr);
+//       B. ket transform and ket contraction (Eq. ket-from-hermite):
+//          X[p][cd] = sum_k sum_q E^cd_{k,q} [p+q]^(0)_{ik};
+//       C. bra transform and bra contraction (Eq. bra-from-hermite):
+//          (ab|cd) += sum_p E^ab_{i,p} X[p][cd], accumulated over bra
+//          primitives i in registers (or in `out` for very large shellsets),
+//     then coalesced stores of the quartet-fastest output.
+// Every FP64 operation of the path runs in these kernels.
+#include <algorithm>
+#include <cstdio>
+
+#include "eri_device.cuh"
+#include "eri_internal.h"
+
+namespace eri {
+
+constexpr int kNT = 128;   // threads per CTA of fwd_kernel
+constexpr int kNACC = 16;  // outputs per thread held in registers
+
+// ---------------------------------------------------------------------------
+// 1. prepass
+// ---------------------------------------------------------------------------
+struct PrepassArgs {
+    const int32_t* shell_l;
+    const int32_t* shell_K;
+    int32_t nshell;
+    const int32_t* bra;
+    int64_t nbra;
+    const int32_t* ket;
+    int64_t nket;
+    const int64_t* quartets;
+    int64_t nq;
+    int l[4];
+    int* info;  // [0..3] max K per centre, [4] error
+};
+
+__device__ __forceinline__ void set_err(int* p, int code) { atomicCAS(p, 0, code); }
+
+__global__ void prepass_kernel(PrepassArgs a)
+{
+    const int64_t n = max(max(a.nbra, a.nket), a.nq);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int side = 0; side < 2; ++side) {
+            const int32_t* pr = side == 0 ? a.bra : a.ket;
+            const int64_t np = side == 0 ? a.nbra : a.nket;
+            if (i >= np) continue;
+            for (int c = 0; c < 2; ++c) {
+                const int32_t s = pr[2 * i + c];
+                if (s < 0 || s >= a.nshell) {
+                    set_err(&a.info[4], DEV_EINDEX);
+                    continue;
+                }
+                const int l = a.shell_l[s], K = a.shell_K[s];
+                if (l != a.l[2 * side + c]) set_err(&a.info[4], DEV_ECLASS);
+                if (K < 1 || K > kKmax) {
+                    set_err(&a.info[4], DEV_EK);
+                    continue;
+                }
+                atomicMax(&a.info[2 * side + c], K);
+            }
+        }
+        if (a.quartets && i < a.nq) {
+            const int64_t b = a.quartets[2 * i], k = a.quartets[2 * i + 1];
+            if (b < 0 || b >= a.nbra || k < 0 || k >= a.nket) set_err(&a.info[4], DEV_EINDEX);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. primitive-pair tables
+// ---------------------------------------------------------------------------
+struct PairArgs {
+    const double* centres;
+    const int32_t* shell_atom;
+    const int32_t* shell_K;
+    const int32_t* shell_off;
+    const double* exps;
+    const double* coefs;
+    const int32_t* pairs;
+    int64_t npairs;
+    int l1, l2;
+    int KS;                 // primitive-pair slots per pair
+    int T;                  // terms
+    const uint8_t* fac;     // [T][3] per-axis E-table indices
+    int ket;                // 1: ket side (sign (-1)^{l_q}, scale 1/zeta_q)
+    double* ps;             // [npairs][KS][PS_N]
+    double* E;              // [npairs][KS][T]
+    int32_t* kprim;         // [npairs] number of valid slots K1*K2
+    // adjoint only (ax == nullptr otherwise): per-axis tables with both
+    // indices raised by up to 2, ax[(g*3 + axis)*eax + (i*(l2+3) + j)*(l1+l2+5) + t]
+    double* ax;
+    int eax;
+    double* zz;             // [npairs][KS][2]: the two exponents
+};
+
+constexpr int kEax = (kLmax + 3) * (kLmax + 3) * (2 * kLmax + 5);  // per-axis E table bound (adjoint shifts)
+
+__global__ void pair_kernel(PairArgs a)
+{
+    const int64_t total = a.npairs * a.KS;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = g / a.KS;
+        const int s = (int)(g - j * a.KS);
+        const int s1 = a.pairs[2 * j], s2 = a.pairs[2 * j + 1];
+        const int K1 = a.shell_K[s1], K2 = a.shell_K[s2];
+        if (s == 0) a.kprim[j] = K1 * K2;
+        if (s >= K1 * K2) {  // padding slot: finite zeros, never contributes
+            for (int t = 0; t < a.T; ++t) a.E[(size_t)g * a.T + t] = 0.0;
+            double* o = a.ps + (size_t)g * PS_N;
+            o[PS_P] = 1.0;
+            o[PS_PX] = o[PS_PY] = o[PS_PZ] = 0.0;
+            o[PS_INVP] = 1.0;
+            if (a.ax) {
+                for (int q = 0; q < 3 * a.eax; ++q) a.ax[(size_t)g * 3 * a.eax + q] = 0.0;
+                a.zz[2 * g] = a.zz[2 * g + 1] = 1.0;
+            }
+            continue;
+        }
+        const int i1 = s / K2, i2 = s - i1 * K2;
+        const int p1 = a.shell_off[s1] + i1, p2 = a.shell_off[s2] + i2;
+        const double z1 = a.exps[p1], z2 = a.exps[p2];
+        const double* A = a.centres + 3 * a.shell_atom[s1];
+        const double* B = a.centres + 3 * a.shell_atom[s2];
+        const double p = z1 + z2;
+        const double invp = 1.0 / p;
+        const double inv2p = 0.5 * invp;
+        double PA[3], PB[3], P[3], AB2 = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            P[x] = (z1 * A[x] + z2 * B[x]) * invp;
+            PA[x] = P[x] - A[x];
+            PB[x] = P[x] - B[x];
+            const double d = A[x] - B[x];
+            AB2 = fma(d, d, AB2);
+        }
+        // K_AB c_1 c_2 carried by the x-axis bootstrap E_00^0 (Eq. E2-000),
+        // 1 on y and z: the products E^x E^y E^z are unchanged.
+        const double e00x = a.coefs[p1] * a.coefs[p2] * exp(-z1 * z2 * invp * AB2);
+        const int ext = a.ax ? 2 : 0;
+        const int m1 = a.l1 + ext, m2 = a.l2 + ext;          // largest raised indices
+        const int L12 = a.l1 + a.l2, n2 = m2 + 1, nt = m1 + m2 + 1;
+        double E[3][kEax];
+        for (int x = 0; x < 3; ++x) {
+            double* Ex = E[x];
+            for (int q = 0; q < (m1 + 1) * n2 * nt; ++q) Ex[q] = 0.0;
+            Ex[0] = x == 0 ? e00x : 1.0;
+            // raise the first index at j = 0 (Eq. E2rr1)
+            for (int i = 0; i < m1; ++i)
+                for (int t = 0; t <= i + 1; ++t) {
+                    double v = 0.0;
+                    if (t >= 1) v = inv2p * Ex[(i * n2) * nt + t - 1];
+                    if (t <= i) v = fma(PA[x], Ex[(i * n2) * nt + t], v);
+                    if (t + 1 <= i) v = fma((double)(float)(t + 1), Ex[(i * n2) * nt + t + 1], v);
+                    Ex[((i + 1) * n2) * nt + t] = v;
+                }
+            // raise the second index for every first index (Eq. E2rr2)
+            for (int i = 0; i <= m1; ++i)
+                for (int jj = 0; jj < m2; ++jj)
+                    for (int t = 0; t <= i + jj + 1; ++t) {
+                        const int b0 = (i * n2 + jj) * nt;
+                        double v = 0.0;
+                        if (t >= 1) v = inv2p * Ex[b0 + t - 1];
+                        if (t <= i + jj) v = fma(PB[x], Ex[b0 + t], v);
+                        if (t + 1 <= i + jj) v = fma((double)(float)(t + 1), Ex[b0 + t + 1], v);
+                        Ex[(i * n2 + jj + 1) * nt + t] = v;
+                    }
+        }
+        double* Eout = a.E + (size_t)g * a.T;
+        const int ntc = L12 + 1, n2c = a.l2 + 1;  // dims the class-table indices use
+        for (int t = 0; t < a.T; ++t) {
+            int idx[3], lq = 0;
+            for (int x = 0; x < 3; ++x) {
+                const int f = a.fac[3 * t + x];
+                const int tt = f % ntc, bb = (f / ntc) % n2c, aa = f / (ntc * n2c);
+                idx[x] = (aa * n2 + bb) * nt + tt;
+                lq += tt;
+            }
+            double v = E[0][idx[0]] * E[1][idx[1]] * E[2][idx[2]];
+            if (a.ket && (lq & 1)) v = -v;
+            Eout[t] = v;
+        }
+        if (a.ax) {
+            for (int x = 0; x < 3; ++x) {
+                double* o = a.ax + ((size_t)g * 3 + x) * a.eax;
+                for (int q = 0; q < (m1 + 1) * n2 * nt; ++q) o[q] = E[x][q];
+            }
+            a.zz[2 * g] = z1;
+            a.zz[2 * g + 1] = z2;
+        }
+        double* o = a.ps + (size_t)g * PS_N;
+        o[PS_P] = p;
+        o[PS_PX] = P[0];
+        o[PS_PY] = P[1];
+        o[PS_PZ] = P[2];
+        o[PS_INVP] = a.ket ? invp : kTwoPi52 * invp;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. forward kernel
+// ---------------------------------------------------------------------------
+struct FwdArgs {
+    ClassTables ct;
+    const double* boys;
+    const RStep* rsteps;
+    const double* bra_ps;
+    const double* bra_E;
+    const int32_t* bra_kp;
+    const double* ket_ps;
+    const double* ket_E;
+    const int32_t* ket_kp;
+    const int64_t* quartets;  // NULL: product form
+    int64_t nq, nbra, nket;
+    double* out;
+    int TQ, KB, KK, IC;
+    int e_smem, acc_regs;
+    int sEbS, sEkS;           // per-quartet strides of staged E (doubles)
+    int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;  // smem offsets (doubles)
+    int64_t ntiles;
+};
+
+struct Strided {
+    double* p;
+    int s;
+    __device__ __forceinline__ double& operator[](int e) const { return p[(size_t)e * s]; }
+};
+
+__device__ __forceinline__ int64_t out_index(const FwdArgs& a, int64_t qq, int ab, int cd)
+{
+    if (a.quartets) return qq + a.nq * ((int64_t)ab * a.ct.ncd + cd);
+    const int64_t bra = qq % a.nbra, ket = qq / a.nbra;
+    return bra + a.nbra * (ab + (int64_t)a.ct.nab * (cd + (int64_t)a.ct.ncd * ket));
+}
+
+__global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
+{
+    extern __shared__ __align__(16) double sm[];
+    const ClassTables& ct = a.ct;
+    const int tid = threadIdx.x;
+    const int TQ = a.TQ, KB = a.KB, KK = a.KK, IC = a.IC;
+    const int nhl = ct.nhl, nhb = ct.nhb, nhk = ct.nhk, ncd = ct.ncd, nab = ct.nab;
+    const int NI = TQ * IC * KK;  // R columns
+
+    // class tables into shared memory (once per CTA)
+    int* s_bstart = reinterpret_cast<int*>(sm + a.o_tab);
+    int* s_kstart = s_bstart + nab + 1;
+    int16_t* s_bp = reinterpret_cast<int16_t*>(s_kstart + ncd + 1);
+    int16_t* s_kq = s_bp + ct.Tab;
+    int16_t* s_pq = s_kq + ct.Tcd;
+    for (int i = tid; i <= nab; i += kNT) s_bstart[i] = ct.bra_start[i];
+    for (int i = tid; i <= ncd; i += kNT) s_kstart[i] = ct.ket_start[i];
+    for (int i = tid; i < ct.Tab; i += kNT) s_bp[i] = ct.bra_p[i];
+    for (int i = tid; i < ct.Tcd; i += kNT) s_kq[i] = ct.ket_q[i];
+    for (int i = tid; i < nhb * nhk; i += kNT) s_pq[i] = ct.pq[i];
+
+    int* s_q = reinterpret_cast<int*>(sm + a.o_q);  // [TQ][4]: bra, ket, Kbra, Kket
+    double* sEb = sm + a.o_Eb;
+    double* sEk = sm + a.o_Ek;
+    double* sPb = sm + a.o_Pb;
+    double* sPk = sm + a.o_Pk;
+    double* sR = sm + a.o_R;
+    double* sX = sm + a.o_X;
+
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const int64_t q0 = tile * TQ;
+        const int nqt = (int)min((int64_t)TQ, a.nq - q0);
+        __syncthreads();
+        for (int q = tid; q < TQ; q += kNT) {
+            int b = 0, k = 0, kb = 0, kk = 0;
+            if (q < nqt) {
+                const int64_t qq = q0 + q;
+                if (a.quartets) {
+                    b = (int)a.quartets[2 * qq];
+                    k = (int)a.quartets[2 * qq + 1];
+                } else {
+                    b = (int)(qq % a.nbra);
+                    k = (int)(qq / a.nbra);
+                }
+                kb = a.bra_kp[b];
+                kk = a.ket_kp[k];
+            }
+            s_q[4 * q] = b;
+            s_q[4 * q + 1] = k;
+            s_q[4 * q + 2] = kb;
+            s_q[4 * q + 3] = kk;
+        }
+        __syncthreads();
+        // stage primitive-pair scalars (and E products) of the tile
+        for (int idx = tid; idx < TQ * KB * PS_N; idx += kNT) {
+            const int q = idx / (KB * PS_N), r = idx - q * KB * PS_N, i = r / PS_N;
+            sPb[idx] = i < s_q[4 * q + 2] ? a.bra_ps[(size_t)s_q[4 * q] * KB * PS_N + r] : 1.0;
+        }
+        for (int idx = tid; idx < TQ * KK * PS_N; idx += kNT) {
+            const int q = idx / (KK * PS_N), r = idx - q * KK * PS_N, k = r / PS_N;
+            sPk[idx] = k < s_q[4 * q + 3] ? a.ket_ps[(size_t)s_q[4 * q + 1] * KK * PS_N + r] : 1.0;
+        }
+        if (a.e_smem) {
+            const int nb = KB * ct.Tab, nk = KK * ct.Tcd;
+            for (int idx = tid; idx < TQ * nb; idx += kNT) {
+                const int q = idx / nb, r = idx - q * nb, i = r / ct.Tab;
+                sEb[q * a.sEbS + r] = i < s_q[4 * q + 2] ? a.bra_E[(size_t)s_q[4 * q] * nb + r] : 0.0;
+            }
+            for (int idx = tid; idx < TQ * nk; idx += kNT) {
+                const int q = idx / nk, r = idx - q * nk, k = r / ct.Tcd;
+                sEk[q * a.sEkS + r] = k < s_q[4 * q + 3] ? a.ket_E[(size_t)s_q[4 * q + 1] * nk + r] : 0.0;
+            }
+        }
+        // output accumulators
+        double acc[kNACC];
+#pragma unroll
+        for (int s = 0; s < kNACC; ++s) acc[s] = 0.0;
+
+        for (int i0 = 0; i0 < KB; i0 += IC) {
+            __syncthreads();
+            // ---- A: auxiliary integrals of the primitive quartets (q, i0+ii, k)
+            for (int item = tid; item < NI; item += kNT) {
+                const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
+                const int i = i0 + ii;
+                Strided R{sR + item, NI};
+                if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
+                    const double* pb = sPb + (q * KB + i) * PS_N;
+                    const double* pk = sPk + (q * KK + k) * PS_N;
+                    const double zp = pb[PS_P], zq = pk[PS_P];
+                    const double rs = rsqrt(zp + zq);
+                    const double rho = zp * zq * (rs * rs);
+                    const double X = pb[PS_PX] - pk[PS_PX], Y = pb[PS_PY] - pk[PS_PY], Z = pb[PS_PZ] - pk[PS_PZ];
+                    const double PQ2 = fma(X, X, fma(Y, Y, Z * Z));
+                    const double T = rho * PQ2;
+                    double base[kLtotMax + 1];
+                    boys_eval(ct.L, T, a.boys, base);
+                    double f = pb[PS_INVP] * pk[PS_INVP] * rs;  // 2 pi^(5/2) / (zp zq sqrt(zp+zq))
+                    const double m2rho = -2.0 * rho;
+                    for (int n = 0; n <= ct.L; ++n) {
+                        base[n] *= f;
+                        f *= m2rho;
+                    }
+                    r_recursion(ct.L, base, X, Y, Z, a.rsteps, R);
+                } else {
+                    for (int e = 0; e < nhl; ++e) R[e] = 0.0;
+                }
+            }
+            __syncthreads();
+            for (int ii = 0; ii < IC && i0 + ii < KB; ++ii) {
+                const int i = i0 + ii;
+                // ---- B: ket transform + ket contraction
+                const int nB = TQ * nhb * ncd;
+                for (int item = tid; item < nB; item += kNT) {
+                    const int q = item % TQ, r = item / TQ, p = r % nhb, cd = r / nhb;
+                    const double* Ek = a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd;
+                    const double* Rc = sR + (q * IC + ii) * KK;
+                    const int16_t* pqrow = s_pq + p * nhk;
+                    const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
+                    double v = 0.0;
+                    for (int k = 0; k < KK; ++k) {
+                        const double* Ekk = Ek + k * ct.Tcd;
+                        const double* Rk = Rc + k;
+                        for (int t = t0; t < t1; ++t) v = fma(Ekk[t], Rk[(size_t)pqrow[s_kq[t]] * NI], v);
+                    }
+                    sX[(p * ncd + cd) * TQ + q] = v;
+                }
+                __syncthreads();
+                // ---- C: bra transform + bra contraction
+                const int nC = TQ * nab * ncd;
+                if (a.acc_regs) {
+#pragma unroll
+                    for (int s = 0; s < kNACC; ++s) {
+                        const int item = tid + s * kNT;
+                        if (item < nC) {
+                            const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
+                            const double* Eb = a.e_smem ? sEb + q * a.sEbS
+                                                        : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab;
+                            Eb += i * ct.Tab;
+                            double v = 0.0;
+                            for (int u = s_bstart[ab]; u < s_bstart[ab + 1]; ++u)
+                                v = fma(Eb[u], sX[(s_bp[u] * ncd + cd) * TQ + q], v);
+                            acc[s] += v;
+                        }
+                    }
+                } else {
+                    for (int item = tid; item < nC; item += kNT) {
+                        const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
+                        if (q >= nqt) continue;
+                        const double* Eb = a.e_smem ? sEb + q * a.sEbS : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab;
+                        Eb += i * ct.Tab;
+                        double v = 0.0;
+                        for (int u = s_bstart[ab]; u < s_bstart[ab + 1]; ++u)
+                            v = fma(Eb[u], sX[(s_bp[u] * ncd + cd) * TQ + q], v);
+                        const int64_t o = out_index(a, q0 + q, ab, cd);
+                        a.out[o] = (i == 0) ? v : a.out[o] + v;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (a.acc_regs) {
+            const int nC = TQ * nab * ncd;
+#pragma unroll
+            for (int s = 0; s < kNACC; ++s) {
+                const int item = tid + s * kNT;
+                if (item < nC) {
+                    const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
+                    if (q < nqt) a.out[out_index(a, q0 + q, ab, cd)] = acc[s];
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Boys entry kernel
+// ---------------------------------------------------------------------------
+__global__ void boys_kernel(int mmax, const double* T, int64_t n, const double* tab, double* F)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double f[ERI_BOYS_MMAX + 1];
+        boys_eval(mmax, T[i], tab, f);
+        for (int m = 0; m <= mmax; ++m) F[i * (mmax + 1) + m] = f[m];
+    }
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+int max_smem_optin()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (n <= 0) n = 48 * 1024;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// Tile planning: pick (TQ, IC, e_smem, acc_regs) so that shared memory fits
+// and the auxiliary-integral stage has enough independent items.
+// ---------------------------------------------------------------------------
+struct TilePlan {
+    int TQ, IC, e_smem, acc_regs;
+    int sEbS, sEkS;
+    int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;
+    size_t bytes;
+};
+
+static int odd_up(int n) { return n | 1; }
+
+static bool layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp)
+{
+    size_t off = 0;
+    auto take = [&](size_t nd) {
+        size_t o = off;
+        off += (nd + 1) & ~size_t(1);  // keep 16-byte alignment
+        return (int)o;
+    };
+    tp->TQ = TQ;
+    tp->IC = IC;
+    tp->e_smem = e_smem;
+    tp->sEbS = e_smem ? odd_up(KB * ct.Tab) : 0;
+    tp->sEkS = e_smem ? odd_up(KK * ct.Tcd) : 0;
+    tp->o_Eb = take((size_t)TQ * tp->sEbS);
+    tp->o_Ek = take((size_t)TQ * tp->sEkS);
+    tp->o_Pb = take((size_t)TQ * KB * PS_N);
+    tp->o_Pk = take((size_t)TQ * KK * PS_N);
+    tp->o_R = take((size_t)TQ * IC * KK * ct.nhl);
+    tp->o_X = take((size_t)TQ * ct.nhb * ct.ncd);
+    const size_t tab_bytes = 4 * (ct.nab + ct.ncd + 2) + 2 * (ct.Tab + ct.Tcd + ct.nhb * ct.nhk);
+    tp->o_tab = take((tab_bytes + 7) / 8);
+    tp->o_q = take((size_t)TQ * 2);
+    tp->bytes = off * 8;
+    tp->acc_regs = (TQ * ct.nab * ct.ncd <= kNT * kNACC) ? 1 : 0;
+    return tp->bytes <= (size_t)max_smem_optin();
+}
+
+static bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best)
+{
+    bool found = false;
+    double best_score = -1.0;
+    for (int e_smem = 1; e_smem >= 0; --e_smem) {
+        for (int TQ = 128; TQ >= 1; TQ /= 2) {
+            if (TQ > 1 && TQ * ct.nab * ct.ncd > kNT * kNACC) continue;  // prefer register accumulation
+            if (TQ > 1 && (int64_t)TQ > 2 * nq) continue;
+            for (int IC = KB; IC >= 1; IC = (IC + 1) / 2 - (IC == 1)) {
+                TilePlan tp;
+                if (!layout(ct, KB, KK, TQ, IC, e_smem, &tp)) {
+                    if (IC == 1) break;
+                    continue;
+                }
+                // score: utilisation of the stage-A items, the ket-stage items
+                // and the bra-stage items (fraction of kNT-wide rounds used)
+                auto util = [](int64_t n) {
+                    const int64_t rounds = (n + kNT - 1) / kNT;
+                    return rounds ? (double)n / (double)(rounds * kNT) : 0.0;
+                };
+                const int64_t nA = (int64_t)TQ * IC * KK;
+                const double wA = (double)ct.nhl * 2.0 + 40.0;
+                const double wB = (double)ct.nhb * ct.Tcd * KK;
+                const double wC = (double)ct.ncd * ct.Tab;
+                const double score = (wA + wB + wC) /
+                                     (wA / util(nA) + wB / util((int64_t)TQ * ct.nhb * ct.ncd) +
+                                      wC / util((int64_t)TQ * ct.nab * ct.ncd)) +
+                                     1e-3 * TQ * IC + (e_smem ? 0.05 : 0.0);
+                if (score > best_score) {
+                    best_score = score;
+                    *best = tp;
+                    found = true;
+                }
+                if (IC == 1) break;
+            }
+        }
+        if (found) break;
+    }
+    return found;
+}
+
+static int dev_err_to_code(int e)
+{
+    switch (e) {
+        case DEV_OK: return ERI_OK;
+        case DEV_ECLASS: return ERI_ECLASS;
+        case DEV_EINDEX: return ERI_EINVAL;
+        case DEV_EK: return ERI_EINVAL;
+        case DEV_ETIMEOUT: return ERI_ETIMEOUT;
+        default: return ERI_ECUDA;
+    }
+}
+
+static size_t align_up(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Prepass + pair tables shared by the forward and adjoint entry points.
+// On success fills the pair tables and the largest K on each centre.
+int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
+                  int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
+                  const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4])
+{
+    int err = ERI_OK;
+    const ClassTables* ct = get_class_tables(cls.la, cls.lb, cls.lc, cls.ld, st, &err);
+    if (!ct) return err;
+    *ct_out = ct;
+    int* status = device_status();
+    if (!status) return ERI_ECUDA;
+    int32_t* hinfo = host_pinned_i32(8);
+    if (!hinfo) return ERI_ENOMEM;
+    // info lives in the status block (slots 8..12), separate from the error word
+    int* dinfo = status + 8;
+    if (cudaMemsetAsync(dinfo, 0, 5 * sizeof(int), st) != cudaSuccess) return ERI_ECUDA;
+    PrepassArgs pa{basis->shell_l, basis->shell_K, basis->nshell, bra, nbra, ket, nket, quartets,
+                   quartets ? nq : (int64_t)0,
+                   {cls.la, cls.lb, cls.lc, cls.ld}, dinfo};
+    const int64_t n = std::max(std::max(nbra, nket), quartets ? nq : (int64_t)0);
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
+    prepass_kernel<<<std::max(grid, 1), 256, 0, st>>>(pa);
+    if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+    if (cudaMemcpyAsync(hinfo, dinfo, 5 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ERI_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ERI_ECUDA;
+    if (hinfo[4] != 0) return dev_err_to_code(hinfo[4]);
+    for (int c = 0; c < 4; ++c) kmax[c] = hinfo[c];
+    *KB = kmax[0] * kmax[1];
+    *KK = kmax[2] * kmax[3];
+    // workspace: pair tables of both sides
+    const size_t nb_ps = align_up(sizeof(double) * nbra * *KB * PS_N), nb_E = align_up(sizeof(double) * nbra * *KB * ct->Tab);
+    const size_t nk_ps = align_up(sizeof(double) * nket * *KK * PS_N), nk_E = align_up(sizeof(double) * nket * *KK * ct->Tcd);
+    const size_t nb_k = align_up(sizeof(int32_t) * nbra), nk_k = align_up(sizeof(int32_t) * nket);
+    const int grad = ldelta > 0;
+    const int eaxb = (cls.la + 3) * (cls.lb + 3) * (cls.la + cls.lb + 5);
+    const int eaxk = (cls.lc + 3) * (cls.ld + 3) * (cls.lc + cls.ld + 5);
+    const size_t nb_ax = grad ? align_up(sizeof(double) * nbra * *KB * 3 * eaxb) : 0;
+    const size_t nk_ax = grad ? align_up(sizeof(double) * nket * *KK * 3 * eaxk) : 0;
+    const size_t nb_z = grad ? align_up(sizeof(double) * nbra * *KB * 2) : 0;
+    const size_t nk_z = grad ? align_up(sizeof(double) * nket * *KK * 2) : 0;
+    uint8_t* ws = (uint8_t*)workspace(nb_ps + nb_E + nk_ps + nk_E + nb_k + nk_k + nb_ax + nk_ax + nb_z + nk_z, &err);
+    if (!ws) return err;
+    {
+        uint8_t* g0 = ws + nb_ps + nb_E + nk_ps + nk_E + nb_k + nk_k;
+        pb->ax = grad ? (double*)g0 : nullptr;
+        pk->ax = grad ? (double*)(g0 + nb_ax) : nullptr;
+        pb->zz = grad ? (double*)(g0 + nb_ax + nk_ax) : nullptr;
+        pk->zz = grad ? (double*)(g0 + nb_ax + nk_ax + nb_z) : nullptr;
+        pb->eax = eaxb;
+        pk->eax = eaxk;
+    }
+    pb->ps = (double*)ws;
+    pb->E = (double*)(ws + nb_ps);
+    pk->ps = (double*)(ws + nb_ps + nb_E);
+    pk->E = (double*)(ws + nb_ps + nb_E + nk_ps);
+    pb->kp = (int32_t*)(ws + nb_ps + nb_E + nk_ps + nk_E);
+    pk->kp = (int32_t*)(ws + nb_ps + nb_E + nk_ps + nk_E + nb_k);
+    for (int side = 0; side < 2; ++side) {
+        PairArgs p{};
+        p.centres = basis->centres;
+        p.shell_atom = basis->shell_atom;
+        p.shell_K = basis->shell_K;
+        p.shell_off = basis->shell_off;
+        p.exps = basis->exps;
+        p.coefs = basis->coefs;
+        p.pairs = side ? ket : bra;
+        p.npairs = side ? nket : nbra;
+        p.l1 = side ? cls.lc : cls.la;
+        p.l2 = side ? cls.ld : cls.lb;
+        p.KS = side ? *KK : *KB;
+        p.T = side ? ct->Tcd : ct->Tab;
+        p.fac = side ? ct->ket_fac : ct->bra_fac;
+        p.ket = side;
+        PairTables& t = side ? *pk : *pb;
+        p.ps = t.ps;
+        p.E = t.E;
+        p.kprim = t.kp;
+        p.ax = t.ax;
+        p.eax = t.eax;
+        p.zz = t.zz;
+        const int64_t tot = p.npairs * p.KS;
+        const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
+        pair_kernel<<<std::max(g, 1), 128, 0, st>>>(p);
+        if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+    }
+    return ERI_OK;
+}
+
+static int check_basis(const eri_basis_t* b)
+{
+    if (!b || !b->centres || !b->shell_atom || !b->shell_l || !b->shell_K || !b->shell_off || !b->exps || !b->coefs)
+        return ERI_EINVAL;
+    if (b->natom < 0 || b->nshell < 0 || b->nprim < 0) return ERI_EINVAL;
+    return ERI_OK;
+}
+
+static int check_class(eri_class_t c)
+{
+    const int l[4] = {c.la, c.lb, c.lc, c.ld};
+    for (int i = 0; i < 4; ++i)
+        if (l[i] < 0 || l[i] > kLmax) return ERI_EINVAL;
+    return ERI_OK;
+}
+
+int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
+                     int64_t nket, const int64_t* quartets, int64_t nq, int64_t len)
+{
+    if (check_class(cls) != ERI_OK || check_basis(basis) != ERI_OK) return ERI_EINVAL;
+    if (nbra < 0 || nket < 0 || (quartets && nq < 0)) return ERI_EINVAL;
+    if ((nbra > 0 && !bra) || (nket > 0 && !ket)) return ERI_EINVAL;
+    if (nbra > INT32_MAX || nket > INT32_MAX) return ERI_EINVAL;
+    const int64_t nqq = quartets ? nq : nbra * nket;
+    const int64_t nab = host_nc(cls.la) * host_nc(cls.lb), ncd = host_nc(cls.lc) * host_nc(cls.ld);
+    if (len < nqq * nab * ncd) return ERI_EINVAL;
+    return ERI_OK;
+}
+
+}  // namespace eri
+
+using namespace eri;
+
+extern "C" int eri_boys(int mmax, const double* T, int64_t n, double* F, void* stream)
+{
+    if (mmax < 0 || mmax > ERI_BOYS_MMAX || n < 0) return ERI_EINVAL;
+    if (n == 0) return ERI_OK;
+    if (!T || !F) return ERI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int err = ERI_OK;
+    const double* tab = get_boys_table(mmax, st, &err);
+    if (!tab) return err;
+    const int grid = (int)std::min<int64_t>((n + 127) / 128, 16 * sm_count());
+    boys_kernel<<<grid, 128, 0, st>>>(mmax, T, n, tab, F);
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
+}
+
+extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
+                         const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq, double* out,
+                         int64_t out_len, int precision, void* stream)
+{
+    int err = check_batch_args(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, out_len);
+    if (err != ERI_OK) return err;
+    if (precision != ERI_PREC_FP64 && precision != ERI_PREC_SPLIT) return ERI_EINVAL;
+    const int64_t nqq = quartets ? nq : nbra * nket;
+    if (nqq == 0 || nbra == 0 || nket == 0) return ERI_OK;
+    if (!out) return ERI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const ClassTables* ct = nullptr;
+    PairTables pb{}, pk{};
+    int KB = 0, KK = 0, kmax[4];
+    err = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB, &KK,
+                        kmax);
+    if (err != ERI_OK) return err;
+    const double* boys = get_boys_table(ct->L, st, &err);
+    if (!boys) return err;
+    const RStep* rs = get_rsteps(st, &err);
+    if (!rs) return err;
+    TilePlan tp;
+    if (!plan_tiles(*ct, KB, KK, nqq, &tp)) return ERI_EINVAL;
+    FwdArgs a{};
+    a.ct = *ct;
+    a.boys = boys;
+    a.rsteps = rs;
+    a.bra_ps = pb.ps;
+    a.bra_E = pb.E;
+    a.bra_kp = pb.kp;
+    a.ket_ps = pk.ps;
+    a.ket_E = pk.E;
+    a.ket_kp = pk.kp;
+    a.quartets = quartets;
+    a.nq = nqq;
+    a.nbra = nbra;
+    a.nket = nket;
+    a.out = out;
+    a.TQ = tp.TQ;
+    a.KB = KB;
+    a.KK = KK;
+    a.IC = tp.IC;
+    a.e_smem = tp.e_smem;
+    a.acc_regs = tp.acc_regs;
+    a.sEbS = tp.sEbS;
+    a.sEkS = tp.sEkS;
+    a.o_Eb = tp.o_Eb;
+    a.o_Ek = tp.o_Ek;
+    a.o_Pb = tp.o_Pb;
+    a.o_Pk = tp.o_Pk;
+    a.o_R = tp.o_R;
+    a.o_X = tp.o_X;
+    a.o_tab = tp.o_tab;
+    a.o_q = tp.o_q;
+    a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
+    if (cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
+        return ERI_ECUDA;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel, kNT, tp.bytes);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)per_sm * sm_count());
+    fwd_kernel<<<(int)grid, kNT, tp.bytes, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
+}

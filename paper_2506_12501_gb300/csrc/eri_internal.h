@@ -1,0 +1,110 @@
+// eri_internal.h -- shared host/device definitions of the GB300 ERI library.
+//
+// Index conventions used by every kernel:
+//  * Hermite functions Lambda_(t,u,v) of total order N = t+u+v <= L are
+//    numbered "tetrahedrally": all orders N = 0,1,2,... in turn, inside an
+//    order by t descending then u descending.  The numbering of order <= L'
+//    is a prefix of the numbering of order <= L for L' < L, so one table
+//    serves every class.  Nh(L) = (L+1)(L+2)(L+3)/6 functions.
+//  * Cartesian components of a shell: x^l first, then lexicographic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/eri.h"
+
+namespace eri {
+
+constexpr int kLmax = ERI_LMAX;            // per shell
+constexpr int kKmax = ERI_KMAX;            // primitives per shell
+constexpr int kLtotMax = 4 * kLmax + 2;    // largest L of an R table (gradient adds 2)
+constexpr int kNhMax = (kLtotMax + 1) * (kLtotMax + 2) * (kLtotMax + 3) / 6;
+
+// Boys-function table: grid T_j = j * kBoysStep, j = 0..kBoysGrid-1.
+constexpr int kBoysInvStep = 32;           // 1/step (a power of two: T*32 is exact)
+constexpr double kBoysStep = 1.0 / kBoysInvStep;
+constexpr double kBoysTmax = 80.0;         // beyond: large-T form (Section 3.2.1)
+constexpr int kBoysGrid = (int)(kBoysTmax * kBoysInvStep) + 2;
+constexpr int kBoysOrder = 7;              // Taylor terms k = 0..6, |delta| <= 1/64
+constexpr int kBoysMtab = ERI_BOYS_MMAX + kBoysOrder;  // rows hold F_0..F_kBoysMtab
+
+constexpr int host_nh(int l) { return (l + 1) * (l + 2) * (l + 3) / 6; }
+constexpr int host_nc(int l) { return (l + 1) * (l + 2) / 2; }
+
+// One step of the auxiliary recursion Eq. r-rr for Hermite function e:
+//   [e]^(m) = X_axis [src1]^(m+1) + coef [src2]^(m+1)
+// with src1 = e - 1_axis, src2 = e - 2_axis (coef = e_axis - 1, src2 unused if 0).
+struct alignas(16) RStep {
+    int16_t src1, src2;
+    int8_t axis, coef;
+    int16_t pad;
+    double coefd;  // coef as a double (no int->double conversion on the device)
+};
+
+// Per-class tables (device copy lives in one blob; pointers into it).
+struct ClassTables {
+    int la, lb, lc, ld, L, Lb, Lk;
+    int nab, ncd, nhb, nhk, nhl;
+    int Tab, Tcd;                 // number of nonzero (component pair, Hermite) terms
+    // bra terms, grouped by ab: [bra_start[ab], bra_start[ab+1])
+    const int* bra_start;         // [nab+1]
+    const int16_t* bra_p;         // [Tab] Hermite index of p (order <= Lb)
+    const uint8_t* bra_fac;       // [Tab][6]: (ax,bx,t),(ay,by,u),(az,bz,v) -> E factor quanta
+    // ket terms, grouped by cd
+    const int* ket_start;         // [ncd+1]
+    const int16_t* ket_q;         // [Tcd] Hermite index of q (order <= Lk)
+    const uint8_t* ket_fac;       // [Tcd][6]
+    const int16_t* pq;            // [nhb][nhk] Hermite index of p+q (order <= L)
+    // adjoint: Hermite ranges widened by 2 on one side (shifted functions)
+    int nhb2, nhk2, nhl2;         // Nh(Lb+2), Nh(Lk+2), Nh(L+2)
+    const int16_t* pq2b;          // [nhb2][nhk] Hermite index of p'+q
+    const int16_t* pq2k;          // [nhb][nhk2] Hermite index of p+q'
+    const int16_t* herm3;         // [(t*H + u)*H + v] Hermite index, H = kLtotMax+1
+};
+
+// Primitive-pair scalars written by the pair kernel.
+enum { PS_P = 0, PS_PX, PS_PY, PS_PZ, PS_INVP, PS_N };
+
+// Device-side error word values (first error wins).
+enum { DEV_OK = 0, DEV_ECLASS = 1, DEV_EINDEX = 2, DEV_EK = 3, DEV_ETIMEOUT = 4 };
+
+// Host helpers implemented in eri_tables.cu
+struct HostClassTables;
+const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t s, int* err);
+const double* get_boys_table(int L, cudaStream_t s, int* err);    // rows of F_{L+k}(T_j)/k!, plus exp
+const double* get_boys_master(cudaStream_t s, int* err);          // rows of F_0..F_kBoysMtab and exp
+const RStep* get_rsteps(cudaStream_t s, int* err);                 // recursion step table (device)
+void release_all();
+
+// Hermite numbering helpers (host)
+int herm_index(int t, int u, int v);
+void herm_tuv(int idx, int* t, int* u, int* v);
+
+// Primitive-pair tables of one side of a batch (inside the workspace).
+struct PairTables {
+    double* ps;   // [npairs][KS][PS_N]
+    double* E;    // [npairs][KS][T] E^x E^y E^z products (ket: times (-1)^{l_q})
+    int32_t* kp;  // [npairs] number of primitive pairs
+    double* ax;   // adjoint only: per-axis E tables with raised indices
+    int eax;      // doubles per axis table
+    double* zz;   // adjoint only: [npairs][KS][2] exponents
+};
+
+// Prepass + pair tables shared by eri_batch and eri_batch_grad.  ldelta > 0
+// also fills the adjoint tables.  Synchronises `st` once (reads the largest
+// contraction degree of each centre).
+int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
+                  int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
+                  const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4]);
+int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
+                     int64_t nket, const int64_t* quartets, int64_t nq, int64_t len);
+int sm_count();
+int max_smem_optin();
+
+// Device workspace (grows, cached per process; calls on one device serialise)
+void* workspace(size_t bytes, int* err);
+int* device_status();   // device error word
+int32_t* host_pinned_i32(int n);
+
+}  // namespace eri

@@ -1,0 +1,398 @@
+// eri_tables.cu -- host-built tables of the ERI library: Hermite numbering,
+// sparse Hermite<->Cartesian term lists per class, the auxiliary-recursion
+// step table, the Boys-function tables, and the cached device workspace.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <array>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "eri_internal.h"
+
+namespace eri {
+
+// ---------------------------------------------------------------------------
+// Hermite numbering (order by total N, then t descending, then u descending)
+// ---------------------------------------------------------------------------
+static std::vector<int> g_herm_idx;   // (t,u,v) -> index, dense (kLtotMax+1)^3
+static std::vector<int> g_herm_t, g_herm_u, g_herm_v;
+static std::once_flag g_herm_once;
+
+static void build_herm()
+{
+    const int n = kLtotMax + 1;
+    g_herm_idx.assign(n * n * n, -1);
+    for (int N = 0; N <= kLtotMax; ++N)
+        for (int t = N; t >= 0; --t)
+            for (int u = N - t; u >= 0; --u) {
+                int v = N - t - u;
+                g_herm_idx[(t * n + u) * n + v] = (int)g_herm_t.size();
+                g_herm_t.push_back(t);
+                g_herm_u.push_back(u);
+                g_herm_v.push_back(v);
+            }
+}
+
+int herm_index(int t, int u, int v)
+{
+    std::call_once(g_herm_once, build_herm);
+    const int n = kLtotMax + 1;
+    if (t < 0 || u < 0 || v < 0 || t + u + v > kLtotMax) return -1;
+    return g_herm_idx[(t * n + u) * n + v];
+}
+
+void herm_tuv(int idx, int* t, int* u, int* v)
+{
+    std::call_once(g_herm_once, build_herm);
+    *t = g_herm_t[idx];
+    *u = g_herm_u[idx];
+    *v = g_herm_v[idx];
+}
+
+static std::vector<std::array<int, 3>> carts(int l)
+{
+    std::vector<std::array<int, 3>> r;
+    for (int ax = l; ax >= 0; --ax)
+        for (int ay = l - ax; ay >= 0; --ay) r.push_back({ax, ay, l - ax - ay});
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Auxiliary recursion steps, Eq. r-rr.  For each Hermite function e of order
+// >= 1 pick the axis that needs the fewest FP64 operations: an axis with
+// e_i = 1 needs only X_i * [e-1_i] (the e_i-1 coefficient vanishes).
+// ---------------------------------------------------------------------------
+const RStep* get_rsteps(cudaStream_t s, int* err)
+{
+    static std::map<int, RStep*> tabs;
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = tabs.find(dev);
+    if (it != tabs.end()) return it->second;
+    std::vector<RStep> st(kNhMax);
+    std::memset(st.data(), 0, sizeof(RStep) * kNhMax);
+    for (int e = 1; e < kNhMax; ++e) {
+        int r[3];
+        herm_tuv(e, &r[0], &r[1], &r[2]);
+        int axis = -1;
+        for (int i = 0; i < 3; ++i)
+            if (r[i] == 1) { axis = i; break; }
+        if (axis < 0)
+            for (int i = 0; i < 3; ++i)
+                if (r[i] > 0 && (axis < 0 || r[i] < r[axis])) axis = i;
+        int d1[3] = {r[0], r[1], r[2]}, d2[3] = {r[0], r[1], r[2]};
+        d1[axis] -= 1;
+        d2[axis] -= 2;
+        st[e].axis = (int8_t)axis;
+        st[e].coef = (int8_t)(r[axis] - 1);
+        st[e].coefd = (double)(r[axis] - 1);
+        st[e].src1 = (int16_t)herm_index(d1[0], d1[1], d1[2]);
+        st[e].src2 = (int16_t)(r[axis] >= 2 ? herm_index(d2[0], d2[1], d2[2]) : 0);
+    }
+    RStep* d = nullptr;
+    if (cudaMalloc(&d, sizeof(RStep) * kNhMax) != cudaSuccess) {
+        *err = ERI_ENOMEM;
+        return nullptr;
+    }
+    if (cudaMemcpyAsync(d, st.data(), sizeof(RStep) * kNhMax, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(d);
+        *err = ERI_ECUDA;
+        return nullptr;
+    }
+    tabs[dev] = d;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Class tables
+// ---------------------------------------------------------------------------
+struct ClassEntry {
+    ClassTables t;
+    void* blob = nullptr;
+};
+static std::map<std::tuple<int, int, int, int, int>, ClassEntry> g_classes;
+static std::mutex g_class_mu;
+
+const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t s, int* err)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_class_mu);
+    auto key = std::make_tuple(dev, la, lb, lc, ld);
+    auto it = g_classes.find(key);
+    if (it != g_classes.end()) return &it->second.t;
+
+    ClassTables t{};
+    t.la = la; t.lb = lb; t.lc = lc; t.ld = ld;
+    t.Lb = la + lb; t.Lk = lc + ld; t.L = t.Lb + t.Lk;
+    t.nab = host_nc(la) * host_nc(lb);
+    t.ncd = host_nc(lc) * host_nc(ld);
+    t.nhb = host_nh(t.Lb); t.nhk = host_nh(t.Lk); t.nhl = host_nh(t.L);
+
+    auto build_terms = [](int l1, int l2, std::vector<int>& start, std::vector<int16_t>& herm,
+                          std::vector<uint8_t>& fac) {
+        const int L12 = l1 + l2;
+        start.push_back(0);
+        for (auto& a : carts(l1))
+            for (auto& b : carts(l2)) {
+                for (int tx = 0; tx <= a[0] + b[0]; ++tx)
+                    for (int ty = 0; ty <= a[1] + b[1]; ++ty)
+                        for (int tz = 0; tz <= a[2] + b[2]; ++tz) {
+                            herm.push_back((int16_t)herm_index(tx, ty, tz));
+                            const int tt[3] = {tx, ty, tz};
+                            for (int i = 0; i < 3; ++i)
+                                fac.push_back((uint8_t)((a[i] * (l2 + 1) + b[i]) * (L12 + 1) + tt[i]));
+                        }
+                start.push_back((int)herm.size());
+            }
+    };
+    std::vector<int> bs, ks;
+    std::vector<int16_t> bp, kq, pq;
+    std::vector<uint8_t> bf, kf;
+    build_terms(la, lb, bs, bp, bf);
+    build_terms(lc, ld, ks, kq, kf);
+    t.Tab = (int)bp.size();
+    t.Tcd = (int)kq.size();
+    auto sum_table = [](int n1, int n2, std::vector<int16_t>& out) {
+        out.resize((size_t)n1 * n2);
+        for (int p = 0; p < n1; ++p)
+            for (int q = 0; q < n2; ++q) {
+                int a, b, c, x, y, z;
+                herm_tuv(p, &a, &b, &c);
+                herm_tuv(q, &x, &y, &z);
+                out[(size_t)p * n2 + q] = (int16_t)herm_index(a + x, b + y, c + z);
+            }
+    };
+    sum_table(t.nhb, t.nhk, pq);
+    t.nhb2 = host_nh(t.Lb + 2);
+    t.nhk2 = host_nh(t.Lk + 2);
+    t.nhl2 = host_nh(t.L + 2);
+    std::vector<int16_t> pq2b, pq2k, h3;
+    sum_table(t.nhb2, t.nhk, pq2b);
+    sum_table(t.nhb, t.nhk2, pq2k);
+    {
+        const int H = kLtotMax + 1;
+        h3.assign((size_t)H * H * H, -1);
+        for (int a = 0; a < H; ++a)
+            for (int b = 0; b < H; ++b)
+                for (int c = 0; c < H; ++c) h3[((size_t)a * H + b) * H + c] = (int16_t)herm_index(a, b, c);
+    }
+    // one blob: ints first (aligned), then int16, then uint8
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 15) & ~size_t(15);
+        return o;
+    };
+    size_t o_bs = take(bs.size() * 4), o_ks = take(ks.size() * 4);
+    size_t o_bp = take(bp.size() * 2), o_kq = take(kq.size() * 2), o_pq = take(pq.size() * 2);
+    size_t o_pq2b = take(pq2b.size() * 2), o_pq2k = take(pq2k.size() * 2), o_h3 = take(h3.size() * 2);
+    size_t o_bf = take(bf.size()), o_kf = take(kf.size());
+    std::vector<uint8_t> host(off);
+    std::memcpy(host.data() + o_bs, bs.data(), bs.size() * 4);
+    std::memcpy(host.data() + o_ks, ks.data(), ks.size() * 4);
+    std::memcpy(host.data() + o_bp, bp.data(), bp.size() * 2);
+    std::memcpy(host.data() + o_kq, kq.data(), kq.size() * 2);
+    std::memcpy(host.data() + o_pq, pq.data(), pq.size() * 2);
+    std::memcpy(host.data() + o_pq2b, pq2b.data(), pq2b.size() * 2);
+    std::memcpy(host.data() + o_pq2k, pq2k.data(), pq2k.size() * 2);
+    std::memcpy(host.data() + o_h3, h3.data(), h3.size() * 2);
+    std::memcpy(host.data() + o_bf, bf.data(), bf.size());
+    std::memcpy(host.data() + o_kf, kf.data(), kf.size());
+    void* blob = nullptr;
+    if (cudaMalloc(&blob, off) != cudaSuccess) {
+        *err = ERI_ENOMEM;
+        return nullptr;
+    }
+    if (cudaMemcpyAsync(blob, host.data(), off, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(blob);
+        *err = ERI_ECUDA;
+        return nullptr;
+    }
+    uint8_t* b = (uint8_t*)blob;
+    t.bra_start = (const int*)(b + o_bs);
+    t.ket_start = (const int*)(b + o_ks);
+    t.bra_p = (const int16_t*)(b + o_bp);
+    t.ket_q = (const int16_t*)(b + o_kq);
+    t.pq = (const int16_t*)(b + o_pq);
+    t.pq2b = (const int16_t*)(b + o_pq2b);
+    t.pq2k = (const int16_t*)(b + o_pq2k);
+    t.herm3 = (const int16_t*)(b + o_h3);
+    t.bra_fac = b + o_bf;
+    t.ket_fac = b + o_kf;
+    ClassEntry& e = g_classes[key];
+    e.t = t;
+    e.blob = blob;
+    return &e.t;
+}
+
+// ---------------------------------------------------------------------------
+// Boys tables.  Master rows: F_m(T_j), m = 0..kBoysMtab, then exp(-T_j),
+// computed in long double: the top order by the series
+//   F_M(T) = exp(-T) sum_k (2T)^k / ((2M+1)(2M+3)...(2M+2k+1))
+// (all terms positive) and the lower orders by the downward recursion
+//   F_m(T) = (2T F_{m+1}(T) + exp(-T)) / (2m+1),
+// which is stable for every T.
+// Per-L rows (8 doubles, one 64-byte line): F_{L+k}(T_j)/k!, k = 0..6, and
+// exp(-T_j): the coefficients of the Taylor expansion about T_j used by the
+// kernels' Boys evaluation.
+// ---------------------------------------------------------------------------
+static std::vector<long double> g_master_host;
+static std::once_flag g_master_once;
+
+static void build_master()
+{
+    const int W = kBoysMtab + 2;
+    g_master_host.assign((size_t)kBoysGrid * W, 0.0L);
+    for (int j = 0; j < kBoysGrid; ++j) {
+        const long double T = (long double)j / kBoysInvStep;
+        const long double eT = expl(-T);
+        long double term = 1.0L / (2 * kBoysMtab + 1), sum = term;
+        for (int k = 1; k < 10000; ++k) {
+            term *= 2.0L * T / (long double)(2 * kBoysMtab + 2 * k + 1);
+            sum += term;
+            if (term < sum * 1e-22L) break;
+        }
+        long double* row = &g_master_host[(size_t)j * W];
+        row[kBoysMtab] = eT * sum;
+        for (int m = kBoysMtab - 1; m >= 0; --m) row[m] = (2.0L * T * row[m + 1] + eT) / (long double)(2 * m + 1);
+        row[kBoysMtab + 1] = eT;
+    }
+}
+
+static std::map<std::pair<int, int>, double*> g_boys_tabs;
+static std::mutex g_boys_mu;
+
+const double* get_boys_table(int L, cudaStream_t s, int* err)
+{
+    std::call_once(g_master_once, build_master);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_boys_mu);
+    auto key = std::make_pair(dev, L);
+    auto it = g_boys_tabs.find(key);
+    if (it != g_boys_tabs.end()) return it->second;
+    const int W = kBoysMtab + 2;
+    std::vector<double> tab((size_t)kBoysGrid * 8);
+    long double fact[kBoysOrder];
+    fact[0] = 1;
+    for (int k = 1; k < kBoysOrder; ++k) fact[k] = fact[k - 1] * k;
+    for (int j = 0; j < kBoysGrid; ++j) {
+        const long double* row = &g_master_host[(size_t)j * W];
+        for (int k = 0; k < kBoysOrder; ++k) tab[(size_t)j * 8 + k] = (double)(row[L + k] / fact[k]);
+        tab[(size_t)j * 8 + 7] = (double)row[kBoysMtab + 1];
+    }
+    double* d = nullptr;
+    if (cudaMalloc(&d, tab.size() * sizeof(double)) != cudaSuccess) {
+        *err = ERI_ENOMEM;
+        return nullptr;
+    }
+    if (cudaMemcpyAsync(d, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(d);
+        *err = ERI_ECUDA;
+        return nullptr;
+    }
+    g_boys_tabs[key] = d;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace, status word, pinned scratch
+// ---------------------------------------------------------------------------
+struct DevState {
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int* status = nullptr;
+};
+static std::map<int, DevState> g_dev;
+static std::mutex g_dev_mu;
+
+void* workspace(size_t bytes, int* err)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevState& d = g_dev[dev];
+    if (bytes <= d.ws_bytes) return d.ws;
+    if (d.ws) {
+        cudaDeviceSynchronize();
+        cudaFree(d.ws);
+        d.ws = nullptr;
+        d.ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&d.ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        *err = ERI_ENOMEM;
+        return nullptr;
+    }
+    d.ws_bytes = want;
+    return d.ws;
+}
+
+int* device_status()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevState& d = g_dev[dev];
+    if (!d.status) {
+        if (cudaMalloc(&d.status, 64) != cudaSuccess) return nullptr;
+        cudaMemset(d.status, 0, 64);
+        cudaDeviceSynchronize();
+    }
+    return d.status;
+}
+
+int32_t* host_pinned_i32(int n)
+{
+    static int32_t* p = nullptr;
+    static int cap = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (n > cap) {
+        if (p) cudaFreeHost(p);
+        if (cudaMallocHost(&p, sizeof(int32_t) * n) != cudaSuccess) {
+            p = nullptr;
+            cap = 0;
+            return nullptr;
+        }
+        cap = n;
+    }
+    return p;
+}
+
+void release_all()
+{
+    {
+        std::lock_guard<std::mutex> lk(g_dev_mu);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        auto it = g_dev.find(dev);
+        if (it != g_dev.end()) {
+            if (it->second.ws) cudaFree(it->second.ws);
+            if (it->second.status) cudaFree(it->second.status);
+            g_dev.erase(it);
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_class_mu);
+        for (auto& kv : g_classes) cudaFree(kv.second.blob);
+        g_classes.clear();
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_boys_mu);
+        for (auto& kv : g_boys_tabs) cudaFree(kv.second);
+        g_boys_tabs.clear();
+    }
+}
+
+}  // namespace eri

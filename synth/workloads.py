@@ -26,7 +26,7 @@ __all__ = [
     "norm_coef", "Basis", "basis_from_shells", "quartet_shells", "class_of",
     "config1_pp_primitive", "class_sweep_pools", "class_sweep_batch", "all_classes",
     "molecule_geometry", "molecule_basis", "adjoint_workload", "split_batch",
-    "small_random_batch",
+    "small_random_batch", "unique_pairs", "class_batches", "all_unique_quartets", "density_weights",
 ]
 
 
@@ -230,3 +230,60 @@ def adjoint_workload(natom: int = 16, radius: float = 4.4, seed: int = 0):
     U = rng.uniform(-1.0, 1.0, size=(nbf, nbf))
     D = np.triu(U) + np.triu(U, 1).T
     return basis, D, bf_off
+
+
+# --------------------------------------------------------------------------
+# Unique shell quartets of a basis, grouped by class (index plumbing only)
+# --------------------------------------------------------------------------
+def unique_pairs(basis):
+    """All shell pairs (i, j), i >= j, each ordered so that l_first >= l_second."""
+    ns = basis.nshell
+    i, j = np.tril_indices(ns)
+    li, lj = basis.shell_l[i], basis.shell_l[j]
+    swap = li < lj
+    a = np.where(swap, j, i)
+    b = np.where(swap, i, j)
+    return np.stack([a, b], axis=1).astype(np.int32)
+
+
+def class_batches(basis, pairs, quartet_pairs):
+    """Group quartets of pair indices (P, Q) by class (l of the four shells).
+    Returns {cls: (bra_pairs, ket_pairs, quartets)} with per-class compact
+    pair lists and (bra index, ket index) quartets."""
+    l = basis.shell_l
+    P, Q = quartet_pairs[:, 0], quartet_pairs[:, 1]
+    cls_arr = np.stack([l[pairs[P, 0]], l[pairs[P, 1]], l[pairs[Q, 0]], l[pairs[Q, 1]]], axis=1)
+    key = ((cls_arr[:, 0] * 8 + cls_arr[:, 1]) * 8 + cls_arr[:, 2]) * 8 + cls_arr[:, 3]
+    out = {}
+    for k in np.unique(key):
+        sel = np.where(key == k)[0]
+        cls = tuple(int(x) for x in cls_arr[sel[0]])
+        bra_u, bra_inv = np.unique(P[sel], return_inverse=True)
+        ket_u, ket_inv = np.unique(Q[sel], return_inverse=True)
+        out[cls] = (np.ascontiguousarray(pairs[bra_u]), np.ascontiguousarray(pairs[ket_u]),
+                    np.stack([bra_inv, ket_inv], axis=1).astype(np.int64))
+    return out
+
+
+def all_unique_quartets(basis):
+    """Every unique quartet (pair P >= pair Q) of the basis, by class."""
+    pairs = unique_pairs(basis)
+    n = pairs.shape[0]
+    P, Q = np.tril_indices(n)
+    return pairs, class_batches(basis, pairs, np.stack([P, Q], axis=1))
+
+
+def density_weights(cls, bra, ket, quartets, D, bf_off):
+    """W_abcd = D_ab D_cd over the Cartesian functions of each quartet, in the
+    list-form output layout W[q + nq*(ab*ncd + cd)]."""
+    la, lb, lc, ld = cls
+    nca, ncb, ncc, ncd_ = ((l + 1) * (l + 2) // 2 for l in cls)
+    q = np.asarray(quartets)
+    A = bf_off[bra[q[:, 0], 0]][:, None] + np.arange(nca)[None, :]
+    B = bf_off[bra[q[:, 0], 1]][:, None] + np.arange(ncb)[None, :]
+    C = bf_off[ket[q[:, 1], 0]][:, None] + np.arange(ncc)[None, :]
+    Dd = bf_off[ket[q[:, 1], 1]][:, None] + np.arange(ncd_)[None, :]
+    Dab = D[A[:, :, None], B[:, None, :]].reshape(len(q), -1)   # [q][ab]
+    Dcd = D[C[:, :, None], Dd[:, None, :]].reshape(len(q), -1)  # [q][cd]
+    W = Dab[:, :, None] * Dcd[:, None, :]                       # [q][ab][cd]
+    return np.ascontiguousarray(W.reshape(len(q), -1).T).reshape(-1)

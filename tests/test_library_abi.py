@@ -1,0 +1,55 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/*.h declares (CPU only: no kernel is launched)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+(eri_[a-z_0-9]+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for n in ("eri_boys", "eri_batch", "eri_last_status", "eri_error_string", "eri_finalize"):
+        assert n in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_2506_12501_gb300 import build
+    path = build.build()
+    assert os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = declared_symbols() - exported
+    assert not missing, missing
+    lib = ctypes.CDLL(path)
+    for n in declared_symbols():
+        assert hasattr(lib, n)
+
+
+def test_error_strings_without_gpu():
+    import paper_2506_12501_gb300 as eri
+    assert "class" in eri.error_string(eri.ERI_ECLASS)
+    assert eri.error_string(eri.ERI_OK) == "ok"
+    assert eri.error_string(12345) == "unknown error"
+
+
+def test_kernels_compiled_for_sm103a():
+    """Every translation unit is compiled with -gencode arch=compute_103a,code=sm_103a."""
+    from paper_2506_12501_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
