@@ -104,9 +104,12 @@ int eri_boys(int mmax, const double* T, int64_t n, double* F, void* stream);
  *                      out_len >= nbra*nket*nab*ncd;
  *        list form     out[q + nq*(ab*ncd + cd)], out_len >= nq*nab*ncd.
  *   precision: ERI_PREC_FP64 or ERI_PREC_SPLIT.
- * A shell whose l disagrees with `cls` makes the kernel skip that pair's
- * quartets (their outputs are left as zeros) and is reported by
- * eri_last_status() as ERI_ECLASS after the stream has been synchronised.
+ * Before any integral kernel runs, a validation kernel checks every shell
+ * and quartet index (ERI_EINVAL if out of range), every contraction degree
+ * (ERI_EINVAL if outside 1..ERI_KMAX) and every shell's angular momentum
+ * against `cls` (ERI_ECLASS); its verdict and the largest contraction degree
+ * per centre are read back, so each call synchronises `stream` once.  On an
+ * error `out` is left untouched.
  * nbra == 0, nket == 0 or nq == 0 is a no-op.
  */
 int eri_batch(eri_class_t cls, const eri_basis_t* basis,
@@ -139,6 +142,20 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
  * error a kernel recorded since the previous call (then clears it).
  */
 int eri_last_status(void* stream);
+
+/*
+ * Kernel timing hook (measurement support, not part of the method).
+ * eri_profile_enable(1) makes every later launch of the dominant kernels
+ * record CUDA events on its own stream; eri_profile_read() waits for them
+ * and returns, per kernel id (0 = forward tile kernel, 1 = adjoint kernel,
+ * 2 = pair kernel, 3 = prepass), the number of launches and their summed
+ * duration in milliseconds since the last reset, then resets.  Arrays are
+ * HOST memory of length n (n <= 8).  eri_launch_count() returns the number
+ * of kernels the library has launched since load (all kernels).
+ */
+int eri_profile_enable(int on);
+int eri_profile_read(int n, int64_t* launches, double* ms);
+int64_t eri_launch_count(void);
 
 /* Human-readable text for an error code (static storage). */
 const char* eri_error_string(int code);

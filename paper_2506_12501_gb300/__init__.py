@@ -14,6 +14,10 @@ from .binding import (  # noqa: F401
     eri_batch_grad,
     eri_last_status,
     eri_finalize,
+    eri_profile_enable,
+    eri_profile_read,
+    eri_launch_count,
+    PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS,
     error_string,
     lib,
     nc,

@@ -40,7 +40,9 @@ class eri_basis_t(ctypes.Structure):
                 ("nprim", ctypes.c_int32)]
 
 
-EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize"]
+EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
+           "eri_profile_enable", "eri_profile_read", "eri_launch_count"]
+PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS = 0, 1, 2, 3
 
 
 def lib() -> ctypes.CDLL:
@@ -59,6 +61,12 @@ def lib() -> ctypes.CDLL:
             L.eri_error_string.argtypes = [I]
             L.eri_error_string.restype = ctypes.c_char_p
             L.eri_finalize.argtypes = []
+            L.eri_profile_enable.argtypes = [I]
+            L.eri_profile_enable.restype = I
+            L.eri_profile_read.argtypes = [I, P, P]
+            L.eri_profile_read.restype = I
+            L.eri_launch_count.argtypes = []
+            L.eri_launch_count.restype = I64
             for f in ("eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_finalize"):
                 getattr(L, f).restype = I
             _lib = L
@@ -172,3 +180,21 @@ def eri_last_status(stream=None) -> int:
 
 def eri_finalize() -> int:
     return lib().eri_finalize()
+
+
+def eri_profile_enable(on: bool = True) -> None:
+    _check(lib().eri_profile_enable(1 if on else 0), "eri_profile_enable")
+
+
+def eri_profile_read() -> dict:
+    """{kernel id: (launches, total ms)} since the last read (waits for the events)."""
+    n = 4
+    launches = (ctypes.c_int64 * n)()
+    ms = (ctypes.c_double * n)()
+    _check(lib().eri_profile_read(n, ctypes.cast(launches, ctypes.c_void_p), ctypes.cast(ms, ctypes.c_void_p)),
+           "eri_profile_read")
+    return {i: (int(launches[i]), float(ms[i])) for i in range(n)}
+
+
+def eri_launch_count() -> int:
+    return int(lib().eri_launch_count())

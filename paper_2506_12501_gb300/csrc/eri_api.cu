@@ -1,7 +1,79 @@
 // eri_api.cu -- status, error strings and teardown of the ERI library.
+#include <atomic>
+#include <mutex>
+#include <vector>
+
 #include "eri_internal.h"
 
+namespace eri {
+
+static std::atomic<int> g_prof_on{0};
+static std::atomic<int64_t> g_launches{0};
+static std::mutex g_prof_mu;
+struct ProfRec {
+    int id;
+    cudaEvent_t a, b;
+};
+static std::vector<ProfRec> g_prof_pending;
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int id_, cudaStream_t st_) : id(id_), st(st_)
+{
+    count_launch();
+    if (g_prof_on.load()) {
+        cudaEventCreate(&e0);
+        cudaEventRecord(e0, st);
+    }
+}
+
+ProfScope::~ProfScope()
+{
+    if (!e0) return;
+    cudaEvent_t e1;
+    cudaEventCreate(&e1);
+    cudaEventRecord(e1, st);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.push_back({id, e0, e1});
+}
+
+}  // namespace eri
+
 using namespace eri;
+
+extern "C" int eri_profile_enable(int on)
+{
+    g_prof_on.store(on ? 1 : 0);
+    return ERI_OK;
+}
+
+extern "C" int eri_profile_read(int n, int64_t* launches, double* ms)
+{
+    if (n < 0 || n > PROF_N || (n > 0 && (!launches || !ms))) return ERI_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        launches[i] = 0;
+        ms[i] = 0.0;
+    }
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        recs.swap(g_prof_pending);
+    }
+    int rc = ERI_OK;
+    for (auto& r : recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) rc = ERI_ECUDA;
+        if (r.id >= 0 && r.id < n) {
+            launches[r.id] += 1;
+            ms[r.id] += t;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    return rc;
+}
+
+extern "C" int64_t eri_launch_count(void) { return g_launches.load(); }
 
 extern "C" const char* eri_error_string(int code)
 {

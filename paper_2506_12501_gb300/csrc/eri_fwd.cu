@@ -222,7 +222,9 @@ struct FwdArgs {
     const double* ket_E;
     const int32_t* ket_kp;
     const int64_t* quartets;  // NULL: product form
-    int64_t nq, nbra, nket;
+    int64_t nq, nbra, nket;   // nbra/nket: the caller's lists (before any swap)
+    int swap;                 // 1: the kernel's bra is the caller's ket
+    int nab_o, ncd_o;         // component-pair counts of the caller's class
     double* out;
     int TQ, KB, KK, IC;
     int e_smem, acc_regs;
@@ -237,11 +239,29 @@ struct Strided {
     __device__ __forceinline__ double& operator[](int e) const { return p[(size_t)e * s]; }
 };
 
+// Output position of the kernel's component pair (ab, cd) of quartet qq, in
+// the caller's layout (ab and cd exchange roles when the sides were swapped).
 __device__ __forceinline__ int64_t out_index(const FwdArgs& a, int64_t qq, int ab, int cd)
 {
-    if (a.quartets) return qq + a.nq * ((int64_t)ab * a.ct.ncd + cd);
+    const int abo = a.swap ? cd : ab, cdo = a.swap ? ab : cd;
+    if (a.quartets) return qq + a.nq * ((int64_t)abo * a.ncd_o + cdo);
     const int64_t bra = qq % a.nbra, ket = qq / a.nbra;
-    return bra + a.nbra * (ab + (int64_t)a.ct.nab * (cd + (int64_t)a.ct.ncd * ket));
+    return bra + a.nbra * (abo + (int64_t)a.nab_o * (cdo + (int64_t)a.ncd_o * ket));
+}
+
+// The kernel's (bra, ket) pair indices of quartet qq.
+__device__ __forceinline__ void quartet_pairs(const FwdArgs& a, int64_t qq, int* b, int* k)
+{
+    int64_t ob, ok;
+    if (a.quartets) {
+        ob = a.quartets[2 * qq];
+        ok = a.quartets[2 * qq + 1];
+    } else {
+        ob = qq % a.nbra;
+        ok = qq / a.nbra;
+    }
+    *b = (int)(a.swap ? ok : ob);
+    *k = (int)(a.swap ? ob : ok);
 }
 
 __global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
@@ -280,14 +300,7 @@ __global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
         for (int q = tid; q < TQ; q += kNT) {
             int b = 0, k = 0, kb = 0, kk = 0;
             if (q < nqt) {
-                const int64_t qq = q0 + q;
-                if (a.quartets) {
-                    b = (int)a.quartets[2 * qq];
-                    k = (int)a.quartets[2 * qq + 1];
-                } else {
-                    b = (int)(qq % a.nbra);
-                    k = (int)(qq / a.nbra);
-                }
+                quartet_pairs(a, q0 + q, &b, &k);
                 kb = a.bra_kp[b];
                 kk = a.ket_kp[k];
             }
@@ -553,12 +566,14 @@ static size_t align_up(size_t n) { return (n + 255) & ~size_t(255); }
 // On success fills the pair tables and the largest K on each centre.
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
-                  const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4])
+                  const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
+                  int allow_swap, int* swapped)
 {
     int err = ERI_OK;
     const ClassTables* ct = get_class_tables(cls.la, cls.lb, cls.lc, cls.ld, st, &err);
     if (!ct) return err;
     *ct_out = ct;
+    if (swapped) *swapped = 0;
     int* status = device_status();
     if (!status) return ERI_ECUDA;
     int32_t* hinfo = host_pinned_i32(8);
@@ -571,7 +586,10 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
                    {cls.la, cls.lb, cls.lc, cls.ld}, dinfo};
     const int64_t n = std::max(std::max(nbra, nket), quartets ? nq : (int64_t)0);
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
-    prepass_kernel<<<std::max(grid, 1), 256, 0, st>>>(pa);
+    {
+        ProfScope ps(PROF_PREPASS, st);
+        prepass_kernel<<<std::max(grid, 1), 256, 0, st>>>(pa);
+    }
     if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
     if (cudaMemcpyAsync(hinfo, dinfo, 5 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ERI_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return ERI_ECUDA;
@@ -579,6 +597,27 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
     for (int c = 0; c < 4; ++c) kmax[c] = hinfo[c];
     *KB = kmax[0] * kmax[1];
     *KK = kmax[2] * kmax[3];
+    if (allow_swap) {
+        // Transform first the side whose transform is cheaper (Section 3.2.2
+        // transforms the ket first, assuming it has the lower l): compare the
+        // FP64 work of the two orders with the sparse term counts.
+        const ClassTables* c2 = get_class_tables(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
+        if (!c2) return err;
+        const double kb = *KB, kk = *KK;
+        const double cost_n = kb * kk * ct->nhb * ct->Tcd + kb * ct->ncd * ct->Tab;
+        const double cost_s = kb * kk * c2->nhb * c2->Tcd + kk * c2->ncd * c2->Tab;
+        if (cost_s < cost_n) {
+            *swapped = 1;
+            ct = c2;
+            *ct_out = c2;
+            cls = eri_class_t{cls.lc, cls.ld, cls.la, cls.lb};
+            std::swap(bra, ket);
+            std::swap(nbra, nket);
+            std::swap(*KB, *KK);
+            std::swap(kmax[0], kmax[2]);
+            std::swap(kmax[1], kmax[3]);
+        }
+    }
     // workspace: pair tables of both sides
     const size_t nb_ps = align_up(sizeof(double) * nbra * *KB * PS_N), nb_E = align_up(sizeof(double) * nbra * *KB * ct->Tab);
     const size_t nk_ps = align_up(sizeof(double) * nket * *KK * PS_N), nk_E = align_up(sizeof(double) * nket * *KK * ct->Tcd);
@@ -632,6 +671,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         p.zz = t.zz;
         const int64_t tot = p.npairs * p.KS;
         const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
+        ProfScope ps(PROF_PAIR, st);
         pair_kernel<<<std::max(g, 1), 128, 0, st>>>(p);
         if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
     }
@@ -681,6 +721,7 @@ extern "C" int eri_boys(int mmax, const double* T, int64_t n, double* F, void* s
     const double* tab = get_boys_table(mmax, st, &err);
     if (!tab) return err;
     const int grid = (int)std::min<int64_t>((n + 127) / 128, 16 * sm_count());
+    count_launch();
     boys_kernel<<<grid, 128, 0, st>>>(mmax, T, n, tab, F);
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
 }
@@ -699,8 +740,9 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     const ClassTables* ct = nullptr;
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
+    int swapped = 0;
     err = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB, &KK,
-                        kmax);
+                        kmax, 1, &swapped);
     if (err != ERI_OK) return err;
     const double* boys = get_boys_table(ct->L, st, &err);
     if (!boys) return err;
@@ -720,8 +762,11 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     a.ket_kp = pk.kp;
     a.quartets = quartets;
     a.nq = nqq;
-    a.nbra = nbra;
+    a.nbra = nbra;  // original roles: output layout and product-form decoding
     a.nket = nket;
+    a.swap = swapped;
+    a.nab_o = swapped ? ct->ncd : ct->nab;
+    a.ncd_o = swapped ? ct->nab : ct->ncd;
     a.out = out;
     a.TQ = tp.TQ;
     a.KB = KB;
@@ -746,6 +791,9 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel, kNT, tp.bytes);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)per_sm * sm_count());
-    fwd_kernel<<<(int)grid, kNT, tp.bytes, st>>>(a);
+    {
+        ProfScope ps(PROF_FWD, st);
+        fwd_kernel<<<(int)grid, kNT, tp.bytes, st>>>(a);
+    }
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
 }

@@ -295,7 +295,7 @@ extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const i
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
     err = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 2, st, &ct, &pb, &pk, &KB, &KK,
-                        kmax);
+                        kmax, 0, nullptr);
     if (err != ERI_OK) return err;
     if (ct->L + 2 > kLtotMax) return ERI_EINVAL;
     const double* boys = get_boys_table(ct->L + 2, st, &err);
@@ -347,6 +347,9 @@ extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const i
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grad_kernel, kGT, bytes);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(nqq, (int64_t)per_sm * sm_count());
-    grad_kernel<<<(int)grid, kGT, bytes, st>>>(a);
+    {
+        ProfScope ps(PROF_GRAD, st);
+        grad_kernel<<<(int)grid, kGT, bytes, st>>>(a);
+    }
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
 }

@@ -96,11 +96,23 @@ struct PairTables {
 // contraction degree of each centre).
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
-                  const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4]);
+                  const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
+                  int allow_swap, int* swapped);
 int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                      int64_t nket, const int64_t* quartets, int64_t nq, int64_t len);
 int sm_count();
 int max_smem_optin();
+
+// Measurement hook: events around launches of kernel `id` (eri_profile_*).
+enum { PROF_FWD = 0, PROF_GRAD = 1, PROF_PAIR = 2, PROF_PREPASS = 3, PROF_N = 8 };
+struct ProfScope {
+    int id;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(int id, cudaStream_t st);
+    ~ProfScope();
+};
+void count_launch();
 
 // Device workspace (grows, cached per process; calls on one device serialise)
 void* workspace(size_t bytes, int* err);

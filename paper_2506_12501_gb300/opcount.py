@@ -1,0 +1,83 @@
+"""Operation counts of one contracted quartet (host-side bookkeeping for the
+benchmark's roofline; no integral arithmetic).
+
+``sparse_flops`` counts the FP64 floating-point operations the library's
+forward path performs (FMA = 2, MUL/ADD = 1, one square root and one
+division counted for the reciprocal square root): the MD sequence of
+Eq. md-2body with the structural zeros of the Hermite expansion coefficients
+skipped.  ``dense_flops`` is the dense-GEMM formulation of the same sequence
+(every Hermite pair of a class taken as nonzero, Boys and prefactor as a
+nominal 50), the per-quartet figure used in the measurement plan.
+"""
+from __future__ import annotations
+
+import math
+
+
+def nh(l: int) -> int:
+    return (l + 1) * (l + 2) * (l + 3) // 6
+
+
+def nc(l: int) -> int:
+    return (l + 1) * (l + 2) // 2
+
+
+def carts(l: int):
+    return [(ax, ay, l - ax - ay) for ax in range(l, -1, -1) for ay in range(l - ax, -1, -1)]
+
+
+def terms(l1: int, l2: int) -> int:
+    """number of nonzero (Cartesian pair, Hermite function) terms of E"""
+    return sum(math.prod(a[i] + b[i] + 1 for i in range(3)) for a in carts(l1) for b in carts(l2))
+
+
+def _herm(L):
+    out = []
+    for N in range(L + 1):
+        for t in range(N, -1, -1):
+            for u in range(N - t, -1, -1):
+                out.append((t, u, N - t - u))
+    return out
+
+
+def r_recursion_flops(L: int) -> int:
+    """FP64 operations of the in-place auxiliary recursion (Eq. r-rr):
+    a multiply per entry and level, plus an FMA where the coefficient
+    r_i - 1 of the chosen axis is nonzero (axis with r_i = 1 preferred)."""
+    H = _herm(L)
+    cost = []
+    for (t, u, v) in H:
+        r = (t, u, v)
+        if max(r) == 0:
+            cost.append(0)
+            continue
+        if 1 in r:
+            cost.append(1)
+        else:
+            cost.append(3)
+    total = 0
+    for n in range(L - 1, -1, -1):
+        total += sum(cost[1:nh(L - n)])
+    return total
+
+
+def prim_quartet_flops(L: int) -> int:
+    """setup (rho, T, prefactor: 15 + rsqrt counted as 2), Boys (Taylor 12,
+    exp(-T) 13, 2T 1, downward 3 per order), scaling 2 per order, recursion"""
+    return 17 + 26 + 3 * L + 2 * (L + 1) + r_recursion_flops(L)
+
+
+def sparse_flops(cls, Kbra: int, Kket: int) -> int:
+    la, lb, lc, ld = cls
+    L = la + lb + lc + ld
+    ket = 2 * nh(la + lb) * terms(lc, ld)                            # per primitive quartet
+    bra = 2 * nc(lc) * nc(ld) * terms(la, lb) + nc(la) * nc(lb) * nc(lc) * nc(ld)  # per bra primitive
+    return Kbra * Kket * (prim_quartet_flops(L) + ket) + Kbra * bra
+
+
+def dense_flops(cls, Kbra: int, Kket: int) -> int:
+    la, lb, lc, ld = cls
+    L = la + lb + lc + ld
+    ncd = nc(lc) * nc(ld)
+    per_prim = 50 + 3 * (math.comb(L + 4, 4) - (L + 1)) + 2 * nh(la + lb) * nh(lc + ld) * ncd
+    return Kbra * Kket * per_prim + Kbra * 2 * nh(la + lb) * nc(la) * nc(lb) * ncd
