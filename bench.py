@@ -47,9 +47,10 @@ def classes():
     return synth.all_classes(2)
 
 
-def sweep(seed):
+def sweep(seed, only=None, nq=NQ_PER_CLASS):
     basis, pools = synth.class_sweep_pools(seed=seed, pool=POOL, K=K_PER_SHELL)
-    batches = {c: synth.class_sweep_batch(pools, c, seed=seed, npairs=NPAIRS, nq=NQ_PER_CLASS) for c in classes()}
+    sel = classes() if only is None else [only]
+    batches = {c: synth.class_sweep_batch(pools, c, seed=seed, npairs=NPAIRS, nq=nq) for c in sel}
     return basis, batches
 
 
@@ -203,7 +204,9 @@ def run_library(args):
     dev = torch.device("cuda", local)
     eri.lib()
 
-    basis, batches = sweep(seed=rank)
+    only = tuple(int(x) for x in args.only_class) if args.only_class else None
+    basis, batches = sweep(seed=rank, only=only, nq=args.nq)
+    nq_class = args.nq
     db = eri.DeviceBasis(basis)
     dev_batches, outs = {}, {}
     for cls, (bra, ket, q) in batches.items():
@@ -259,21 +262,21 @@ def run_library(args):
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    nq_step = len(batches) * NQ_PER_CLASS
+    nq_step = len(batches) * nq_class
     value = world * nq_step * args.steps / (total_ms / 1e3)
 
     per_class = {}
     for cls in batches:
         ms = statistics.median(a.elapsed_time(b) for a, b in timing[cls])
-        qps = NQ_PER_CLASS / (ms / 1e3)
+        qps = nq_class / (ms / 1e3)
         per_class["".join(map(str, cls))] = {
             "ms": round(ms, 4), "quartets_per_s": qps,
             "gflops_sparse": sparse[cls] * qps / 1e9, "gflops_dense": dense[cls] * qps / 1e9,
             "frac_fp64_peak_sparse": sparse[cls] * qps / 1e9 / FP64_PEAK_GFLOPS,
             "frac_fp64_peak_dense": dense[cls] * qps / 1e9 / FP64_PEAK_GFLOPS}
     fwd_launches, fwd_ms = prof[eri.PROF_FWD]
-    flops_per_step = sum(sparse[c] * NQ_PER_CLASS for c in batches)
-    dense_per_step = sum(dense[c] * NQ_PER_CLASS for c in batches)
+    flops_per_step = sum(sparse[c] * nq_class for c in batches)
+    dense_per_step = sum(dense[c] * nq_class for c in batches)
     fwd_gflops = flops_per_step * args.steps / (fwd_ms / 1e3) / 1e9 if fwd_ms > 0 else None
     roofline = {"bound": "alu", "kernel": "fwd_kernel", "achieved": fwd_gflops, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "frac": (fwd_gflops / FP64_PEAK_GFLOPS) if fwd_gflops else None,
@@ -334,7 +337,8 @@ def run_library(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "classes": len(batches), "quartets_per_class": NQ_PER_CLASS,
+            "config": {"workload": WORKLOAD if only is None else f"single class {args.only_class}, {nq_class} quartets",
+                       "classes": len(batches), "quartets_per_class": nq_class,
                        "K_per_shell": K_PER_SHELL, "pairs_per_side": NPAIRS, "pool_per_l": POOL,
                        "l2": "flushed between timed steps (256 MiB write); outputs 8 GB/step also exceed L2",
                        "parallelism": f"weak x{world}: each rank its own seeded sweep"},
@@ -356,6 +360,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=18.0, help="seconds of oracle CPU work per reference step")
+    ap.add_argument("--only-class", default=None, help="profiling aid: one class, e.g. 2222")
+    ap.add_argument("--nq", type=int, default=NQ_PER_CLASS, help="quartets per class")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -9,6 +9,7 @@ the CUDA library never touches it.
 (``ld``) and ``double`` (``d``).  ``os_oracle.c`` is an independent
 Obara-Saika recursion used to pin the MD oracle on small inputs.
 """
+from . import oracle  # noqa: F401
 from .oracle import (  # noqa: F401
     build,
     lib,

@@ -55,6 +55,12 @@ typedef long double REAL;
 
 #define PI_R ((REAL)3.14159265358979323846264338327950288L)
 
+/* ORACLE_MUTANT (default 0) plants one deliberate mistake so that a test can
+ * show that the pins catch it; the oracle proper is built with 0. */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+
 /* largest total angular momentum handled (4 shells of l <= 5, plus 2 for
  * the exponent derivative) */
 #define OMAX_L 24
@@ -82,7 +88,7 @@ void ORACLE_SYM(boys)(int mmax, REAL T, REAL* F)
             REAL term = (REAL)1 / (REAL)(2 * m + 1);
             REAL sum = term;
             for (int k = 1; k < 100000; ++k) {
-                term *= (REAL)2 * T / (REAL)(2 * m + 2 * k + 1);
+                term *= (REAL)2 * T / (REAL)(2 * m + 2 * k + 1 - (ORACLE_MUTANT == 6 ? 2 : 0));
                 sum += term;
                 if (term < sum * (REAL)1e-40L) break;
             }
@@ -124,8 +130,8 @@ static void hermite_E(int la, int lb, REAL za, REAL zb, REAL Ax, REAL Bx, REAL* 
         for (int t = 0; t <= i + 1; ++t) {
             REAL v = 0;
             if (t >= 1) v += inv2p * E[EIDX(i, 0, t - 1)];
-            if (t <= i) v += PA * E[EIDX(i, 0, t)];
-            if (t + 1 <= i) v += (REAL)(t + 1) * E[EIDX(i, 0, t + 1)];
+            if (t <= i) v += (ORACLE_MUTANT == 2 ? PB : PA) * E[EIDX(i, 0, t)];
+            if (t + 1 <= i && ORACLE_MUTANT != 1) v += (REAL)(t + 1) * E[EIDX(i, 0, t + 1)];
             E[EIDX(i + 1, 0, t)] = v;
         }
     /* raise b for every a (Eq. E2rr2) */
@@ -165,11 +171,12 @@ static void build_rtable(int L, REAL p, REAL q, const REAL P[3], const REAL Q[3]
 {
     const int n = L + 1;
     const REAL rho = p * q / (p + q);
-    const REAL X[3] = {P[0] - Q[0], P[1] - Q[1], P[2] - Q[2]};
+    const REAL sgn = ORACLE_MUTANT == 4 ? (REAL)-1 : (REAL)1;
+    const REAL X[3] = {sgn * (P[0] - Q[0]), sgn * (P[1] - Q[1]), sgn * (P[2] - Q[2])};
     const REAL T = rho * (X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
     REAL F[OMAX_M + 1];
     ORACLE_SYM(boys)(L, T, F);
-    const REAL pref = (REAL)2 * RX(pow)(PI_R, (REAL)2.5) / (p * q * RX(sqrt)(p + q));
+    const REAL pref = (REAL)2 * RX(pow)(PI_R, ORACLE_MUTANT == 7 ? (REAL)2 : (REAL)2.5) / (p * q * RX(sqrt)(p + q));
     /* cube[m][t][u][v] */
     REAL* cube = (REAL*)calloc((size_t)n * n * n * n, sizeof(REAL));
 #define CI(m, t, u, v) ((((size_t)(m) * n + (t)) * n + (u)) * n + (v))
@@ -187,7 +194,7 @@ static void build_rtable(int L, REAL p, REAL q, const REAL P[3], const REAL Q[3]
                     REAL val;
                     if (t > 0) {
                         val = X[0] * cube[CI(m + 1, t - 1, u, v)];
-                        if (t > 1) val += (REAL)(t - 1) * cube[CI(m + 1, t - 2, u, v)];
+                        if (t > 1 && ORACLE_MUTANT != 3) val += (REAL)(t - 1) * cube[CI(m + 1, t - 2, u, v)];
                     } else if (u > 0) {
                         val = X[1] * cube[CI(m + 1, t, u - 1, v)];
                         if (u > 1) val += (REAL)(u - 1) * cube[CI(m + 1, t, u - 2, v)];
@@ -258,7 +265,8 @@ static REAL prim_md(const primquartet* pq, const int a[3], const int b[3], const
         int nb = a[i] + b[i] + 1, nk = c[i] + d[i] + 1;
         hermite_E(a[i], b[i], pq->za, pq->zb, pq->A[i], pq->B[i], tb);
         for (int t = 0; t < nb; ++t) Eb[i][t] = tb[(a[i] * (b[i] + 1) + b[i]) * nb + t];
-        hermite_E(c[i], d[i], pq->zc, pq->zd, pq->C[i], pq->D[i], tb);
+        hermite_E(c[i], d[i], pq->zc, pq->zd, ORACLE_MUTANT == 8 ? pq->D[i] : pq->C[i],
+                  ORACLE_MUTANT == 8 ? pq->C[i] : pq->D[i], tb);
         for (int t = 0; t < nk; ++t) Ek[i][t] = tb[(c[i] * (d[i] + 1) + d[i]) * nk + t];
     }
     REAL sum = 0;
@@ -270,7 +278,7 @@ static REAL prim_md(const primquartet* pq, const int a[3], const int b[3], const
                 for (int tau = 0; tau <= c[0] + d[0]; ++tau)
                     for (int nu = 0; nu <= c[1] + d[1]; ++nu)
                         for (int phi = 0; phi <= c[2] + d[2]; ++phi) {
-                            REAL sign = ((tau + nu + phi) & 1) ? (REAL)-1 : (REAL)1;
+                            REAL sign = (((tau + nu + phi) & 1) && ORACLE_MUTANT != 5) ? (REAL)-1 : (REAL)1;
                             inner += sign * Ek[0][tau] * Ek[1][nu] * Ek[2][phi] *
                                      pq->rt.R0[((t + tau) * n + (u + nu)) * n + (v + phi)];
                         }

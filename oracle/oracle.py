@@ -45,14 +45,38 @@ def build(force: bool = False) -> None:
         os.replace(tmp, out)
 
 
+def build_mutant(n: int, outdir: str) -> str:
+    """Compile the long-double oracle with deliberate mistake number ``n``
+    planted (ORACLE_MUTANT, see md_oracle.c) into ``outdir``; returns the
+    library path.  Used only by the test that shows the pins catch mistakes."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    out = os.path.join(outdir, f"liboracle_mutant{n}.so")
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
+                           f"-DORACLE_MUTANT={n}", *srcs, "-o", out, "-lm"])
+    return out
+
+
+def use_library(prec: str, path: str | None) -> None:
+    """Point the ``prec`` front end at another build (None: the normal one)."""
+    with _lock:
+        _libs.pop(prec, None)
+        _override[prec] = path
+
+
+_override: dict[str, str | None] = {}
+
+
 def lib(prec: str = "ld") -> ctypes.CDLL:
     """Load (building first if needed) the oracle library for ``prec`` in {'ld','d'}."""
     if prec not in ("ld", "d"):
         raise ValueError(prec)
     with _lock:
         if prec not in _libs:
-            build()
-            L = ctypes.CDLL(_lib_path(prec))
+            path = _override.get(prec)
+            if path is None:
+                build()
+                path = _lib_path(prec)
+            L = ctypes.CDLL(path)
             P = ctypes.c_void_p
             getattr(L, f"oracle_{prec}_boys_batch").argtypes = [ctypes.c_int, P, ctypes.c_long, P]
             getattr(L, f"oracle_{prec}_hermite_E").argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [P]
