@@ -138,6 +138,44 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
                    double* grad_centres, double* grad_exps, void* stream);
 
 /*
+ * eri_batch_noalloc -- the same integrals as eri_batch (FP64, list or
+ * product form, same layout and errors), for callers that may not allocate
+ * memory: the paper has no counterpart of this entry point.
+ *
+ * Who needs it: a process whose device memory belongs to another allocator
+ * (a serving or training framework's memory pool) may not call cudaMalloc
+ * itself, and code running while a stream is captured into a CUDA graph
+ * must not allocate.  eri_batch caches its scratch (the primitive-pair
+ * tables) in memory it allocates; this entry point instead keeps that
+ * scratch in a fixed device array of ERI_NOALLOC_SCRATCH_BYTES, compiled
+ * into the library, and its constant tables in fixed arrays as well.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * - The fixed arrays take ERI_NOALLOC_SCRATCH_BYTES (+ about 2.6 MB of
+ *   tables) on every GPU that loads the library, until the process exits.
+ * - A batch needs 8*(nbra*KB*(T_ab+5) + nket*KK*(T_cd+5)) bytes of scratch
+ *   plus small padding (KB = largest K_a*K_b, T_ab = nonzero Hermite terms
+ *   of the class); a larger batch is rejected with ERI_EINVAL before any
+ *   integral kernel runs.  Split such batches.
+ * - The first call on a device sets that device up (the device must be
+ *   current): it fills the constant tables with synchronous copies and
+ *   looks up the arrays' device addresses.  Make that first call before
+ *   any stream capture begins.
+ * - Every call uses the same arrays, which keep the last call's contents;
+ *   the call clears what must start at zero.  Calls whose GPU work overlaps
+ *   in time (different streams, or several host threads) race on them:
+ *   serialise them.
+ * - Like eri_batch, each call synchronises `stream` once (validation).
+ * - precision is always FP64; the sides are never swapped.
+ */
+#define ERI_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int eri_batch_noalloc(eri_class_t cls, const eri_basis_t* basis,
+                      const int32_t* bra_pairs, int64_t nbra,
+                      const int32_t* ket_pairs, int64_t nket,
+                      const int64_t* quartets, int64_t nq,
+                      double* out, int64_t out_len, void* stream);
+
+/*
  * eri_last_status -- synchronises `stream` and returns ERI_OK or the first
  * error a kernel recorded since the previous call (then clears it).
  */

@@ -12,6 +12,8 @@ from .binding import (  # noqa: F401
     eri_boys,
     eri_batch,
     eri_batch_grad,
+    eri_batch_noalloc,
+    ERI_NOALLOC_SCRATCH_BYTES,
     eri_last_status,
     eri_finalize,
     eri_profile_enable,

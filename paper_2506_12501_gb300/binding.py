@@ -41,7 +41,8 @@ class eri_basis_t(ctypes.Structure):
 
 
 EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
-           "eri_profile_enable", "eri_profile_read", "eri_launch_count"]
+           "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc"]
+ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS = 0, 1, 2, 3
 
 
@@ -61,6 +62,9 @@ def lib() -> ctypes.CDLL:
             L.eri_error_string.argtypes = [I]
             L.eri_error_string.restype = ctypes.c_char_p
             L.eri_finalize.argtypes = []
+            L.eri_batch_noalloc.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P,
+                                            I64, P]
+            L.eri_batch_noalloc.restype = I
             L.eri_profile_enable.argtypes = [I]
             L.eri_profile_enable.restype = I
             L.eri_profile_read.argtypes = [I, P, P]
@@ -198,3 +202,20 @@ def eri_profile_read() -> dict:
 
 def eri_launch_count() -> int:
     return int(lib().eri_launch_count())
+
+
+def eri_batch_noalloc(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pairs: torch.Tensor,
+                      quartets: torch.Tensor | None, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """The allocation-free variant of eri_batch (FP64): the caller passes the
+    output tensor, and the library uses only its fixed, compiled-in scratch
+    (see include/eri.h).  Nothing is allocated by this call."""
+    nbra, nket = bra_pairs.shape[0], ket_pairs.shape[0]
+    nq = quartets.shape[0] if quartets is not None else None
+    if out_len(cls, nbra, nket, nq) == 0:
+        return out
+    b = basis.struct()
+    code = lib().eri_batch_noalloc(eri_class_t(*cls), ctypes.byref(b), _ptr(bra_pairs), nbra, _ptr(ket_pairs), nket,
+                                   _ptr(quartets), nq if nq is not None else 0, _ptr(out), out.numel(),
+                                   _stream(stream))
+    _check(code, "eri_batch_noalloc")
+    return out

@@ -797,3 +797,118 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     }
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
 }
+
+namespace eri {
+
+// ---------------------------------------------------------------------------
+// The forward batch on tables and scratch the caller supplies (no allocation,
+// no swap of the sides): used by the allocation-free entry point.  `dinfo`
+// is 5 device ints, `scratch` holds the pair tables of both sides.
+// ---------------------------------------------------------------------------
+int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
+                 int64_t nket, const int64_t* quartets, int64_t nq, double* out, const ClassTables& ct,
+                 const double* boys, const RStep* rs, int* dinfo, double* scratch, size_t scratch_doubles,
+                 cudaStream_t st)
+{
+    if (cudaMemsetAsync(dinfo, 0, 5 * sizeof(int), st) != cudaSuccess) return ERI_ECUDA;
+    PrepassArgs pa{basis->shell_l, basis->shell_K, basis->nshell, bra, nbra, ket, nket, quartets,
+                   quartets ? nq : (int64_t)0, {cls.la, cls.lb, cls.lc, cls.ld}, dinfo};
+    const int64_t n = std::max(std::max(nbra, nket), quartets ? nq : (int64_t)0);
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
+    count_launch();
+    prepass_kernel<<<std::max(grid, 1), 256, 0, st>>>(pa);
+    if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+    int hinfo[5] = {0, 0, 0, 0, 0};
+    if (cudaMemcpyAsync(hinfo, dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ERI_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ERI_ECUDA;
+    if (hinfo[4] != 0) return dev_err_to_code(hinfo[4]);
+    const int KB = hinfo[0] * hinfo[1], KK = hinfo[2] * hinfo[3];
+    // carve the scratch: [ps_b | E_b | ps_k | E_k | kp_b | kp_k], 32-double aligned pieces
+    auto up = [](size_t d) { return (d + 31) & ~size_t(31); };
+    const size_t n_psb = up((size_t)nbra * KB * PS_N), n_Eb = up((size_t)nbra * KB * ct.Tab);
+    const size_t n_psk = up((size_t)nket * KK * PS_N), n_Ek = up((size_t)nket * KK * ct.Tcd);
+    const size_t n_kpb = up(((size_t)nbra + 1) / 2), n_kpk = up(((size_t)nket + 1) / 2);
+    if (n_psb + n_Eb + n_psk + n_Ek + n_kpb + n_kpk > scratch_doubles) return ERI_EINVAL;
+    PairTables pb{}, pk{};
+    pb.ps = scratch;
+    pb.E = pb.ps + n_psb;
+    pk.ps = pb.E + n_Eb;
+    pk.E = pk.ps + n_psk;
+    pb.kp = reinterpret_cast<int32_t*>(pk.E + n_Ek);
+    pk.kp = reinterpret_cast<int32_t*>(pk.E + n_Ek + n_kpb);
+    for (int side = 0; side < 2; ++side) {
+        PairArgs p{};
+        p.centres = basis->centres;
+        p.shell_atom = basis->shell_atom;
+        p.shell_K = basis->shell_K;
+        p.shell_off = basis->shell_off;
+        p.exps = basis->exps;
+        p.coefs = basis->coefs;
+        p.pairs = side ? ket : bra;
+        p.npairs = side ? nket : nbra;
+        p.l1 = side ? cls.lc : cls.la;
+        p.l2 = side ? cls.ld : cls.lb;
+        p.KS = side ? KK : KB;
+        p.T = side ? ct.Tcd : ct.Tab;
+        p.fac = side ? ct.ket_fac : ct.bra_fac;
+        p.ket = side;
+        const PairTables& t = side ? pk : pb;
+        p.ps = t.ps;
+        p.E = t.E;
+        p.kprim = t.kp;
+        const int64_t tot = p.npairs * p.KS;
+        const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
+        count_launch();
+        pair_kernel<<<std::max(g, 1), 128, 0, st>>>(p);
+        if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+    }
+    const int64_t nqq = quartets ? nq : nbra * nket;
+    TilePlan tp;
+    if (!plan_tiles(ct, KB, KK, nqq, &tp)) return ERI_EINVAL;
+    FwdArgs a{};
+    a.ct = ct;
+    a.boys = boys;
+    a.rsteps = rs;
+    a.bra_ps = pb.ps;
+    a.bra_E = pb.E;
+    a.bra_kp = pb.kp;
+    a.ket_ps = pk.ps;
+    a.ket_E = pk.E;
+    a.ket_kp = pk.kp;
+    a.quartets = quartets;
+    a.nq = nqq;
+    a.nbra = nbra;
+    a.nket = nket;
+    a.swap = 0;
+    a.nab_o = ct.nab;
+    a.ncd_o = ct.ncd;
+    a.out = out;
+    a.TQ = tp.TQ;
+    a.KB = KB;
+    a.KK = KK;
+    a.IC = tp.IC;
+    a.e_smem = tp.e_smem;
+    a.acc_regs = tp.acc_regs;
+    a.sEbS = tp.sEbS;
+    a.sEkS = tp.sEkS;
+    a.o_Eb = tp.o_Eb;
+    a.o_Ek = tp.o_Ek;
+    a.o_Pb = tp.o_Pb;
+    a.o_Pk = tp.o_Pk;
+    a.o_R = tp.o_R;
+    a.o_X = tp.o_X;
+    a.o_tab = tp.o_tab;
+    a.o_q = tp.o_q;
+    a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
+    if (cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
+        return ERI_ECUDA;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel, kNT, tp.bytes);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid2 = std::min<int64_t>(a.ntiles, (int64_t)per_sm * sm_count());
+    count_launch();
+    fwd_kernel<<<(int)grid2, kNT, tp.bytes, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
+}
+
+}  // namespace eri

@@ -98,6 +98,10 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
                   int allow_swap, int* swapped);
+int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
+                 int64_t nket, const int64_t* quartets, int64_t nq, double* out, const ClassTables& ct,
+                 const double* boys, const RStep* rs, int* dinfo, double* scratch, size_t scratch_doubles,
+                 cudaStream_t st);
 int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                      int64_t nket, const int64_t* quartets, int64_t nq, int64_t len);
 int sm_count();
