@@ -188,6 +188,19 @@ def profile_traffic():
     return float(t.group(1))
 
 
+def reduce_max(value, dist, device):
+    """Max over ranks of a per-rank float (the slowest rank sets the job time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, quartets_per_rank_step, steps, max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * quartets_per_rank_step * steps / (max_ms / 1e3)
+
+
 def run_library(args):
     import torch
     import torch.distributed as dist
@@ -259,11 +272,9 @@ def run_library(args):
     step_ms = [a.elapsed_time(b) for a, b in step_events]
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max(total_ms, dist, dev)
     nq_step = len(batches) * nq_class
-    value = world * nq_step * args.steps / (total_ms / 1e3)
+    value = job_rate(world, nq_step, args.steps, total_ms)
 
     per_class = {}
     for cls in batches:

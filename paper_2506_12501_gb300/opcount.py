@@ -67,7 +67,20 @@ def prim_quartet_flops(L: int) -> int:
     return 17 + 26 + 3 * L + 2 * (L + 1) + r_recursion_flops(L)
 
 
-def sparse_flops(cls, Kbra: int, Kket: int) -> int:
+def swapped(cls, Kbra: int, Kket: int) -> bool:
+    """The library's choice of transform order: the sides are swapped when the
+    swapped order needs fewer operations in the two transforms."""
+    la, lb, lc, ld = cls
+    n = Kbra * Kket * nh(la + lb) * terms(lc, ld) + Kbra * nc(lc) * nc(ld) * terms(la, lb)
+    s = Kbra * Kket * nh(lc + ld) * terms(la, lb) + Kket * nc(la) * nc(lb) * terms(lc, ld)
+    return s < n
+
+
+def sparse_flops(cls, Kbra: int, Kket: int, orient: str = "auto") -> int:
+    """orient: 'auto' (the library's choice), 'as-is' (ket transformed first)."""
+    if orient == "auto" and swapped(cls, Kbra, Kket):
+        cls = (cls[2], cls[3], cls[0], cls[1])
+        Kbra, Kket = Kket, Kbra
     la, lb, lc, ld = cls
     L = la + lb + lc + ld
     ket = 2 * nh(la + lb) * terms(lc, ld)                            # per primitive quartet
