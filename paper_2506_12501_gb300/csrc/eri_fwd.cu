@@ -27,7 +27,7 @@
 
 namespace eri {
 
-constexpr int kNT = 128;   // threads per CTA of fwd_kernel
+constexpr int kNT = 256;   // threads per CTA of fwd_kernel
 constexpr int kNACC = 16;  // outputs per thread held in registers
 
 // ---------------------------------------------------------------------------
@@ -97,16 +97,40 @@ struct PairArgs {
     const uint8_t* fac;     // [T][3] per-axis E-table indices
     int ket;                // 1: ket side (sign (-1)^{l_q}, scale 1/zeta_q)
     double* ps;             // [npairs][KS][PS_N]
-    double* E;              // [npairs][KS][T]
+    double* E;              // [npairs][T][KS] (slot fastest)
     int32_t* kprim;         // [npairs] number of valid slots K1*K2
     // adjoint only (ax == nullptr otherwise): per-axis tables with both
     // indices raised by up to 2, ax[(g*3 + axis)*eax + (i*(l2+3) + j)*(l1+l2+5) + t]
     double* ax;
     int eax;
     double* zz;             // [npairs][KS][2]: the two exponents
+    int split;              // 1: E products stored as float pairs (hi, lo) in the double slots
 };
 
 constexpr int kEax = (kLmax + 3) * (kLmax + 3) * (2 * kLmax + 5);  // per-axis E table bound (adjoint shifts)
+
+// ---- split precision: a double x is carried as hi + lo with hi = fl32(x),
+// lo = fl32(x - hi) (about 48 significant bits); products of two such pairs
+// keep the exact error of hi*hi (from an FMA) and the two cross terms, and
+// sums are compensated (TwoSum), so a long sum keeps about 44 bits.  The
+// rounded intrinsics keep the compiler from contracting the error terms.
+__device__ __forceinline__ float2 split_f64(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// (S, c) += a * b with a, b split pairs
+__device__ __forceinline__ void ff_mac(float2 a, float2 b, float& S, float& c)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    const float pe = __fmaf_rn(a.x, b.x, -p);
+    const float t = __fadd_rn(S, p);
+    const float z = __fsub_rn(t, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, z)), __fsub_rn(p, z));
+    S = t;
+    c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, pe))));
+}
 
 __global__ void pair_kernel(PairArgs a)
 {
@@ -118,7 +142,7 @@ __global__ void pair_kernel(PairArgs a)
         const int K1 = a.shell_K[s1], K2 = a.shell_K[s2];
         if (s == 0) a.kprim[j] = K1 * K2;
         if (s >= K1 * K2) {  // padding slot: finite zeros, never contributes
-            for (int t = 0; t < a.T; ++t) a.E[(size_t)g * a.T + t] = 0.0;
+            for (int t = 0; t < a.T; ++t) a.E[((size_t)j * a.T + t) * a.KS + s] = 0.0;
             double* o = a.ps + (size_t)g * PS_N;
             o[PS_P] = 1.0;
             o[PS_PX] = o[PS_PY] = o[PS_PZ] = 0.0;
@@ -177,7 +201,7 @@ __global__ void pair_kernel(PairArgs a)
                         Ex[(i * n2 + jj + 1) * nt + t] = v;
                     }
         }
-        double* Eout = a.E + (size_t)g * a.T;
+        double* Eout = a.E + (size_t)j * a.T * a.KS + s;  // term t at Eout[t * KS]
         const int ntc = L12 + 1, n2c = a.l2 + 1;  // dims the class-table indices use
         for (int t = 0; t < a.T; ++t) {
             int idx[3], lq = 0;
@@ -189,7 +213,10 @@ __global__ void pair_kernel(PairArgs a)
             }
             double v = E[0][idx[0]] * E[1][idx[1]] * E[2][idx[2]];
             if (a.ket && (lq & 1)) v = -v;
-            Eout[t] = v;
+            if (a.split)
+                reinterpret_cast<float2*>(Eout)[(size_t)t * a.KS] = split_f64(v);
+            else
+                Eout[(size_t)t * a.KS] = v;
         }
         if (a.ax) {
             for (int x = 0; x < 3; ++x) {
@@ -264,7 +291,33 @@ __device__ __forceinline__ void quartet_pairs(const FwdArgs& a, int64_t qq, int*
     *k = (int)(a.swap ? ob : ok);
 }
 
-__global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
+// Stage C inner sum: sum_{u in [u0,u1)} E^ab_u X[p_u][cd] of one quartet and
+// one bra primitive (E term u at Eb[u * KB]).  Two alternating chains; the
+// split form returns its compensated float sum as a double (2 FP64 ops).
+template <bool SPLIT>
+__device__ __forceinline__ double bra_sum(const double* Eb, int KB, const double* sX, int u0, int u1,
+                                          const int16_t* s_bp, int ncd, int cd, int TQ, int q)
+{
+    if (!SPLIT) {
+        double va = 0.0, vb = 0.0;
+        int u = u0;
+        for (; u + 1 < u1; u += 2) {
+            va = fma(Eb[(size_t)u * KB], sX[(s_bp[u] * ncd + cd) * TQ + q], va);
+            vb = fma(Eb[(size_t)(u + 1) * KB], sX[(s_bp[u + 1] * ncd + cd) * TQ + q], vb);
+        }
+        if (u < u1) va = fma(Eb[(size_t)u * KB], sX[(s_bp[u] * ncd + cd) * TQ + q], va);
+        return va + vb;
+    } else {
+        const float2* E2 = reinterpret_cast<const float2*>(Eb);
+        const float2* X2 = reinterpret_cast<const float2*>(sX);
+        float S = 0.f, c = 0.f;
+        for (int u = u0; u < u1; ++u) ff_mac(E2[(size_t)u * KB], X2[(s_bp[u] * ncd + cd) * TQ + q], S, c);
+        return (double)S + (double)c;
+    }
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kNT) fwd_kernel_t(FwdArgs a)
 {
     extern __shared__ __align__(16) double sm[];
     const ClassTables& ct = a.ct;
@@ -322,11 +375,11 @@ __global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
         if (a.e_smem) {
             const int nb = KB * ct.Tab, nk = KK * ct.Tcd;
             for (int idx = tid; idx < TQ * nb; idx += kNT) {
-                const int q = idx / nb, r = idx - q * nb, i = r / ct.Tab;
+                const int q = idx / nb, r = idx - q * nb, i = r % KB;
                 sEb[q * a.sEbS + r] = i < s_q[4 * q + 2] ? a.bra_E[(size_t)s_q[4 * q] * nb + r] : 0.0;
             }
             for (int idx = tid; idx < TQ * nk; idx += kNT) {
-                const int q = idx / nk, r = idx - q * nk, k = r / ct.Tcd;
+                const int q = idx / nk, r = idx - q * nk, k = r % KK;
                 sEk[q * a.sEkS + r] = k < s_q[4 * q + 3] ? a.ket_E[(size_t)s_q[4 * q + 1] * nk + r] : 0.0;
             }
         }
@@ -360,6 +413,12 @@ __global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
                         f *= m2rho;
                     }
                     r_recursion(ct.L, base, X, Y, Z, a.rsteps, R);
+                    if (SPLIT)  // each entry becomes its (hi, lo) float pair, in place
+                        for (int e = 0; e < nhl; ++e) {
+                            double& slot = R[e];
+                            const float2 f = split_f64(slot);
+                            reinterpret_cast<float2&>(slot) = f;
+                        }
                 } else {
                     for (int e = 0; e < nhl; ++e) R[e] = 0.0;
                 }
@@ -372,16 +431,47 @@ __global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
                 for (int item = tid; item < nB; item += kNT) {
                     const int q = item % TQ, r = item / TQ, p = r % nhb, cd = r / nhb;
                     const double* Ek = a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd;
-                    const double* Rc = sR + (q * IC + ii) * KK;
+                    const double* Rc = sR + (q * IC + ii) * KK;  // + e * NI + k
                     const int16_t* pqrow = s_pq + p * nhk;
                     const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
-                    double v = 0.0;
-                    for (int k = 0; k < KK; ++k) {
-                        const double* Ekk = Ek + k * ct.Tcd;
-                        const double* Rk = Rc + k;
-                        for (int t = t0; t < t1; ++t) v = fma(Ekk[t], Rk[(size_t)pqrow[s_kq[t]] * NI], v);
+                    // terms outer, ket primitives inner: one p+q lookup per term
+                    // serves all KK primitives (E is stored slot-fastest); two
+                    // accumulator chains alternate to hide the DFMA latency
+                    if (!SPLIT) {
+                        double va = 0.0, vb = 0.0;
+                        for (int t = t0; t < t1; ++t) {
+                            const double* Rk = Rc + (size_t)pqrow[s_kq[t]] * NI;
+                            const double* Et = Ek + t * KK;
+                            int k = 0;
+                            for (; k + 1 < KK; k += 2) {
+                                va = fma(Et[k], Rk[k], va);
+                                vb = fma(Et[k + 1], Rk[k + 1], vb);
+                            }
+                            if (k < KK) {
+                                const double w = fma(Et[k], Rk[k], va);
+                                va = vb;
+                                vb = w;
+                            }
+                        }
+                        sX[(p * ncd + cd) * TQ + q] = va + vb;
+                    } else {
+                        float Sa = 0.f, ca = 0.f, Sb = 0.f, cb = 0.f;
+                        for (int t = t0; t < t1; ++t) {
+                            const float2* Rk = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NI);
+                            const float2* Et = reinterpret_cast<const float2*>(Ek + t * KK);
+                            int k = 0;
+                            for (; k + 1 < KK; k += 2) {
+                                ff_mac(Et[k], Rk[k], Sa, ca);
+                                ff_mac(Et[k + 1], Rk[k + 1], Sb, cb);
+                            }
+                            if (k < KK) ff_mac(Et[k], Rk[k], Sa, ca);
+                        }
+                        // (Sa + Sb, ca + cb) as one split pair (error-free sum of the highs)
+                        const float t2 = __fadd_rn(Sa, Sb), z = __fsub_rn(t2, Sa);
+                        const float err = __fadd_rn(__fsub_rn(Sa, __fsub_rn(t2, z)), __fsub_rn(Sb, z));
+                        reinterpret_cast<float2*>(sX)[(p * ncd + cd) * TQ + q] =
+                            make_float2(t2, __fadd_rn(__fadd_rn(ca, cb), err));
                     }
-                    sX[(p * ncd + cd) * TQ + q] = v;
                 }
                 __syncthreads();
                 // ---- C: bra transform + bra contraction
@@ -394,11 +484,7 @@ __global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
                             const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
                             const double* Eb = a.e_smem ? sEb + q * a.sEbS
                                                         : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab;
-                            Eb += i * ct.Tab;
-                            double v = 0.0;
-                            for (int u = s_bstart[ab]; u < s_bstart[ab + 1]; ++u)
-                                v = fma(Eb[u], sX[(s_bp[u] * ncd + cd) * TQ + q], v);
-                            acc[s] += v;
+                            acc[s] += bra_sum<SPLIT>(Eb + i, KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
                         }
                     }
                 } else {
@@ -406,10 +492,8 @@ __global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
                         const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
                         if (q >= nqt) continue;
                         const double* Eb = a.e_smem ? sEb + q * a.sEbS : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab;
-                        Eb += i * ct.Tab;
-                        double v = 0.0;
-                        for (int u = s_bstart[ab]; u < s_bstart[ab + 1]; ++u)
-                            v = fma(Eb[u], sX[(s_bp[u] * ncd + cd) * TQ + q], v);
+                        const double v =
+                            bra_sum<SPLIT>(Eb + i, KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
                         const int64_t o = out_index(a, q0 + q, ab, cd);
                         a.out[o] = (i == 0) ? v : a.out[o] + v;
                     }
@@ -430,6 +514,9 @@ __global__ void __launch_bounds__(kNT) fwd_kernel(FwdArgs a)
         }
     }
 }
+
+static const auto fwd_kernel = fwd_kernel_t<false>;
+static const auto fwd_kernel_split = fwd_kernel_t<true>;
 
 // ---------------------------------------------------------------------------
 // Boys entry kernel
@@ -567,7 +654,7 @@ static size_t align_up(size_t n) { return (n + 255) & ~size_t(255); }
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
-                  int allow_swap, int* swapped)
+                  int allow_swap, int* swapped, int split)
 {
     int err = ERI_OK;
     const ClassTables* ct = get_class_tables(cls.la, cls.lb, cls.lc, cls.ld, st, &err);
@@ -669,6 +756,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         p.ax = t.ax;
         p.eax = t.eax;
         p.zz = t.zz;
+        p.split = split;
         const int64_t tot = p.npairs * p.KS;
         const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
         ProfScope ps(PROF_PAIR, st);
@@ -741,8 +829,9 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
     int swapped = 0;
+    const int split = precision == ERI_PREC_SPLIT;
     err = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB, &KK,
-                        kmax, 1, &swapped);
+                        kmax, 1, &swapped, split);
     if (err != ERI_OK) return err;
     const double* boys = get_boys_table(ct->L, st, &err);
     if (!boys) return err;
@@ -785,15 +874,16 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     a.o_tab = tp.o_tab;
     a.o_q = tp.o_q;
     a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
-    if (cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
+    void (*kern)(FwdArgs) = split ? fwd_kernel_split : fwd_kernel;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
         return ERI_ECUDA;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel, kNT, tp.bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, tp.bytes);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)per_sm * sm_count());
     {
         ProfScope ps(PROF_FWD, st);
-        fwd_kernel<<<(int)grid, kNT, tp.bytes, st>>>(a);
+        kern<<<(int)grid, kNT, tp.bytes, st>>>(a);
     }
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
 }

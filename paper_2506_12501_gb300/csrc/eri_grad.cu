@@ -174,14 +174,12 @@ __global__ void __launch_bounds__(kGT) grad_kernel(GradArgs a)
                 for (int h = 0; h < nhO; ++h) Vrow[h] = 0.0;
                 for (int co = 0; co < nO; ++co) {
                     const double w = pass == 0 ? sW[cs * ncd + co] : sW[co * ncd + cs];
-                    if (pass == 0) {
-                        const double* Ek = sEk + ko * ct.Tcd;
+                    if (pass == 0) {  // E stored term-major, primitive slot fastest
                         for (int t = ct.ket_start[co]; t < ct.ket_start[co + 1]; ++t)
-                            Vrow[ct.ket_q[t]] = fma(w, Ek[t], Vrow[ct.ket_q[t]]);
+                            Vrow[ct.ket_q[t]] = fma(w, sEk[t * KK + ko], Vrow[ct.ket_q[t]]);
                     } else {
-                        const double* Eb = sEb + ko * ct.Tab;
                         for (int t = ct.bra_start[co]; t < ct.bra_start[co + 1]; ++t)
-                            Vrow[ct.bra_p[t]] = fma(w, Eb[t], Vrow[ct.bra_p[t]]);
+                            Vrow[ct.bra_p[t]] = fma(w, sEb[t * KB + ko], Vrow[ct.bra_p[t]]);
                     }
                 }
             }

@@ -84,7 +84,7 @@ void herm_tuv(int idx, int* t, int* u, int* v);
 // Primitive-pair tables of one side of a batch (inside the workspace).
 struct PairTables {
     double* ps;   // [npairs][KS][PS_N]
-    double* E;    // [npairs][KS][T] E^x E^y E^z products (ket: times (-1)^{l_q})
+    double* E;    // [npairs][T][KS] E^x E^y E^z products, slot fastest (ket: times (-1)^{l_q})
     int32_t* kp;  // [npairs] number of primitive pairs
     double* ax;   // adjoint only: per-axis E tables with raised indices
     int eax;      // doubles per axis table
@@ -97,7 +97,7 @@ struct PairTables {
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
-                  int allow_swap, int* swapped);
+                  int allow_swap, int* swapped, int split = 0);
 int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                  int64_t nket, const int64_t* quartets, int64_t nq, double* out, const ClassTables& ct,
                  const double* boys, const RStep* rs, int* dinfo, double* scratch, size_t scratch_doubles,

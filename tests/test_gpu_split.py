@@ -1,0 +1,61 @@
+"""f-shell classes in FP64 and the split-precision (FP32 hi+lo transforms,
+FP64 Boys/R/accumulation) form, against the oracle and against the FP64
+path at the 1e-10 absolute bar of the measurement plan."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_2506_12501_gb300 as eri
+from gpu_helpers import assert_close, gpu_list, oracle_blocks
+
+pytestmark = pytest.mark.gpu
+
+F_CLASSES = [(3, 0, 0, 0), (3, 1, 2, 0), (2, 3, 1, 3), (3, 3, 1, 1), (3, 2, 3, 2), (3, 3, 2, 2), (3, 3, 3, 3)]
+
+
+@pytest.mark.parametrize("cls", F_CLASSES)
+def test_f_classes_fp64_against_oracle(cuda, cls):
+    """Exponents log-uniform in [0.05, 50] (the high-l workload), K = 1 and 2."""
+    L = sum(cls)
+    K = 1 if L >= 10 else 2
+    nq = 12 if L >= 10 else 40
+    basis, bra, ket, q = synth.split_batch(cls, K=K, seed=L, nq=nq, pool=16, npairs=8)
+    got = gpu_list(cls, basis, bra, ket, q)
+    ref = oracle_blocks(cls, basis, bra, ket, q, prec="d")
+    assert_close(got, ref, what=f"fp64 {cls}")
+
+
+@pytest.mark.parametrize("cls,K,nq", [((2, 2, 2, 2), 1, 2000), ((3, 3, 3, 3), 1, 300), ((3, 3, 2, 2), 1, 1000),
+                                      ((2, 2, 2, 2), 5, 60), ((3, 3, 3, 3), 5, 8), ((3, 3, 2, 2), 5, 20)])
+def test_split_against_fp64_path(cuda, cls, K, nq):
+    """The split-precision form stays within 1e-10 absolute of the FP64 form on
+    the high-l workload (K = 1 and K = 5 per shell)."""
+    basis, bra, ket, q = synth.split_batch(cls, K=K, seed=100 + K, nq=nq, pool=64, npairs=48)
+    f64 = gpu_list(cls, basis, bra, ket, q)
+    spl = gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT)
+    err = np.abs(spl - f64)
+    print(f"split {cls} K={K}: max |split - fp64| = {err.max():.3e}, max |fp64| = {np.abs(f64).max():.3e}")
+    assert_close(spl, f64, atol=1e-10, rtol=0.0, what=f"split {cls} K={K}")
+
+
+@pytest.mark.parametrize("cls,K,nq", [((2, 2, 2, 2), 1, 16), ((3, 3, 2, 2), 1, 16), ((3, 3, 3, 3), 1, 8),
+                                      ((3, 3, 2, 2), 5, 2)])
+def test_fp64_and_split_against_oracle(cuda, cls, K, nq):
+    """Both forms against the oracle on the high-l workload, K = 5 included."""
+    basis, bra, ket, q = synth.split_batch(cls, K=K, seed=7, nq=nq, pool=16, npairs=8)
+    ref = oracle_blocks(cls, basis, bra, ket, q, prec="d")
+    f64 = gpu_list(cls, basis, bra, ket, q)
+    assert_close(f64, ref, what=f"fp64 vs oracle {cls} K={K}")
+    spl = gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT)
+    assert_close(spl, ref, atol=1e-10, rtol=1e-10, what=f"split vs oracle {cls} K={K}")
+
+
+@pytest.mark.parametrize("cls", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 1, 0, 2), (2, 2, 1, 1)])
+def test_split_low_l_contracted(cuda, cls):
+    """The class-sweep inputs (K = 3) in split precision."""
+    basis, pools = synth.class_sweep_pools(seed=4, pool=64, K=3)
+    bra, ket, q = synth.class_sweep_batch(pools, cls, seed=4, npairs=100, nq=500)
+    f64 = gpu_list(cls, basis, bra, ket, q)
+    spl = gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT)
+    assert_close(spl, f64, atol=1e-10, rtol=0.0, what=f"split sweep {cls}")
