@@ -201,6 +201,92 @@ def job_rate(world, quartets_per_rank_step, steps, max_ms):
     return world * quartets_per_rank_step * steps / (max_ms / 1e3)
 
 
+def run_variants(args, eri, dev):
+    """The split-precision, adjoint and batched forms, each timed against the
+    plain FP64 per-class kernels on the same GPU (bounded sizes; see config)."""
+    import torch
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    out = {}
+    # split precision on the high-l workload
+    split = {}
+    for cls in [(2, 2, 2, 2), (3, 3, 3, 3), (3, 3, 2, 2)]:
+        for K, nq in ((1, 100_000), (5, args.split_nq_k5)):
+            basis, bra, ket, q = synth.split_batch(cls, K=K, seed=0, nq=nq)
+            db = eri.DeviceBasis(basis)
+            b = torch.as_tensor(bra, device=dev)
+            k = torch.as_tensor(ket, device=dev)
+            qq = torch.as_tensor(q, device=dev)
+            o64 = torch.empty(eri.out_len(cls, len(bra), len(ket), nq), dtype=torch.float64, device=dev)
+            osp = torch.empty_like(o64)
+            t64 = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o64))
+            tsp = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=osp, precision=eri.ERI_PREC_SPLIT))
+            err = float((osp - o64).abs().max())
+            split["".join(map(str, cls)) + f"_K{K}"] = {
+                "quartets": nq, "fp64_ms": t64, "split_ms": tsp, "speedup": t64 / tsp,
+                "fp64_quartets_per_s": nq / (t64 / 1e3), "split_quartets_per_s": nq / (tsp / 1e3),
+                "max_abs_err_vs_fp64": err, "max_abs_fp64": float(o64.abs().max())}
+            del o64, osp
+    out["split"] = split
+    # adjoint: the 16-atom molecule-shaped basis, a sample of every class
+    basis, D, bf_off = synth.adjoint_workload(natom=16, radius=4.4, seed=0)
+    pairs, batches = synth.all_unique_quartets(basis)
+    db = eri.DeviceBasis(basis)
+    tf = tg = 0.0
+    nq_tot = 0
+    for cls, (bra, ket, q) in batches.items():
+        q = q[: args.adjoint_nq]
+        W = synth.density_weights(cls, bra, ket, q, D, bf_off)
+        b = torch.as_tensor(bra, device=dev)
+        k = torch.as_tensor(ket, device=dev)
+        qq = torch.as_tensor(q, device=dev)
+        Wd = torch.as_tensor(W, device=dev)
+        o = torch.empty(W.size, dtype=torch.float64, device=dev)
+        gc = torch.zeros_like(db.centres)
+        ge = torch.zeros_like(db.exps)
+        tf += timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o), reps=1)
+        tg += timed(lambda: eri.eri_batch_grad(cls, db, b, k, qq, Wd, gc, ge), reps=1)
+        nq_tot += len(q)
+    out["adjoint"] = {"workload": f"16-atom molecule basis, {len(batches)} classes, <= {args.adjoint_nq} "
+                                  "quartets per class", "quartets": nq_tot, "fwd_ms": tf, "grad_ms": tg,
+                      "grad_over_fwd": tg / tf, "grad_quartets_per_s": nq_tot / (tg / 1e3)}
+    # batched: the screened molecule-shaped workload in one persistent graph launch
+    mb = synth.molecule_basis(natom=args.molecule_natom, radius=7.0 * (args.molecule_natom / 64) ** (1 / 3), seed=0)
+    mdb = eri.DeviceBasis(mb)
+    nbf = int(((mb.shell_l + 1) * (mb.shell_l + 2) // 2).sum())
+    rng = np.random.default_rng(2)
+    U = rng.uniform(-1, 1, (nbf, nbf))
+    Dm = torch.as_tensor(np.triu(U) + np.triu(U, 1).T, device=dev)
+    t0 = time.perf_counter()
+    plan = eri.Plan(mdb, threshold=1e-12)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    info = plan.info()
+    e = torch.zeros(1, dtype=torch.float64, device=dev)
+    t_exec = timed(lambda: plan.execute(D=Dm, energy=e), reps=2)
+    out["batched"] = {"workload": f"{args.molecule_natom} atoms (s x3 K=6,3,1, p x2 K=3,1, d K=1), Schwarz 1e-12, "
+                                  "energy digestion, one persistent graph-captured launch",
+                      "quartets": info["nquartets"], "jobs": info["njobs"], "work_items": info["nitems"],
+                      "create_s": t_create, "execute_ms": t_exec,
+                      "quartets_per_s": info["nquartets"] / (t_exec / 1e3), "energy": float(e.item()),
+                      "status": plan.status()}
+    plan.destroy()
+    return out
+
+
 def run_library(args):
     import torch
     import torch.distributed as dist
@@ -334,6 +420,10 @@ def run_library(args):
         e2e = {"value": world * nq_step / (statistics.median(e_ms) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": len(e_ms)}
 
+    variants = None
+    if rank == 0 and not args.no_variants and only is None:
+        variants = run_variants(args, eri, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sampled = oracle_sweep_rate(basis, batches, budget_s=args.ref_budget)
@@ -354,7 +444,8 @@ def run_library(args):
                        "l2": "flushed between timed steps (256 MiB write); outputs 8 GB/step also exceed L2",
                        "parallelism": f"weak x{world}: each rank its own seeded sweep"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-            "clocks": clk.summary(), "wall_s_timed": t_wall, "step_ms": step_ms, "per_class": per_class,
+            "clocks": clk.summary(), "wall_s_timed": t_wall, "step_ms": step_ms, "variants": variants,
+            "per_class": per_class,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -372,6 +463,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=18.0, help="seconds of oracle CPU work per reference step")
     ap.add_argument("--only-class", default=None, help="profiling aid: one class, e.g. 2222")
+    ap.add_argument("--no-variants", action="store_true", help="skip the split/adjoint/batched measurements")
+    ap.add_argument("--split-nq-k5", type=int, default=10_000)
+    ap.add_argument("--adjoint-nq", type=int, default=20_000)
+    ap.add_argument("--molecule-natom", type=int, default=16)
     ap.add_argument("--nq", type=int, default=NQ_PER_CLASS, help="quartets per class")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -176,6 +176,52 @@ int eri_batch_noalloc(eri_class_t cls, const eri_basis_t* basis,
                       double* out, int64_t out_len, void* stream);
 
 /*
+ * Plans: the batched form over a whole basis.
+ *
+ * eri_plan_create -- every unique shell quartet (pair P >= pair Q over the
+ * unique shell pairs i >= j) of `basis` whose Schwarz bound
+ * Q_P Q_Q, Q_P = sqrt(max_ab |(ab|ab)|), reaches `threshold` (<= 0 keeps
+ * every quartet), all classes together (batch-level screening, Section 3.1).
+ * The plan copies the shell table to the host once (synchronising
+ * `stream`), computes the Schwarz factors with eri_batch, buckets the pairs
+ * by (class, contraction signature), sorts them by Q, builds the pair
+ * tables and a device work queue, and owns all of it until
+ * eri_plan_destroy.  The basis arrays must stay valid and unchanged for the
+ * plan's lifetime.
+ *   flags: ERI_PLAN_STORE  keep every integral (eri_plan_execute writes
+ *                          them, job after job; for verification sizes);
+ *          ERI_PLAN_SPLIT  split-precision transforms.
+ * eri_plan_execute -- one persistent kernel over the queue, replayed as a
+ * CUDA graph (captured on the first call).  Without ERI_PLAN_STORE it
+ * writes *energy = sum over the plan's quartets of
+ * sum_abcd D_ab D_cd (ab|cd) (D: [nbf][nbf] device, nbf = the number of
+ * Cartesian functions of the basis, shells in order), and `out` must be
+ * NULL.  With ERI_PLAN_STORE it writes the integrals to `out` (out_len >=
+ * eri_plan_info's out_len): job j (see eri_plan_job) at offset out_off, in
+ * the list-form layout of eri_batch for its own class and quartet order.
+ * eri_plan_set_budget -- bound each CTA of later executions to `cycles`
+ * SM clock cycles (0 = no bound); a CTA over budget stops taking work and
+ * the execution reports ERI_ETIMEOUT through eri_plan_status, which
+ * synchronises `stream`.
+ * eri_plan_info / eri_plan_job -- sizes; job j's class, quartet count,
+ * output offset, and (if quartet_shells is a HOST buffer of 4*nq ints)
+ * its quartets as shell indices (a, b, c, d) in output order.
+ */
+typedef struct eri_plan eri_plan_t;
+#define ERI_PLAN_STORE 1
+#define ERI_PLAN_SPLIT 2
+#define ERI_PLAN_NO_TUNE 4
+int eri_plan_create(const eri_basis_t* basis, double threshold, int flags, void* stream, eri_plan_t** plan);
+int eri_plan_execute(eri_plan_t* plan, const double* D, int32_t nbf, double* energy,
+                     double* out, int64_t out_len, void* stream);
+int eri_plan_set_budget(eri_plan_t* plan, int64_t cycles);
+int eri_plan_status(eri_plan_t* plan, void* stream);
+int eri_plan_info(eri_plan_t* plan, int64_t* nquartets, int32_t* njobs, int64_t* nitems, int64_t* out_len);
+int eri_plan_job(eri_plan_t* plan, int32_t job, eri_class_t* cls, int64_t* nq, int64_t* out_off,
+                 int32_t* quartet_shells);
+int eri_plan_destroy(eri_plan_t* plan);
+
+/*
  * eri_last_status -- synchronises `stream` and returns ERI_OK or the first
  * error a kernel recorded since the previous call (then clears it).
  */

@@ -13,6 +13,8 @@ from .binding import (  # noqa: F401
     eri_batch,
     eri_batch_grad,
     eri_batch_noalloc,
+    Plan,
+    ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE,
     ERI_NOALLOC_SCRATCH_BYTES,
     eri_last_status,
     eri_finalize,

@@ -41,8 +41,11 @@ class eri_basis_t(ctypes.Structure):
 
 
 EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
-           "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc"]
+           "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc", "eri_plan_create",
+           "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
+           "eri_plan_destroy"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
+ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS = 0, 1, 2, 3
 
 
@@ -65,6 +68,16 @@ def lib() -> ctypes.CDLL:
             L.eri_batch_noalloc.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P,
                                             I64, P]
             L.eri_batch_noalloc.restype = I
+            L.eri_plan_create.argtypes = [ctypes.POINTER(eri_basis_t), ctypes.c_double, I, P, ctypes.POINTER(P)]
+            L.eri_plan_execute.argtypes = [P, P, ctypes.c_int32, P, P, I64, P]
+            L.eri_plan_set_budget.argtypes = [P, I64]
+            L.eri_plan_status.argtypes = [P, P]
+            L.eri_plan_info.argtypes = [P, P, P, P, P]
+            L.eri_plan_job.argtypes = [P, ctypes.c_int32, P, P, P, P]
+            L.eri_plan_destroy.argtypes = [P]
+            for f in ("eri_plan_create", "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status",
+                      "eri_plan_info", "eri_plan_job", "eri_plan_destroy"):
+                getattr(L, f).restype = I
             L.eri_profile_enable.argtypes = [I]
             L.eri_profile_enable.restype = I
             L.eri_profile_read.argtypes = [I, P, P]
@@ -219,3 +232,57 @@ def eri_batch_noalloc(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pair
                                    _stream(stream))
     _check(code, "eri_batch_noalloc")
     return out
+
+
+class Plan:
+    """eri_plan_* over a DeviceBasis (kept alive with the plan)."""
+
+    def __init__(self, basis: DeviceBasis, threshold: float = 1e-12, flags: int = 0, stream=None):
+        self.basis = basis
+        self._struct = basis.struct()
+        self.ptr = ctypes.c_void_p()
+        self.flags = flags
+        _check(lib().eri_plan_create(ctypes.byref(self._struct), float(threshold), flags, _stream(stream),
+                                     ctypes.byref(self.ptr)), "eri_plan_create")
+
+    def info(self):
+        nq, nj, ni, ol = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().eri_plan_info(self.ptr, ctypes.byref(nq), ctypes.byref(nj), ctypes.byref(ni), ctypes.byref(ol)),
+               "eri_plan_info")
+        return {"nquartets": nq.value, "njobs": nj.value, "nitems": ni.value, "out_len": ol.value}
+
+    def job(self, j: int, with_quartets: bool = False):
+        import numpy as np
+        cls = eri_class_t()
+        nq, off = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().eri_plan_job(self.ptr, j, ctypes.byref(cls), ctypes.byref(nq), ctypes.byref(off), None),
+               "eri_plan_job")
+        shells = None
+        if with_quartets:
+            shells = np.zeros((nq.value, 4), dtype=np.int32)
+            _check(lib().eri_plan_job(self.ptr, j, None, None, None, ctypes.c_void_p(shells.ctypes.data)),
+                   "eri_plan_job")
+        return (cls.la, cls.lb, cls.lc, cls.ld), nq.value, off.value, shells
+
+    def execute(self, D: torch.Tensor | None = None, energy: torch.Tensor | None = None,
+                out: torch.Tensor | None = None, stream=None):
+        nbf = D.shape[0] if D is not None else 0
+        _check(lib().eri_plan_execute(self.ptr, _ptr(D), nbf, _ptr(energy), _ptr(out),
+                                      out.numel() if out is not None else 0, _stream(stream)), "eri_plan_execute")
+
+    def set_budget(self, cycles: int):
+        _check(lib().eri_plan_set_budget(self.ptr, int(cycles)), "eri_plan_set_budget")
+
+    def status(self, stream=None) -> int:
+        return lib().eri_plan_status(self.ptr, _stream(stream))
+
+    def destroy(self):
+        if self.ptr:
+            lib().eri_plan_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

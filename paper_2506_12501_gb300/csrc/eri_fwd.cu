@@ -24,11 +24,9 @@
 
 #include "eri_device.cuh"
 #include "eri_internal.h"
+#include "eri_tile.cuh"
 
 namespace eri {
-
-constexpr int kNT = 256;   // threads per CTA of fwd_kernel
-constexpr int kNACC = 16;  // outputs per thread held in registers
 
 // ---------------------------------------------------------------------------
 // 1. prepass
@@ -108,29 +106,6 @@ struct PairArgs {
 };
 
 constexpr int kEax = (kLmax + 3) * (kLmax + 3) * (2 * kLmax + 5);  // per-axis E table bound (adjoint shifts)
-
-// ---- split precision: a double x is carried as hi + lo with hi = fl32(x),
-// lo = fl32(x - hi) (about 48 significant bits); products of two such pairs
-// keep the exact error of hi*hi (from an FMA) and the two cross terms, and
-// sums are compensated (TwoSum), so a long sum keeps about 44 bits.  The
-// rounded intrinsics keep the compiler from contracting the error terms.
-__device__ __forceinline__ float2 split_f64(double x)
-{
-    const float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
-}
-
-// (S, c) += a * b with a, b split pairs
-__device__ __forceinline__ void ff_mac(float2 a, float2 b, float& S, float& c)
-{
-    const float p = __fmul_rn(a.x, b.x);
-    const float pe = __fmaf_rn(a.x, b.x, -p);
-    const float t = __fadd_rn(S, p);
-    const float z = __fsub_rn(t, S);
-    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, z)), __fsub_rn(p, z));
-    S = t;
-    c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, pe))));
-}
 
 __global__ void pair_kernel(PairArgs a)
 {
@@ -235,286 +210,6 @@ __global__ void pair_kernel(PairArgs a)
     }
 }
 
-// ---------------------------------------------------------------------------
-// 3. forward kernel
-// ---------------------------------------------------------------------------
-struct FwdArgs {
-    ClassTables ct;
-    const double* boys;
-    const RStep* rsteps;
-    const double* bra_ps;
-    const double* bra_E;
-    const int32_t* bra_kp;
-    const double* ket_ps;
-    const double* ket_E;
-    const int32_t* ket_kp;
-    const int64_t* quartets;  // NULL: product form
-    int64_t nq, nbra, nket;   // nbra/nket: the caller's lists (before any swap)
-    int swap;                 // 1: the kernel's bra is the caller's ket
-    int nab_o, ncd_o;         // component-pair counts of the caller's class
-    double* out;
-    int TQ, KB, KK, IC;
-    int e_smem, acc_regs;
-    int sEbS, sEkS;           // per-quartet strides of staged E (doubles)
-    int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;  // smem offsets (doubles)
-    int64_t ntiles;
-};
-
-struct Strided {
-    double* p;
-    int s;
-    __device__ __forceinline__ double& operator[](int e) const { return p[(size_t)e * s]; }
-};
-
-// Output position of the kernel's component pair (ab, cd) of quartet qq, in
-// the caller's layout (ab and cd exchange roles when the sides were swapped).
-__device__ __forceinline__ int64_t out_index(const FwdArgs& a, int64_t qq, int ab, int cd)
-{
-    const int abo = a.swap ? cd : ab, cdo = a.swap ? ab : cd;
-    if (a.quartets) return qq + a.nq * ((int64_t)abo * a.ncd_o + cdo);
-    const int64_t bra = qq % a.nbra, ket = qq / a.nbra;
-    return bra + a.nbra * (abo + (int64_t)a.nab_o * (cdo + (int64_t)a.ncd_o * ket));
-}
-
-// The kernel's (bra, ket) pair indices of quartet qq.
-__device__ __forceinline__ void quartet_pairs(const FwdArgs& a, int64_t qq, int* b, int* k)
-{
-    int64_t ob, ok;
-    if (a.quartets) {
-        ob = a.quartets[2 * qq];
-        ok = a.quartets[2 * qq + 1];
-    } else {
-        ob = qq % a.nbra;
-        ok = qq / a.nbra;
-    }
-    *b = (int)(a.swap ? ok : ob);
-    *k = (int)(a.swap ? ob : ok);
-}
-
-// Stage C inner sum: sum_{u in [u0,u1)} E^ab_u X[p_u][cd] of one quartet and
-// one bra primitive (E term u at Eb[u * KB]).  Two alternating chains; the
-// split form returns its compensated float sum as a double (2 FP64 ops).
-template <bool SPLIT>
-__device__ __forceinline__ double bra_sum(const double* Eb, int KB, const double* sX, int u0, int u1,
-                                          const int16_t* s_bp, int ncd, int cd, int TQ, int q)
-{
-    if (!SPLIT) {
-        double va = 0.0, vb = 0.0;
-        int u = u0;
-        for (; u + 1 < u1; u += 2) {
-            va = fma(Eb[(size_t)u * KB], sX[(s_bp[u] * ncd + cd) * TQ + q], va);
-            vb = fma(Eb[(size_t)(u + 1) * KB], sX[(s_bp[u + 1] * ncd + cd) * TQ + q], vb);
-        }
-        if (u < u1) va = fma(Eb[(size_t)u * KB], sX[(s_bp[u] * ncd + cd) * TQ + q], va);
-        return va + vb;
-    } else {
-        const float2* E2 = reinterpret_cast<const float2*>(Eb);
-        const float2* X2 = reinterpret_cast<const float2*>(sX);
-        float S = 0.f, c = 0.f;
-        for (int u = u0; u < u1; ++u) ff_mac(E2[(size_t)u * KB], X2[(s_bp[u] * ncd + cd) * TQ + q], S, c);
-        return (double)S + (double)c;
-    }
-}
-
-template <bool SPLIT>
-__global__ void __launch_bounds__(kNT) fwd_kernel_t(FwdArgs a)
-{
-    extern __shared__ __align__(16) double sm[];
-    const ClassTables& ct = a.ct;
-    const int tid = threadIdx.x;
-    const int TQ = a.TQ, KB = a.KB, KK = a.KK, IC = a.IC;
-    const int nhl = ct.nhl, nhb = ct.nhb, nhk = ct.nhk, ncd = ct.ncd, nab = ct.nab;
-    const int NI = TQ * IC * KK;  // R columns
-
-    // class tables into shared memory (once per CTA)
-    int* s_bstart = reinterpret_cast<int*>(sm + a.o_tab);
-    int* s_kstart = s_bstart + nab + 1;
-    int16_t* s_bp = reinterpret_cast<int16_t*>(s_kstart + ncd + 1);
-    int16_t* s_kq = s_bp + ct.Tab;
-    int16_t* s_pq = s_kq + ct.Tcd;
-    for (int i = tid; i <= nab; i += kNT) s_bstart[i] = ct.bra_start[i];
-    for (int i = tid; i <= ncd; i += kNT) s_kstart[i] = ct.ket_start[i];
-    for (int i = tid; i < ct.Tab; i += kNT) s_bp[i] = ct.bra_p[i];
-    for (int i = tid; i < ct.Tcd; i += kNT) s_kq[i] = ct.ket_q[i];
-    for (int i = tid; i < nhb * nhk; i += kNT) s_pq[i] = ct.pq[i];
-
-    int* s_q = reinterpret_cast<int*>(sm + a.o_q);  // [TQ][4]: bra, ket, Kbra, Kket
-    double* sEb = sm + a.o_Eb;
-    double* sEk = sm + a.o_Ek;
-    double* sPb = sm + a.o_Pb;
-    double* sPk = sm + a.o_Pk;
-    double* sR = sm + a.o_R;
-    double* sX = sm + a.o_X;
-
-    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const int64_t q0 = tile * TQ;
-        const int nqt = (int)min((int64_t)TQ, a.nq - q0);
-        __syncthreads();
-        for (int q = tid; q < TQ; q += kNT) {
-            int b = 0, k = 0, kb = 0, kk = 0;
-            if (q < nqt) {
-                quartet_pairs(a, q0 + q, &b, &k);
-                kb = a.bra_kp[b];
-                kk = a.ket_kp[k];
-            }
-            s_q[4 * q] = b;
-            s_q[4 * q + 1] = k;
-            s_q[4 * q + 2] = kb;
-            s_q[4 * q + 3] = kk;
-        }
-        __syncthreads();
-        // stage primitive-pair scalars (and E products) of the tile
-        for (int idx = tid; idx < TQ * KB * PS_N; idx += kNT) {
-            const int q = idx / (KB * PS_N), r = idx - q * KB * PS_N, i = r / PS_N;
-            sPb[idx] = i < s_q[4 * q + 2] ? a.bra_ps[(size_t)s_q[4 * q] * KB * PS_N + r] : 1.0;
-        }
-        for (int idx = tid; idx < TQ * KK * PS_N; idx += kNT) {
-            const int q = idx / (KK * PS_N), r = idx - q * KK * PS_N, k = r / PS_N;
-            sPk[idx] = k < s_q[4 * q + 3] ? a.ket_ps[(size_t)s_q[4 * q + 1] * KK * PS_N + r] : 1.0;
-        }
-        if (a.e_smem) {
-            const int nb = KB * ct.Tab, nk = KK * ct.Tcd;
-            for (int idx = tid; idx < TQ * nb; idx += kNT) {
-                const int q = idx / nb, r = idx - q * nb, i = r % KB;
-                sEb[q * a.sEbS + r] = i < s_q[4 * q + 2] ? a.bra_E[(size_t)s_q[4 * q] * nb + r] : 0.0;
-            }
-            for (int idx = tid; idx < TQ * nk; idx += kNT) {
-                const int q = idx / nk, r = idx - q * nk, k = r % KK;
-                sEk[q * a.sEkS + r] = k < s_q[4 * q + 3] ? a.ket_E[(size_t)s_q[4 * q + 1] * nk + r] : 0.0;
-            }
-        }
-        // output accumulators
-        double acc[kNACC];
-#pragma unroll
-        for (int s = 0; s < kNACC; ++s) acc[s] = 0.0;
-
-        for (int i0 = 0; i0 < KB; i0 += IC) {
-            __syncthreads();
-            // ---- A: auxiliary integrals of the primitive quartets (q, i0+ii, k)
-            for (int item = tid; item < NI; item += kNT) {
-                const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
-                const int i = i0 + ii;
-                Strided R{sR + item, NI};
-                if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
-                    const double* pb = sPb + (q * KB + i) * PS_N;
-                    const double* pk = sPk + (q * KK + k) * PS_N;
-                    const double zp = pb[PS_P], zq = pk[PS_P];
-                    const double rs = rsqrt(zp + zq);
-                    const double rho = zp * zq * (rs * rs);
-                    const double X = pb[PS_PX] - pk[PS_PX], Y = pb[PS_PY] - pk[PS_PY], Z = pb[PS_PZ] - pk[PS_PZ];
-                    const double PQ2 = fma(X, X, fma(Y, Y, Z * Z));
-                    const double T = rho * PQ2;
-                    double base[kLtotMax + 1];
-                    boys_eval(ct.L, T, a.boys, base);
-                    double f = pb[PS_INVP] * pk[PS_INVP] * rs;  // 2 pi^(5/2) / (zp zq sqrt(zp+zq))
-                    const double m2rho = -2.0 * rho;
-                    for (int n = 0; n <= ct.L; ++n) {
-                        base[n] *= f;
-                        f *= m2rho;
-                    }
-                    r_recursion(ct.L, base, X, Y, Z, a.rsteps, R);
-                    if (SPLIT)  // each entry becomes its (hi, lo) float pair, in place
-                        for (int e = 0; e < nhl; ++e) {
-                            double& slot = R[e];
-                            const float2 f = split_f64(slot);
-                            reinterpret_cast<float2&>(slot) = f;
-                        }
-                } else {
-                    for (int e = 0; e < nhl; ++e) R[e] = 0.0;
-                }
-            }
-            __syncthreads();
-            for (int ii = 0; ii < IC && i0 + ii < KB; ++ii) {
-                const int i = i0 + ii;
-                // ---- B: ket transform + ket contraction
-                const int nB = TQ * nhb * ncd;
-                for (int item = tid; item < nB; item += kNT) {
-                    const int q = item % TQ, r = item / TQ, p = r % nhb, cd = r / nhb;
-                    const double* Ek = a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd;
-                    const double* Rc = sR + (q * IC + ii) * KK;  // + e * NI + k
-                    const int16_t* pqrow = s_pq + p * nhk;
-                    const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
-                    // terms outer, ket primitives inner: one p+q lookup per term
-                    // serves all KK primitives (E is stored slot-fastest); two
-                    // accumulator chains alternate to hide the DFMA latency
-                    if (!SPLIT) {
-                        double va = 0.0, vb = 0.0;
-                        for (int t = t0; t < t1; ++t) {
-                            const double* Rk = Rc + (size_t)pqrow[s_kq[t]] * NI;
-                            const double* Et = Ek + t * KK;
-                            int k = 0;
-                            for (; k + 1 < KK; k += 2) {
-                                va = fma(Et[k], Rk[k], va);
-                                vb = fma(Et[k + 1], Rk[k + 1], vb);
-                            }
-                            if (k < KK) {
-                                const double w = fma(Et[k], Rk[k], va);
-                                va = vb;
-                                vb = w;
-                            }
-                        }
-                        sX[(p * ncd + cd) * TQ + q] = va + vb;
-                    } else {
-                        float Sa = 0.f, ca = 0.f, Sb = 0.f, cb = 0.f;
-                        for (int t = t0; t < t1; ++t) {
-                            const float2* Rk = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NI);
-                            const float2* Et = reinterpret_cast<const float2*>(Ek + t * KK);
-                            int k = 0;
-                            for (; k + 1 < KK; k += 2) {
-                                ff_mac(Et[k], Rk[k], Sa, ca);
-                                ff_mac(Et[k + 1], Rk[k + 1], Sb, cb);
-                            }
-                            if (k < KK) ff_mac(Et[k], Rk[k], Sa, ca);
-                        }
-                        // (Sa + Sb, ca + cb) as one split pair (error-free sum of the highs)
-                        const float t2 = __fadd_rn(Sa, Sb), z = __fsub_rn(t2, Sa);
-                        const float err = __fadd_rn(__fsub_rn(Sa, __fsub_rn(t2, z)), __fsub_rn(Sb, z));
-                        reinterpret_cast<float2*>(sX)[(p * ncd + cd) * TQ + q] =
-                            make_float2(t2, __fadd_rn(__fadd_rn(ca, cb), err));
-                    }
-                }
-                __syncthreads();
-                // ---- C: bra transform + bra contraction
-                const int nC = TQ * nab * ncd;
-                if (a.acc_regs) {
-#pragma unroll
-                    for (int s = 0; s < kNACC; ++s) {
-                        const int item = tid + s * kNT;
-                        if (item < nC) {
-                            const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
-                            const double* Eb = a.e_smem ? sEb + q * a.sEbS
-                                                        : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab;
-                            acc[s] += bra_sum<SPLIT>(Eb + i, KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
-                        }
-                    }
-                } else {
-                    for (int item = tid; item < nC; item += kNT) {
-                        const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
-                        if (q >= nqt) continue;
-                        const double* Eb = a.e_smem ? sEb + q * a.sEbS : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab;
-                        const double v =
-                            bra_sum<SPLIT>(Eb + i, KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
-                        const int64_t o = out_index(a, q0 + q, ab, cd);
-                        a.out[o] = (i == 0) ? v : a.out[o] + v;
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        if (a.acc_regs) {
-            const int nC = TQ * nab * ncd;
-#pragma unroll
-            for (int s = 0; s < kNACC; ++s) {
-                const int item = tid + s * kNT;
-                if (item < nC) {
-                    const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
-                    if (q < nqt) a.out[out_index(a, q0 + q, ab, cd)] = acc[s];
-                }
-            }
-        }
-    }
-}
-
 static const auto fwd_kernel = fwd_kernel_t<false>;
 static const auto fwd_kernel_split = fwd_kernel_t<true>;
 
@@ -558,16 +253,9 @@ int max_smem_optin()
 // Tile planning: pick (TQ, IC, e_smem, acc_regs) so that shared memory fits
 // and the auxiliary-integral stage has enough independent items.
 // ---------------------------------------------------------------------------
-struct TilePlan {
-    int TQ, IC, e_smem, acc_regs;
-    int sEbS, sEkS;
-    int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;
-    size_t bytes;
-};
-
 static int odd_up(int n) { return n | 1; }
 
-static bool layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp)
+bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp)
 {
     size_t off = 0;
     auto take = [&](size_t nd) {
@@ -594,7 +282,7 @@ static bool layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_
     return tp->bytes <= (size_t)max_smem_optin();
 }
 
-static bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best)
+bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best)
 {
     bool found = false;
     double best_score = -1.0;
@@ -604,7 +292,7 @@ static bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePl
             if (TQ > 1 && (int64_t)TQ > 2 * nq) continue;
             for (int IC = KB; IC >= 1; IC = (IC + 1) / 2 - (IC == 1)) {
                 TilePlan tp;
-                if (!layout(ct, KB, KK, TQ, IC, e_smem, &tp)) {
+                if (!tile_layout(ct, KB, KK, TQ, IC, e_smem, &tp)) {
                     if (IC == 1) break;
                     continue;
                 }
@@ -998,6 +686,41 @@ int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, 
     const int64_t grid2 = std::min<int64_t>(a.ntiles, (int64_t)per_sm * sm_count());
     count_launch();
     fwd_kernel<<<(int)grid2, kNT, tp.bytes, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
+}
+
+}  // namespace eri
+
+namespace eri {
+
+// Pair tables of one list of shell pairs with a uniform K1*K2 = KS, written
+// into caller-provided buffers (plans own theirs).
+int build_pair_tables_on(const eri_basis_t* basis, const int32_t* d_pairs, int64_t npairs, int l1, int l2, int KS,
+                         int T, const uint8_t* fac, int ket, int split, PairTables* out, cudaStream_t st)
+{
+    PairArgs p{};
+    p.centres = basis->centres;
+    p.shell_atom = basis->shell_atom;
+    p.shell_K = basis->shell_K;
+    p.shell_off = basis->shell_off;
+    p.exps = basis->exps;
+    p.coefs = basis->coefs;
+    p.pairs = d_pairs;
+    p.npairs = npairs;
+    p.l1 = l1;
+    p.l2 = l2;
+    p.KS = KS;
+    p.T = T;
+    p.fac = fac;
+    p.ket = ket;
+    p.ps = out->ps;
+    p.E = out->E;
+    p.kprim = out->kp;
+    p.split = split;
+    const int64_t tot = npairs * KS;
+    const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
+    count_launch();
+    pair_kernel<<<std::max(g, 1), 128, 0, st>>>(p);
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
 }
 

@@ -107,6 +107,16 @@ int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* b
 int sm_count();
 int max_smem_optin();
 
+// Tile shape of the forward kernel for one class (eri_fwd.cu).
+struct TilePlan {
+    int TQ, IC, e_smem, acc_regs;
+    int sEbS, sEkS;
+    int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;
+    size_t bytes;
+};
+bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best);
+bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp);
+
 // Measurement hook: events around launches of kernel `id` (eri_profile_*).
 enum { PROF_FWD = 0, PROF_GRAD = 1, PROF_PAIR = 2, PROF_PREPASS = 3, PROF_N = 8 };
 struct ProfScope {

@@ -1,0 +1,175 @@
+"""The batched form (eri_plan_*): Schwarz-screened unique quartets of a
+molecule-shaped basis, all classes in one persistent graph-replayed kernel,
+digested into sum D_ab D_cd (ab|cd) or stored; checked against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2506_12501_gb300 as eri
+from gpu_helpers import THREADS, assert_close
+
+pytestmark = pytest.mark.gpu
+
+
+def nc(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def bf_offsets(basis):
+    ncs = (basis.shell_l + 1) * (basis.shell_l + 2) // 2
+    return np.concatenate([[0], np.cumsum(ncs)[:-1]]).astype(np.int64), int(ncs.sum())
+
+
+def weights(basis, shells, D):
+    """W[q][ab][cd] = D_ab D_cd for quartets of shell indices (a, b, c, d)."""
+    off, _ = bf_offsets(basis)
+    l = basis.shell_l
+    out = []
+    for a, b, c, d in shells:
+        ia = off[a] + np.arange(nc(l[a]))
+        ib = off[b] + np.arange(nc(l[b]))
+        ic = off[c] + np.arange(nc(l[c]))
+        id_ = off[d] + np.arange(nc(l[d]))
+        out.append(np.einsum("ab,cd->abcd", D[np.ix_(ia, ib)], D[np.ix_(ic, id_)]).ravel())
+    return np.concatenate(out)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    basis = synth.molecule_basis(natom=3, radius=2.2, seed=5)
+    _, nbf = bf_offsets(basis)
+    rng = np.random.default_rng(6)
+    U = rng.uniform(-1, 1, (nbf, nbf))
+    D = np.triu(U) + np.triu(U, 1).T
+    return basis, D
+
+
+def test_plan_store_matches_oracle(cuda, tiny):
+    basis, D = tiny
+    db = eri.DeviceBasis(basis)
+    plan = eri.Plan(db, threshold=0.0, flags=eri.ERI_PLAN_STORE)
+    info = plan.info()
+    ns = basis.nshell
+    npairs = ns * (ns + 1) // 2
+    assert info["nquartets"] == npairs * (npairs + 1) // 2   # every unique quartet, once
+    out = torch.full((info["out_len"],), float("nan"), dtype=torch.float64, device=cuda)
+    plan.execute(out=out)
+    torch.cuda.synchronize()
+    host = out.cpu().numpy()
+    seen = set()
+    for j in range(info["njobs"]):
+        cls, nq, off, shells = plan.job(j, with_quartets=True)
+        nab, ncd = nc(cls[0]) * nc(cls[1]), nc(cls[2]) * nc(cls[3])
+        got = host[off:off + nq * nab * ncd].reshape(nab * ncd, nq).T
+        ref = oracle.eri_quartets(basis, shells, prec="d", threads=THREADS).reshape(nq, nab * ncd)
+        assert_close(got, ref, what=f"plan job {j} {cls}")
+        for a, b, c, d in shells:
+            key = (min(a, b), max(a, b), min(c, d), max(c, d))
+            key = min(key, key[2:] + key[:2])
+            assert key not in seen
+            seen.add(key)
+    assert len(seen) == info["nquartets"]
+
+
+def test_plan_energy_digest_against_oracle(cuda, tiny):
+    basis, D = tiny
+    db = eri.DeviceBasis(basis)
+    plan = eri.Plan(db, threshold=0.0)
+    Dd = torch.as_tensor(D, device=cuda)
+    e = torch.zeros(1, dtype=torch.float64, device=cuda)
+    plan.execute(D=Dd, energy=e)
+    assert plan.status() == eri.ERI_OK
+    got = float(e.item())
+    store = eri.Plan(db, threshold=0.0, flags=eri.ERI_PLAN_STORE)
+    ref = 0.0
+    for j in range(store.info()["njobs"]):
+        cls, nq, off, shells = store.job(j, with_quartets=True)
+        vals = oracle.eri_quartets(basis, shells, prec="d", threads=THREADS)
+        ref += float(np.dot(vals, weights(basis, shells, D)))
+    assert abs(got - ref) <= 1e-10 * max(1.0, abs(ref)), (got, ref)
+    # graph replay gives the same number; the parameters (D) are re-read
+    plan.execute(D=Dd, energy=e)
+    assert float(e.item()) == pytest.approx(got, rel=1e-13, abs=0)
+    plan.execute(D=2.0 * Dd, energy=e)
+    assert float(e.item()) == pytest.approx(4.0 * got, rel=1e-12)
+
+
+def test_plan_schwarz_screening(cuda):
+    """The screened plan keeps exactly the quartets with Q_P Q_Q >= threshold,
+    Q from the oracle's diagonal integrals, and its energy differs from the
+    unscreened one by no more than the bound the dropped quartets allow."""
+    basis = synth.molecule_basis(natom=6, radius=9.0, seed=11)
+    db = eri.DeviceBasis(basis)
+    thr = 1e-8
+    plan = eri.Plan(db, threshold=thr)
+    full = eri.Plan(db, threshold=0.0)
+    pairs = synth.unique_pairs(basis)
+    diag = oracle.eri_quartets(basis, np.concatenate([pairs, pairs], axis=1), prec="d", threads=THREADS)
+    sizes = oracle.shellset_size(basis, np.concatenate([pairs, pairs], axis=1))
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    Q = np.empty(len(pairs))
+    for i, (a, b) in enumerate(pairs):
+        nab = nc(basis.shell_l[a]) * nc(basis.shell_l[b])
+        blk = diag[offs[i]:offs[i + 1]].reshape(nab, nab)
+        Q[i] = np.sqrt(np.max(np.abs(np.diag(blk))))
+    prod = np.multiply.outer(Q, Q)[np.tril_indices(len(Q))]
+    border = np.abs(prod - thr) <= 1e-9 * thr
+    kept = int(np.sum(prod >= thr))
+    assert abs(plan.info()["nquartets"] - kept) <= int(border.sum())
+    assert plan.info()["nquartets"] < full.info()["nquartets"]
+    _, nbf = bf_offsets(basis)
+    D = torch.as_tensor(np.random.default_rng(3).uniform(-1, 1, (nbf, nbf)), device=cuda)
+    D = 0.5 * (D + D.T)
+    e1 = torch.zeros(1, dtype=torch.float64, device=cuda)
+    e2 = torch.zeros(1, dtype=torch.float64, device=cuda)
+    plan.execute(D=D, energy=e1)
+    full.execute(D=D, energy=e2)
+    dropped = full.info()["nquartets"] - plan.info()["nquartets"]
+    # |(ab|cd)| <= Q_P Q_Q < thr for every dropped element; |W| <= 1; at most 6^4 elements each
+    assert abs(float(e1.item()) - float(e2.item())) <= dropped * thr * 6 ** 4
+
+
+def test_plan_split_precision(cuda, tiny):
+    basis, D = tiny
+    db = eri.DeviceBasis(basis)
+    Dd = torch.as_tensor(D, device=cuda)
+    e64 = torch.zeros(1, dtype=torch.float64, device=cuda)
+    esp = torch.zeros(1, dtype=torch.float64, device=cuda)
+    eri.Plan(db, threshold=1e-12).execute(D=Dd, energy=e64)
+    eri.Plan(db, threshold=1e-12, flags=eri.ERI_PLAN_SPLIT).execute(D=Dd, energy=esp)
+    assert abs(float(esp.item()) - float(e64.item())) <= 1e-10 * max(1.0, abs(float(e64.item())))
+
+
+def test_plan_budget_timeout_and_recovery(cuda, tiny):
+    """A cycle budget bounds the persistent kernel: an exhausted budget is
+    reported as ERI_ETIMEOUT (no fault, no hang) and the plan stays usable."""
+    basis, D = tiny
+    db = eri.DeviceBasis(basis)
+    Dd = torch.as_tensor(D, device=cuda)
+    plan = eri.Plan(db, threshold=0.0)
+    e = torch.zeros(1, dtype=torch.float64, device=cuda)
+    plan.execute(D=Dd, energy=e)
+    ref = float(e.item())
+    plan.set_budget(1)
+    plan.execute(D=Dd, energy=e)
+    assert plan.status() == eri.ERI_ETIMEOUT
+    plan.set_budget(0)
+    plan.execute(D=Dd, energy=e)
+    assert plan.status() == eri.ERI_OK
+    assert float(e.item()) == pytest.approx(ref, rel=1e-13)
+
+
+def test_plan_misuse(cuda, tiny):
+    basis, D = tiny
+    db = eri.DeviceBasis(basis)
+    plan = eri.Plan(db, threshold=0.0)
+    e = torch.zeros(1, dtype=torch.float64, device=cuda)
+    with pytest.raises(eri.EriError) as ex:
+        plan.execute(D=torch.zeros((3, 3), dtype=torch.float64, device=cuda), energy=e)
+    assert ex.value.code == eri.ERI_EPLAN
+    store = eri.Plan(db, threshold=0.0, flags=eri.ERI_PLAN_STORE)
+    with pytest.raises(eri.EriError) as ex:
+        store.execute(out=torch.zeros(10, dtype=torch.float64, device=cuda))
+    assert ex.value.code == eri.ERI_EPLAN
