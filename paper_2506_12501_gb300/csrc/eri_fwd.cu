@@ -21,6 +21,10 @@
 // Every FP64 operation of the path runs in these kernels.
 #include <algorithm>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "eri_device.cuh"
 #include "eri_internal.h"
@@ -483,6 +487,105 @@ int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* b
     return ERI_OK;
 }
 
+static void set_tile(FwdArgs& a, const TilePlan& tp)
+{
+    a.TQ = tp.TQ;
+    a.IC = tp.IC;
+    a.e_smem = tp.e_smem;
+    a.acc_regs = tp.acc_regs;
+    a.sEbS = tp.sEbS;
+    a.sEkS = tp.sEkS;
+    a.o_Eb = tp.o_Eb;
+    a.o_Ek = tp.o_Ek;
+    a.o_Pb = tp.o_Pb;
+    a.o_Pk = tp.o_Pk;
+    a.o_R = tp.o_R;
+    a.o_X = tp.o_X;
+    a.o_tab = tp.o_tab;
+    a.o_q = tp.o_q;
+}
+
+// Autotuner of eri_batch: on the first large batch of a (class, K_bra, K_ket,
+// precision) signature, time every feasible tile shape (TQ in 1..128 with
+// register accumulation, IC in {K_bra, K_bra/2, 1}, E staged when it fits)
+// on the batch's first kTuneQuartets quartets and remember the fastest.  The
+// trial launches write (part of) `out`; the real launch overwrites it.
+constexpr int64_t kTuneMinQuartets = 16384;
+constexpr int64_t kTuneQuartets = 8192;
+static std::map<std::tuple<int, int, int, int, int, int, int, int>, TilePlan> g_tuned;
+static std::mutex g_tuned_mu;
+
+static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cudaStream_t st, TilePlan* best)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const ClassTables& ct = base.ct;
+    const auto key = std::make_tuple(dev, ct.la, ct.lb, ct.lc, ct.ld, base.KB, base.KK, split);
+    {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *best = it->second;
+            return true;
+        }
+    }
+    std::vector<TilePlan> cands;
+    for (int TQ = 1; TQ <= 128; TQ *= 2) {
+        if (TQ * ct.nab * ct.ncd > kNT * kNACC) break;
+        for (int IC : {base.KB, (base.KB + 1) / 2, 1}) {
+            for (int es = 1; es >= 0; --es) {
+                TilePlan tp;
+                if (tile_layout(ct, base.KB, base.KK, TQ, IC, es, &tp) && tp.acc_regs) {
+                    bool dup = false;
+                    for (auto& c : cands) dup |= (c.TQ == TQ && c.IC == IC && c.e_smem == es);
+                    if (!dup) cands.push_back(tp);
+                    break;
+                }
+            }
+        }
+    }
+    if (cands.size() < 2) return false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int64_t nq = std::min(base.nq, kTuneQuartets);
+    double best_ms = 1e300;
+    bool ok = false;
+    for (const TilePlan& tp : cands) {
+        FwdArgs a = base;
+        set_tile(a, tp);
+        a.ntiles = (nq + tp.TQ - 1) / tp.TQ;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
+            continue;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, tp.bytes);
+        const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)std::max(per_sm, 1) * sm_count());
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, st);
+            count_launch();
+            kern<<<(int)grid, kNT, tp.bytes, st>>>(a);
+            cudaEventRecord(e1, st);
+        }
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = tp;
+            ok = true;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ok) {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        g_tuned[key] = *best;
+    }
+    return ok;
+}
+
 }  // namespace eri
 
 using namespace eri;
@@ -527,6 +630,7 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     if (!rs) return err;
     TilePlan tp;
     if (!plan_tiles(*ct, KB, KK, nqq, &tp)) return ERI_EINVAL;
+    void (*kern)(FwdArgs) = split ? fwd_kernel_split : fwd_kernel;
     FwdArgs a{};
     a.ct = *ct;
     a.boys = boys;
@@ -562,7 +666,15 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     a.o_tab = tp.o_tab;
     a.o_q = tp.o_q;
     a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
-    void (*kern)(FwdArgs) = split ? fwd_kernel_split : fwd_kernel;
+    // large batches: tile shape from the autotuner (cached per class and signature)
+    if (nqq >= kTuneMinQuartets) {
+        TilePlan best;
+        if (tuned_tile(a, kern, split, st, &best)) {
+            tp = best;
+            set_tile(a, tp);
+            a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
+        }
+    }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
         return ERI_ECUDA;
     int per_sm = 0;

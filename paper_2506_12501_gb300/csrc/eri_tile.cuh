@@ -129,9 +129,14 @@ __device__ __forceinline__ double bra_sum(const double* Eb, int KB, const double
     } else {
         const float2* E2 = reinterpret_cast<const float2*>(Eb);
         const float2* X2 = reinterpret_cast<const float2*>(sX);
-        float S = 0.f, c = 0.f;
-        for (int u = u0; u < u1; ++u) ff_mac(E2[(size_t)u * KB], X2[(s_bp[u] * ncd + cd) * TQ + q], S, c);
-        return (double)S + (double)c;
+        float Sa = 0.f, ca = 0.f, Sb = 0.f, cb = 0.f;
+        int u = u0;
+        for (; u + 1 < u1; u += 2) {
+            ff_mac(E2[(size_t)u * KB], X2[(s_bp[u] * ncd + cd) * TQ + q], Sa, ca);
+            ff_mac(E2[(size_t)(u + 1) * KB], X2[(s_bp[u + 1] * ncd + cd) * TQ + q], Sb, cb);
+        }
+        if (u < u1) ff_mac(E2[(size_t)u * KB], X2[(s_bp[u] * ncd + cd) * TQ + q], Sa, ca);
+        return ((double)Sa + (double)Sb) + ((double)ca + (double)cb);
     }
 }
 
@@ -271,42 +276,81 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 const int16_t* pqrow = s_pq + p * nhk;
                 const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
                 // terms outer, ket primitives inner: one p+q lookup per term
-                // serves all KK primitives (E is stored slot-fastest); two
-                // accumulator chains alternate to hide the DFMA latency
+                // serves all KK primitives (E is stored slot-fastest).  Two
+                // terms and two primitives at a time feed four independent
+                // accumulator chains, which hides the FP64 (or TwoSum)
+                // latency with few warps per scheduler.
                 if (!SPLIT) {
-                    double va = 0.0, vb = 0.0;
-                    for (int t = t0; t < t1; ++t) {
-                        const double* Rk = Rc + (size_t)pqrow[s_kq[t]] * NI;
-                        const double* Et = Ek + t * KK;
+                    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                    int t = t0;
+                    for (; t + 1 < t1; t += 2) {
+                        const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NI;
+                        const double* Rb = Rc + (size_t)pqrow[s_kq[t + 1]] * NI;
+                        const double* Ea = Ek + t * KK;
+                        const double* Eb2 = Ea + KK;
                         int k = 0;
                         for (; k + 1 < KK; k += 2) {
-                            va = fma(Et[k], Rk[k], va);
-                            vb = fma(Et[k + 1], Rk[k + 1], vb);
+                            v0 = fma(Ea[k], Ra[k], v0);
+                            v1 = fma(Ea[k + 1], Ra[k + 1], v1);
+                            v2 = fma(Eb2[k], Rb[k], v2);
+                            v3 = fma(Eb2[k + 1], Rb[k + 1], v3);
                         }
                         if (k < KK) {
-                            const double w = fma(Et[k], Rk[k], va);
-                            va = vb;
-                            vb = w;
+                            v0 = fma(Ea[k], Ra[k], v0);
+                            v2 = fma(Eb2[k], Rb[k], v2);
                         }
                     }
-                    sX[(p * ncd + cd) * TQ + q] = va + vb;
-                } else {
-                    float Sa = 0.f, ca = 0.f, Sb = 0.f, cb = 0.f;
-                    for (int t = t0; t < t1; ++t) {
-                        const float2* Rk = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NI);
-                        const float2* Et = reinterpret_cast<const float2*>(Ek + t * KK);
+                    if (t < t1) {
+                        const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NI;
+                        const double* Ea = Ek + t * KK;
                         int k = 0;
                         for (; k + 1 < KK; k += 2) {
-                            ff_mac(Et[k], Rk[k], Sa, ca);
-                            ff_mac(Et[k + 1], Rk[k + 1], Sb, cb);
+                            v0 = fma(Ea[k], Ra[k], v0);
+                            v1 = fma(Ea[k + 1], Ra[k + 1], v1);
                         }
-                        if (k < KK) ff_mac(Et[k], Rk[k], Sa, ca);
+                        if (k < KK) v0 = fma(Ea[k], Ra[k], v0);
                     }
-                    // (Sa + Sb, ca + cb) as one split pair (error-free sum of the highs)
-                    const float t2 = __fadd_rn(Sa, Sb), z = __fsub_rn(t2, Sa);
-                    const float err = __fadd_rn(__fsub_rn(Sa, __fsub_rn(t2, z)), __fsub_rn(Sb, z));
-                    reinterpret_cast<float2*>(sX)[(p * ncd + cd) * TQ + q] =
-                        make_float2(t2, __fadd_rn(__fadd_rn(ca, cb), err));
+                    sX[(p * ncd + cd) * TQ + q] = (v0 + v1) + (v2 + v3);
+                } else {
+                    float S[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+                    int t = t0;
+                    for (; t + 1 < t1; t += 2) {
+                        const float2* Ra = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NI);
+                        const float2* Rb = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t + 1]] * NI);
+                        const float2* Ea = reinterpret_cast<const float2*>(Ek + t * KK);
+                        const float2* Eb2 = Ea + KK;
+                        int k = 0;
+                        for (; k + 1 < KK; k += 2) {
+                            ff_mac(Ea[k], Ra[k], S[0], c[0]);
+                            ff_mac(Ea[k + 1], Ra[k + 1], S[1], c[1]);
+                            ff_mac(Eb2[k], Rb[k], S[2], c[2]);
+                            ff_mac(Eb2[k + 1], Rb[k + 1], S[3], c[3]);
+                        }
+                        if (k < KK) {
+                            ff_mac(Ea[k], Ra[k], S[0], c[0]);
+                            ff_mac(Eb2[k], Rb[k], S[2], c[2]);
+                        }
+                    }
+                    if (t < t1) {
+                        const float2* Ra = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NI);
+                        const float2* Ea = reinterpret_cast<const float2*>(Ek + t * KK);
+                        int k = 0;
+                        for (; k + 1 < KK; k += 2) {
+                            ff_mac(Ea[k], Ra[k], S[0], c[0]);
+                            ff_mac(Ea[k + 1], Ra[k + 1], S[1], c[1]);
+                        }
+                        if (k < KK) ff_mac(Ea[k], Ra[k], S[0], c[0]);
+                    }
+                    // fold the four chains into one split pair (error-free sums of the highs)
+                    float Sh = S[0], ch = c[0];
+#pragma unroll
+                    for (int j = 1; j < 4; ++j) {
+                        const float t2 = __fadd_rn(Sh, S[j]), z = __fsub_rn(t2, Sh);
+                        const float err = __fadd_rn(__fsub_rn(Sh, __fsub_rn(t2, z)), __fsub_rn(S[j], z));
+                        Sh = t2;
+                        ch = __fadd_rn(__fadd_rn(ch, c[j]), err);
+                    }
+                    reinterpret_cast<float2*>(sX)[(p * ncd + cd) * TQ + q] = make_float2(Sh, ch);
                 }
             }
             __syncthreads();

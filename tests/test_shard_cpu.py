@@ -1,0 +1,79 @@
+"""Sharding of a screened quartet list over ranks (CPU, gloo, world size 2):
+the cost-balanced partition covers every quartet exactly once, and the
+per-rank partial energies (oracle) all-reduce to the single-rank energy."""
+import os
+import socket
+
+import numpy as np
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import oracle
+import synth
+from paper_2506_12501_gb300 import opcount, shard
+
+
+def _quartets():
+    basis = synth.molecule_basis(natom=2, radius=1.5, seed=3)
+    pairs, batches = synth.all_unique_quartets(basis)
+    shells, costs = [], []
+    for cls, (bra, ket, q) in batches.items():
+        qs = synth.quartet_shells(bra, ket, q)
+        for s in qs:
+            Kb = basis.shell_K[s[0]] * basis.shell_K[s[1]]
+            Kk = basis.shell_K[s[2]] * basis.shell_K[s[3]]
+            costs.append(opcount.sparse_flops(cls, int(Kb), int(Kk)))
+        shells.append(qs)
+    return basis, np.concatenate(shells), np.asarray(costs, dtype=np.float64)
+
+
+def _energy(basis, shells, D):
+    off = np.concatenate([[0], np.cumsum((basis.shell_l + 1) * (basis.shell_l + 2) // 2)[:-1]])
+    vals = oracle.eri_quartets(basis, shells, prec="d")
+    e, pos = 0.0, 0
+    for a, b, c, d in shells:
+        n = [(basis.shell_l[x] + 1) * (basis.shell_l[x] + 2) // 2 for x in (a, b, c, d)]
+        blk = vals[pos:pos + np.prod(n)].reshape(n)
+        pos += int(np.prod(n))
+        Dab = D[off[a]:off[a] + n[0], off[b]:off[b] + n[1]]
+        Dcd = D[off[c]:off[c] + n[2], off[d]:off[d] + n[3]]
+        e += float(np.einsum("abcd,ab,cd->", blk, Dab, Dcd))
+    return e
+
+
+def test_partition_balanced_and_complete():
+    costs = np.random.default_rng(0).lognormal(0, 2, 5000)
+    parts = shard.partition(costs, 4)
+    allidx = np.sort(np.concatenate(parts))
+    assert np.array_equal(allidx, np.arange(5000))
+    loads = [costs[p].sum() for p in parts]
+    assert max(loads) - min(loads) <= costs.max()
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        basis, shells, costs = _quartets()
+        nbf = int(((basis.shell_l + 1) * (basis.shell_l + 2) // 2).sum())
+        U = np.random.default_rng(1).uniform(-1, 1, (nbf, nbf))
+        D = np.triu(U) + np.triu(U, 1).T
+        mine = shard.partition(costs, world)[rank]
+        part = _energy(basis, shells[mine], D)
+        out[rank] = (shard.allreduce_sum(part, dist), len(mine), _energy(basis, shells, D) if rank == 0 else None)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_energy_equals_single_rank():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    out = mp.get_context("spawn").Manager().dict()
+    mp.start_processes(_worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    total, single = out[0][0], out[0][2]
+    assert out[0][0] == out[1][0]
+    assert abs(total - single) <= 1e-12 * max(1.0, abs(single))
+    assert out[0][1] > 0 and out[1][1] > 0
