@@ -341,6 +341,7 @@ def run_library(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees only the timed steps
         t_wall = time.perf_counter()
         for _ in range(args.steps):
             flush.fill_(1.0)  # L2 flush between timed steps (outside the step events)
@@ -352,6 +353,7 @@ def run_library(args):
             step_events.append((s0, s1))
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+        torch.cuda.profiler.stop()
     n_launch = eri.eri_launch_count() - n_launch0
     prof = eri.eri_profile_read()
     eri.eri_profile_enable(False)

@@ -67,25 +67,66 @@ def prim_quartet_flops(L: int) -> int:
     return 17 + 26 + 3 * L + 2 * (L + 1) + r_recursion_flops(L)
 
 
-def swapped(cls, Kbra: int, Kket: int) -> bool:
-    """The library's choice of transform order: the sides are swapped when the
-    swapped order needs fewer operations in the two transforms."""
+def terms_hrr(l1: int, l2: int) -> int:
+    """nonzero terms of E_{e,0} over the functions e with l1 <= |e| <= l1 + l2"""
+    return sum(math.prod(e[i] + 1 for i in range(3)) for l in range(l1, l1 + l2 + 1) for e in carts(l))
+
+
+def ncols_hrr(l1: int, l2: int) -> int:
+    return sum(nc(l) for l in range(l1, l1 + l2 + 1))
+
+
+def hrr_steps(l1: int, l2: int) -> int:
+    """FMA steps of the horizontal recursion building (l1 l2| from (e0|"""
+    return sum(nc(j) * sum(nc(l) for l in range(l1, l1 + l2 - j + 1)) for j in range(1, l2 + 1))
+
+
+def _form(cls, hrr: bool):
+    """(rows, cols, bra terms, ket terms, HRR FMAs per quartet) of one form"""
     la, lb, lc, ld = cls
-    n = Kbra * Kket * nh(la + lb) * terms(lc, ld) + Kbra * nc(lc) * nc(ld) * terms(la, lb)
-    s = Kbra * Kket * nh(lc + ld) * terms(la, lb) + Kket * nc(la) * nc(lb) * terms(lc, ld)
-    return s < n
+    if not hrr:
+        return nc(la) * nc(lb), nc(lc) * nc(ld), terms(la, lb), terms(lc, ld), 0
+    rows, cols = ncols_hrr(la, lb), ncols_hrr(lc, ld)
+    return rows, cols, terms_hrr(la, lb), terms_hrr(lc, ld), rows * hrr_steps(lc, ld) + nc(lc) * nc(ld) * hrr_steps(la, lb)
 
 
-def sparse_flops(cls, Kbra: int, Kket: int, orient: str = "auto") -> int:
-    """orient: 'auto' (the library's choice), 'as-is' (ket transformed first)."""
-    if orient == "auto" and swapped(cls, Kbra, Kket):
+def choice(cls, Kbra: int, Kket: int, allow_hrr: bool = True):
+    """The library's choice of form for eri_batch: (swapped, hrr), the cheapest
+    by the same cost model (transform terms, half an operation per R entry,
+    the recursions), the horizontal-recursion form only when its (f0|e0)
+    accumulators fit (rows * cols <= 4096)."""
+    best, best_cost = None, None
+    for o in range(4 if allow_hrr else 2):
+        sw, hrr = bool(o & 1), o >= 2
+        c = (cls[2], cls[3], cls[0], cls[1]) if sw else cls
+        kb, kk = (Kket, Kbra) if sw else (Kbra, Kket)
+        rows, cols, tb, tk, hs = _form(c, hrr)
+        if hrr and rows * cols > 4096:
+            continue
+        L = sum(c)
+        cost = kb * kk * (nh(c[0] + c[1]) * tk + 0.5 * nh(L)) + kb * cols * tb + hs
+        if best is None or cost < best_cost:
+            best, best_cost = (sw, hrr), cost
+    return best
+
+
+def swapped(cls, Kbra: int, Kket: int) -> bool:
+    return choice(cls, Kbra, Kket)[0]
+
+
+def sparse_flops(cls, Kbra: int, Kket: int, orient: str = "auto", allow_hrr: bool = True) -> int:
+    """FP64 flops of the form the library runs (orient='auto'), or of the
+    ket-first plain form (orient='as-is')."""
+    sw, hrr = choice(cls, Kbra, Kket, allow_hrr) if orient == "auto" else (False, False)
+    if sw:
         cls = (cls[2], cls[3], cls[0], cls[1])
         Kbra, Kket = Kket, Kbra
     la, lb, lc, ld = cls
     L = la + lb + lc + ld
-    ket = 2 * nh(la + lb) * terms(lc, ld)                            # per primitive quartet
-    bra = 2 * nc(lc) * nc(ld) * terms(la, lb) + nc(la) * nc(lb) * nc(lc) * nc(ld)  # per bra primitive
-    return Kbra * Kket * (prim_quartet_flops(L) + ket) + Kbra * bra
+    rows, cols, tb, tk, hs = _form(cls, hrr)
+    ket = 2 * nh(la + lb) * tk                       # per primitive quartet
+    bra = 2 * cols * tb + rows * cols                # per bra primitive
+    return Kbra * Kket * (prim_quartet_flops(L) + ket) + Kbra * bra + 2 * hs
 
 
 def dense_flops(cls, Kbra: int, Kket: int) -> int:
