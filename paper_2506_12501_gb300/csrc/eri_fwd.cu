@@ -107,6 +107,7 @@ struct PairArgs {
     int eax;
     double* zz;             // [npairs][KS][2]: the two exponents
     int split;              // 1: E products stored as float pairs (hi, lo) in the double slots
+    int hrr;                // 1: terms of E_{e,0}, |e| = l1..l1+l2 (horizontal-recursion form)
 };
 
 constexpr int kEax = (kLmax + 3) * (kLmax + 3) * (2 * kLmax + 5);  // per-axis E table bound (adjoint shifts)
@@ -152,7 +153,9 @@ __global__ void pair_kernel(PairArgs a)
         // 1 on y and z: the products E^x E^y E^z are unchanged.
         const double e00x = a.coefs[p1] * a.coefs[p2] * exp(-z1 * z2 * invp * AB2);
         const int ext = a.ax ? 2 : 0;
-        const int m1 = a.l1 + ext, m2 = a.l2 + ext;          // largest raised indices
+        // largest raised indices: the adjoint raises both by 2; the
+        // horizontal-recursion form needs E_{i,0} for i <= l1 + l2
+        const int m1 = a.hrr ? a.l1 + a.l2 : a.l1 + ext, m2 = a.hrr ? 0 : a.l2 + ext;
         const int L12 = a.l1 + a.l2, n2 = m2 + 1, nt = m1 + m2 + 1;
         double E[3][kEax];
         for (int x = 0; x < 3; ++x) {
@@ -181,7 +184,7 @@ __global__ void pair_kernel(PairArgs a)
                     }
         }
         double* Eout = a.E + (size_t)j * a.T * a.KS + s;  // term t at Eout[t * KS]
-        const int ntc = L12 + 1, n2c = a.l2 + 1;  // dims the class-table indices use
+        const int ntc = L12 + 1, n2c = a.hrr ? 1 : a.l2 + 1;  // dims the class-table indices use
         for (int t = 0; t < a.T; ++t) {
             int idx[3], lq = 0;
             for (int x = 0; x < 3; ++x) {
@@ -276,13 +279,18 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     tp->o_Ek = take((size_t)TQ * tp->sEkS);
     tp->o_Pb = take((size_t)TQ * KB * PS_N);
     tp->o_Pk = take((size_t)TQ * KK * PS_N);
-    tp->o_R = take((size_t)TQ * IC * KK * ct.nhl);
+    size_t r_need = (size_t)TQ * IC * KK * ct.nhl;
+    if (ct.hrr)  // the recursion buffers of the epilogue reuse this region
+        r_need = std::max(r_need, (size_t)TQ * ((size_t)ct.nab * ct.ncd + (size_t)ct.nab * ct.nkI +
+                                               (size_t)ct.ncd_f * ct.nbI));
+    tp->o_R = take(r_need);
     tp->o_X = take((size_t)TQ * ct.nhb * ct.ncd);
     const size_t tab_bytes = 4 * (ct.nab + ct.ncd + 2) + 2 * (ct.Tab + ct.Tcd + ct.nhb * ct.nhk);
     tp->o_tab = take((tab_bytes + 7) / 8);
     tp->o_q = take((size_t)TQ * 2);
     tp->bytes = off * 8;
     tp->acc_regs = (TQ * ct.nab * ct.ncd <= kNT * kNACC) ? 1 : 0;
+    if (ct.hrr && !tp->acc_regs) return false;
     return tp->bytes <= (size_t)max_smem_optin();
 }
 
@@ -377,18 +385,42 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
     *KB = kmax[0] * kmax[1];
     *KK = kmax[2] * kmax[3];
     if (allow_swap) {
-        // Transform first the side whose transform is cheaper (Section 3.2.2
-        // transforms the ket first, assuming it has the lower l): compare the
-        // FP64 work of the two orders with the sparse term counts.
-        const ClassTables* c2 = get_class_tables(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
-        if (!c2) return err;
-        const double kb = *KB, kk = *KK;
-        const double cost_n = kb * kk * ct->nhb * ct->Tcd + kb * ct->ncd * ct->Tab;
-        const double cost_s = kb * kk * c2->nhb * c2->Tcd + kk * c2->ncd * c2->Tab;
-        if (cost_s < cost_n) {
+        // Pick the cheapest of four forms by their FP64 work: which side is
+        // transformed first (Section 3.2.2 transforms the ket first, assuming
+        // it has the lower l) and whether the transforms run on (e0) functions
+        // followed by horizontal recursions in the contracted basis.
+        const ClassTables* opt[4] = {ct, get_class_tables(cls.lc, cls.ld, cls.la, cls.lb, st, &err), nullptr, nullptr};
+        if (!opt[1]) return err;
+        if (allow_swap > 1) {
+            opt[2] = get_class_tables_hrr(cls.la, cls.lb, cls.lc, cls.ld, st, &err);
+            opt[3] = get_class_tables_hrr(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
+            if (!opt[2] || !opt[3]) return err;
+        }
+        int best = 0;
+        double best_cost = 0;
+        for (int o = 0; o < 4; ++o) {
+            const ClassTables* c = opt[o];
+            if (!c) continue;
+            const double kb = (o & 1) ? *KK : *KB, kk = (o & 1) ? *KB : *KK;
+            if (c->hrr) {
+                // (f0|e0) must fit the register accumulators and the
+                // recursion buffers of the epilogue the shared memory
+                TilePlan tp;
+                if (c->nab * c->ncd > kNT * kNACC ||
+                    !plan_tiles(*c, (int)kb, (int)kk, quartets ? nq : nbra * nket, &tp))
+                    continue;
+            }
+            const double cost = kb * kk * (c->nhb * c->Tcd + 0.5 * c->nhl) + kb * c->ncd * c->Tab +
+                                (c->hrr ? c->nab * c->nks + c->ncd_f * c->nbs : 0);
+            if (o == 0 || cost < best_cost) {
+                best = o;
+                best_cost = cost;
+            }
+        }
+        ct = opt[best];
+        *ct_out = ct;
+        if (best & 1) {
             *swapped = 1;
-            ct = c2;
-            *ct_out = c2;
             cls = eri_class_t{cls.lc, cls.ld, cls.la, cls.lb};
             std::swap(bra, ket);
             std::swap(nbra, nket);
@@ -449,6 +481,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         p.eax = t.eax;
         p.zz = t.zz;
         p.split = split;
+        p.hrr = ct->hrr;
         const int64_t tot = p.npairs * p.KS;
         const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
         ProfScope ps(PROF_PAIR, st);
@@ -505,14 +538,14 @@ static void set_tile(FwdArgs& a, const TilePlan& tp)
     a.o_q = tp.o_q;
 }
 
-// Autotuner of eri_batch: on the first large batch of a (class, K_bra, K_ket,
-// precision) signature, time every feasible tile shape (TQ in 1..128 with
+// Autotuner of eri_batch: on the first large batch of a (class, form, K_bra,
+// K_ket, precision) signature, time every feasible tile shape (TQ in 1..128 with
 // register accumulation, IC in {K_bra, K_bra/2, 1}, E staged when it fits)
 // on the batch's first kTuneQuartets quartets and remember the fastest.  The
 // trial launches write (part of) `out`; the real launch overwrites it.
 constexpr int64_t kTuneMinQuartets = 16384;
 constexpr int64_t kTuneQuartets = 8192;
-static std::map<std::tuple<int, int, int, int, int, int, int, int>, TilePlan> g_tuned;
+static std::map<std::tuple<int, int, int, int, int, int, int, int, int>, TilePlan> g_tuned;
 static std::mutex g_tuned_mu;
 
 static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cudaStream_t st, TilePlan* best)
@@ -520,7 +553,7 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
     int dev = 0;
     cudaGetDevice(&dev);
     const ClassTables& ct = base.ct;
-    const auto key = std::make_tuple(dev, ct.la, ct.lb, ct.lc, ct.ld, base.KB, base.KK, split);
+    const auto key = std::make_tuple(dev, ct.la, ct.lb, ct.lc, ct.ld, ct.hrr, base.KB, base.KK, split);
     {
         std::lock_guard<std::mutex> lk(g_tuned_mu);
         auto it = g_tuned.find(key);
@@ -622,7 +655,7 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     int swapped = 0;
     const int split = precision == ERI_PREC_SPLIT;
     err = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB, &KK,
-                        kmax, 1, &swapped, split);
+                        kmax, 2, &swapped, split);
     if (err != ERI_OK) return err;
     const double* boys = get_boys_table(ct->L, st, &err);
     if (!boys) return err;
@@ -646,9 +679,13 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     a.nbra = nbra;  // original roles: output layout and product-form decoding
     a.nket = nket;
     a.swap = swapped;
-    a.nab_o = swapped ? ct->ncd : ct->nab;
-    a.ncd_o = swapped ? ct->nab : ct->ncd;
+    a.nab_o = swapped ? ct->ncd_f : ct->nab_f;
+    a.ncd_o = swapped ? ct->nab_f : ct->ncd_f;
     a.out = out;
+    a.bra_sh = swapped ? ket_pairs : bra_pairs;  // the kernel's lists
+    a.ket_sh = swapped ? bra_pairs : ket_pairs;
+    a.centres = basis->centres;
+    a.shell_atom = basis->shell_atom;
     a.TQ = tp.TQ;
     a.KB = KB;
     a.KK = KK;
@@ -770,8 +807,8 @@ int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, 
     a.nbra = nbra;
     a.nket = nket;
     a.swap = 0;
-    a.nab_o = ct.nab;
-    a.ncd_o = ct.ncd;
+    a.nab_o = ct.nab_f;
+    a.ncd_o = ct.ncd_f;
     a.out = out;
     a.TQ = tp.TQ;
     a.KB = KB;

@@ -61,6 +61,22 @@ struct ClassTables {
     const int16_t* pq2b;          // [nhb2][nhk] Hermite index of p'+q
     const int16_t* pq2k;          // [nhb][nhk2] Hermite index of p+q'
     const int16_t* herm3;         // [(t*H + u)*H + v] Hermite index, H = kLtotMax+1
+    // Horizontal-recursion form (hrr = 1): the transforms produce (f0|e0)
+    // with f over the Cartesians of orders la..la+lb on A and e over lc..lc+ld
+    // on C (nab, ncd above then count f and e; the term lists are those of
+    // E_{f,0} and E_{e,0}); after the contraction the recursions
+    //   (c, d+1_i) = (c+1_i, d) + (C_i - D_i) (c, d)   on every f row,
+    //   (a, b+1_i) = (a+1_i, b) + (A_i - B_i) (a, b)   on every (cd) column
+    // give (ab|cd).  Steps: dst, src1, src2, axis over an intermediate index
+    // space whose first nab (bra) / ncd (ket) entries are the (f0)/(e0) values.
+    int hrr;
+    int nab_f, ncd_f;             // final component-pair counts
+    int nbI, nkI;                 // intermediates per column (bra) / per row (ket)
+    int nbs, nks;                 // number of steps
+    const int16_t* bsteps;        // [nbs][4]
+    const int16_t* ksteps;        // [nks][4]
+    const int16_t* bout;          // [nab_f] intermediate index of (a, b)
+    const int16_t* kout;          // [ncd_f] intermediate index of (c, d)
 };
 
 // Primitive-pair scalars written by the pair kernel.
@@ -72,6 +88,7 @@ enum { DEV_OK = 0, DEV_ECLASS = 1, DEV_EINDEX = 2, DEV_EK = 3, DEV_ETIMEOUT = 4 
 // Host helpers implemented in eri_tables.cu
 struct HostClassTables;
 const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t s, int* err);
+const ClassTables* get_class_tables_hrr(int la, int lb, int lc, int ld, cudaStream_t s, int* err);
 const double* get_boys_table(int L, cudaStream_t s, int* err);    // rows of F_{L+k}(T_j)/k!, plus exp
 const double* get_boys_master(cudaStream_t s, int* err);          // rows of F_0..F_kBoysMtab and exp
 const RStep* get_rsteps(cudaStream_t s, int* err);                 // recursion step table (device)

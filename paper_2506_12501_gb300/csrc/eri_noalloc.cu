@@ -188,6 +188,8 @@ static void class_tables(eri_class_t c, const uint8_t* dev_blob, ClassTables* t)
     t->nab = host_nc(c.la) * host_nc(c.lb);
     t->ncd = host_nc(c.lc) * host_nc(c.ld);
     t->nhb = host_nh(t->Lb); t->nhk = host_nh(t->Lk); t->nhl = host_nh(t->L);
+    t->nab_f = t->nab;
+    t->ncd_f = t->ncd;
     t->Tab = terms_of(c.la, c.lb, h_blob.bstart, h_blob.bp, h_blob.bfac);
     t->Tcd = terms_of(c.lc, c.ld, h_blob.kstart, h_blob.kq, h_blob.kfac);
     for (int p = 0; p < t->nhb; ++p)

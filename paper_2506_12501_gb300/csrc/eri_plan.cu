@@ -516,8 +516,8 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
             a.nbra = nbp;
             a.nket = (int64_t)qk.size();
             a.swap = 0;
-            a.nab_o = ct->nab;
-            a.ncd_o = ct->ncd;
+            a.nab_o = ct->nab_f;
+            a.ncd_o = ct->ncd_f;
             a.out = reinterpret_cast<double*>((size_t)J.out_off);  // offset, rebased by the kernel
             a.TQ = tp.TQ;
             a.KB = KB;

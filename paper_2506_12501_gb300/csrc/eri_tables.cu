@@ -116,15 +116,67 @@ struct ClassEntry {
     ClassTables t;
     void* blob = nullptr;
 };
-static std::map<std::tuple<int, int, int, int, int>, ClassEntry> g_classes;
+static std::map<std::tuple<int, int, int, int, int, int>, ClassEntry> g_classes;
 static std::mutex g_class_mu;
 
+// Horizontal-recursion steps of one side (l1, l2): intermediate index space
+// = level 0 (the (e,0) functions, |e| = l1..l1+l2, in term-list order), then
+// levels j = 1..l2 of (c', d') with |d'| = j, |c'| = l1..l1+l2-j.
+struct HrrSide {
+    std::vector<int16_t> steps;  // [n][4]
+    std::vector<int16_t> out;    // [nc(l1) nc(l2)]
+    int nI = 0;
+};
+
+static HrrSide hrr_side(int l1, int l2)
+{
+    HrrSide h;
+    std::map<std::array<int, 6>, int> idx;
+    int n = 0;
+    for (int l = l1; l <= l1 + l2; ++l)
+        for (auto& e : carts(l)) idx[{e[0], e[1], e[2], 0, 0, 0}] = n++;
+    for (int j = 1; j <= l2; ++j)
+        for (int l = l1; l <= l1 + l2 - j; ++l)
+            for (auto& c : carts(l))
+                for (auto& d : carts(j)) {
+                    const std::array<int, 6> key{c[0], c[1], c[2], d[0], d[1], d[2]};
+                    int ax = 0;
+                    while (d[ax] == 0) ++ax;
+                    std::array<int, 6> s1 = key, s2 = key;
+                    s1[ax] += 1;      // (c + 1_ax, d - 1_ax)
+                    s1[3 + ax] -= 1;
+                    s2[3 + ax] -= 1;  // (c, d - 1_ax)
+                    idx[key] = n;
+                    h.steps.push_back((int16_t)n);
+                    h.steps.push_back((int16_t)idx.at(s1));
+                    h.steps.push_back((int16_t)idx.at(s2));
+                    h.steps.push_back((int16_t)ax);
+                    ++n;
+                }
+    for (auto& c : carts(l1))
+        for (auto& d : carts(l2)) h.out.push_back((int16_t)idx.at({c[0], c[1], c[2], d[0], d[1], d[2]}));
+    h.nI = n;
+    return h;
+}
+
+static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int hrr, cudaStream_t s, int* err);
+
 const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t s, int* err)
+{
+    return class_tables_impl(la, lb, lc, ld, 0, s, err);
+}
+
+const ClassTables* get_class_tables_hrr(int la, int lb, int lc, int ld, cudaStream_t s, int* err)
+{
+    return class_tables_impl(la, lb, lc, ld, 1, s, err);
+}
+
+static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int hrr, cudaStream_t s, int* err)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_class_mu);
-    auto key = std::make_tuple(dev, la, lb, lc, ld);
+    auto key = std::make_tuple(dev, la, lb, lc, ld, hrr);
     auto it = g_classes.find(key);
     if (it != g_classes.end()) return &it->second.t;
 
@@ -152,11 +204,47 @@ const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t
                 start.push_back((int)herm.size());
             }
     };
+    // E_{e,0} terms of the functions e with l1 <= |e| <= l1+l2 (table dims
+    // (l1+l2+1) x 1 x (l1+l2+1)), in the order of the HRR level 0
+    auto build_terms_hrr = [](int l1, int l2, std::vector<int>& start, std::vector<int16_t>& herm,
+                              std::vector<uint8_t>& fac) {
+        const int L12 = l1 + l2;
+        start.push_back(0);
+        for (int l = l1; l <= L12; ++l)
+            for (auto& e : carts(l)) {
+                for (int tx = 0; tx <= e[0]; ++tx)
+                    for (int ty = 0; ty <= e[1]; ++ty)
+                        for (int tz = 0; tz <= e[2]; ++tz) {
+                            herm.push_back((int16_t)herm_index(tx, ty, tz));
+                            const int tt[3] = {tx, ty, tz};
+                            for (int i = 0; i < 3; ++i) fac.push_back((uint8_t)(e[i] * (L12 + 1) + tt[i]));
+                        }
+                start.push_back((int)herm.size());
+            }
+    };
     std::vector<int> bs, ks;
     std::vector<int16_t> bp, kq, pq;
     std::vector<uint8_t> bf, kf;
-    build_terms(la, lb, bs, bp, bf);
-    build_terms(lc, ld, ks, kq, kf);
+    if (hrr) {
+        build_terms_hrr(la, lb, bs, bp, bf);
+        build_terms_hrr(lc, ld, ks, kq, kf);
+        t.hrr = 1;
+        t.nab_f = t.nab;
+        t.ncd_f = t.ncd;
+        t.nab = (int)bs.size() - 1;
+        t.ncd = (int)ks.size() - 1;
+    } else {
+        build_terms(la, lb, bs, bp, bf);
+        build_terms(lc, ld, ks, kq, kf);
+        t.hrr = 0;
+        t.nab_f = t.nab;
+        t.ncd_f = t.ncd;
+    }
+    HrrSide hb = hrr_side(la, lb), hk = hrr_side(lc, ld);
+    t.nbI = hb.nI;
+    t.nkI = hk.nI;
+    t.nbs = (int)hb.steps.size() / 4;
+    t.nks = (int)hk.steps.size() / 4;
     t.Tab = (int)bp.size();
     t.Tcd = (int)kq.size();
     auto sum_table = [](int n1, int n2, std::vector<int16_t>& out) {
@@ -193,6 +281,8 @@ const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t
     size_t o_bs = take(bs.size() * 4), o_ks = take(ks.size() * 4);
     size_t o_bp = take(bp.size() * 2), o_kq = take(kq.size() * 2), o_pq = take(pq.size() * 2);
     size_t o_pq2b = take(pq2b.size() * 2), o_pq2k = take(pq2k.size() * 2), o_h3 = take(h3.size() * 2);
+    size_t o_bst = take(hb.steps.size() * 2 + 2), o_kst = take(hk.steps.size() * 2 + 2);
+    size_t o_bo = take(hb.out.size() * 2), o_ko = take(hk.out.size() * 2);
     size_t o_bf = take(bf.size()), o_kf = take(kf.size());
     std::vector<uint8_t> host(off);
     std::memcpy(host.data() + o_bs, bs.data(), bs.size() * 4);
@@ -203,6 +293,10 @@ const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t
     std::memcpy(host.data() + o_pq2b, pq2b.data(), pq2b.size() * 2);
     std::memcpy(host.data() + o_pq2k, pq2k.data(), pq2k.size() * 2);
     std::memcpy(host.data() + o_h3, h3.data(), h3.size() * 2);
+    if (!hb.steps.empty()) std::memcpy(host.data() + o_bst, hb.steps.data(), hb.steps.size() * 2);
+    if (!hk.steps.empty()) std::memcpy(host.data() + o_kst, hk.steps.data(), hk.steps.size() * 2);
+    std::memcpy(host.data() + o_bo, hb.out.data(), hb.out.size() * 2);
+    std::memcpy(host.data() + o_ko, hk.out.data(), hk.out.size() * 2);
     std::memcpy(host.data() + o_bf, bf.data(), bf.size());
     std::memcpy(host.data() + o_kf, kf.data(), kf.size());
     void* blob = nullptr;
@@ -225,6 +319,10 @@ const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t
     t.pq2b = (const int16_t*)(b + o_pq2b);
     t.pq2k = (const int16_t*)(b + o_pq2k);
     t.herm3 = (const int16_t*)(b + o_h3);
+    t.bsteps = (const int16_t*)(b + o_bst);
+    t.ksteps = (const int16_t*)(b + o_kst);
+    t.bout = (const int16_t*)(b + o_bo);
+    t.kout = (const int16_t*)(b + o_ko);
     t.bra_fac = b + o_bf;
     t.ket_fac = b + o_kf;
     ClassEntry& e = g_classes[key];

@@ -72,6 +72,9 @@ struct FwdArgs {
     const int32_t* bf_off;    // [nshell] first Cartesian function of each shell
     const int32_t* bra_sh;    // kernel's bra pairs as shell indices [nbra][2]
     const int32_t* ket_sh;    // kernel's ket pairs [nket][2]
+    // horizontal-recursion form: A-B and C-D from the shell centres
+    const double* centres;
+    const int32_t* shell_atom;
 };
 
 struct Strided {
@@ -384,17 +387,67 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     if (a.acc_regs) {
         const int nC = TQ * nab * ncd;
         double esum = 0.0;
+        if (!ct.hrr) {
 #pragma unroll
-        for (int s = 0; s < kNACC; ++s) {
-            const int item = tid + s * kNT;
-            if (item < nC) {
-                const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
-                if (q < nqt) {
-                    if (a.energy)
-                        esum = fma(acc[s], digest_weight(a, s_q[4 * q], s_q[4 * q + 1], ab, cd), esum);
-                    else
-                        a.out[out_index(a, q0 + q, ab, cd)] = acc[s];
+            for (int s = 0; s < kNACC; ++s) {
+                const int item = tid + s * kNT;
+                if (item < nC) {
+                    const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
+                    if (q < nqt) {
+                        if (a.energy)
+                            esum = fma(acc[s], digest_weight(a, s_q[4 * q], s_q[4 * q + 1], ab, cd), esum);
+                        else
+                            a.out[out_index(a, q0 + q, ab, cd)] = acc[s];
+                    }
                 }
+            }
+        } else {
+            // horizontal recursions on the contracted (f0|e0): rows (ket), then
+            // columns (bra); the buffers reuse the auxiliary-integral region
+            double* sY = sm + a.o_R;                             // [f][e][q]
+            double* sI = sY + (size_t)TQ * nab * ncd;            // [f][q][nkI]
+            double* sJ = sI + (size_t)TQ * nab * ct.nkI;         // [cd][q][nbI]
+#pragma unroll
+            for (int s = 0; s < kNACC; ++s) {
+                const int item = tid + s * kNT;
+                if (item < nC) sY[item] = acc[s];
+            }
+            __syncthreads();
+            for (int item = tid; item < TQ * nab; item += kNT) {
+                const int q = item % TQ, f = item / TQ;
+                double* I = sI + (size_t)item * ct.nkI;
+                for (int e = 0; e < ncd; ++e) I[e] = sY[((size_t)f * ncd + e) * TQ + q];
+                const int k = s_q[4 * q + 1];
+                const double* C = a.centres + 3 * a.shell_atom[a.ket_sh[2 * k]];
+                const double* D = a.centres + 3 * a.shell_atom[a.ket_sh[2 * k + 1]];
+                const double CD[3] = {C[0] - D[0], C[1] - D[1], C[2] - D[2]};
+                for (int st = 0; st < ct.nks; ++st) {
+                    const int16_t* s4 = ct.ksteps + 4 * st;
+                    I[s4[0]] = fma(CD[s4[3]], I[s4[2]], I[s4[1]]);
+                }
+            }
+            __syncthreads();
+            for (int item = tid; item < TQ * ct.ncd_f; item += kNT) {
+                const int q = item % TQ, cdf = item / TQ;
+                double* J = sJ + (size_t)item * ct.nbI;
+                const int kq = ct.kout[cdf];
+                for (int f = 0; f < nab; ++f) J[f] = sI[((size_t)f * TQ + q) * ct.nkI + kq];
+                const int b = s_q[4 * q];
+                const double* A = a.centres + 3 * a.shell_atom[a.bra_sh[2 * b]];
+                const double* B = a.centres + 3 * a.shell_atom[a.bra_sh[2 * b + 1]];
+                const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+                for (int st = 0; st < ct.nbs; ++st) {
+                    const int16_t* s4 = ct.bsteps + 4 * st;
+                    J[s4[0]] = fma(AB[s4[3]], J[s4[2]], J[s4[1]]);
+                }
+                if (q < nqt)
+                    for (int ab = 0; ab < ct.nab_f; ++ab) {
+                        const double v = J[ct.bout[ab]];
+                        if (a.energy)
+                            esum = fma(v, digest_weight(a, b, s_q[4 * q + 1], ab, cdf), esum);
+                        else
+                            a.out[out_index(a, q0 + q, ab, cdf)] = v;
+                    }
             }
         }
         if (a.energy) {
