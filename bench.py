@@ -277,11 +277,15 @@ def run_variants(args, eri, dev):
     info = plan.info()
     e = torch.zeros(1, dtype=torch.float64, device=dev)
     t_exec = timed(lambda: plan.execute(D=Dm, energy=e), reps=2)
+    J = torch.empty_like(Dm)
+    t_j = timed(lambda: plan.coulomb(Dm, J), reps=2)
     out["batched"] = {"workload": f"{args.molecule_natom} atoms (s x3 K=6,3,1, p x2 K=3,1, d K=1), Schwarz 1e-12, "
                                   "energy digestion, one persistent graph-captured launch",
                       "quartets": info["nquartets"], "jobs": info["njobs"], "work_items": info["nitems"],
                       "create_s": t_create, "execute_ms": t_exec,
                       "quartets_per_s": info["nquartets"] / (t_exec / 1e3), "energy": float(e.item()),
+                      "coulomb_ms": t_j, "coulomb_quartets_per_s": info["nquartets"] / (t_j / 1e3),
+                      "coulomb_trace_DJ": float((Dm * J).sum().item()),
                       "status": plan.status()}
     plan.destroy()
     return out
@@ -314,9 +318,9 @@ def run_library(args):
         outs[cls] = torch.empty(eri.out_len(cls, bra.shape[0], ket.shape[0], q.shape[0]), dtype=torch.float64,
                                 device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    sparse = {c: opcount.sparse_flops(c, K_PER_SHELL ** 2, K_PER_SHELL ** 2) for c in batches}
     dense = {c: opcount.dense_flops(c, K_PER_SHELL ** 2, K_PER_SHELL ** 2) for c in batches}
     stream = torch.cuda.current_stream()
+    forms = {}
 
     def step(timing=None):
         for cls, (b, k, q) in dev_batches.items():
@@ -325,6 +329,7 @@ def run_library(args):
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
             eri.eri_batch(cls, db, b, k, q, out=outs[cls])
+            forms[cls] = eri.eri_last_form()
             if timing is not None:
                 e1.record(stream)
                 timing[cls].append((e0, e1))
@@ -332,6 +337,8 @@ def run_library(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # the FP64 operations of the form each class runs (chosen during warm-up)
+    sparse = {c: opcount.sparse_flops(c, K_PER_SHELL ** 2, K_PER_SHELL ** 2, form=forms[c]) for c in batches}
     eri.eri_profile_read()
     eri.eri_profile_enable(True)
     timing = {c: [] for c in batches}
@@ -370,6 +377,7 @@ def run_library(args):
         qps = nq_class / (ms / 1e3)
         per_class["".join(map(str, cls))] = {
             "ms": round(ms, 4), "quartets_per_s": qps,
+            "form": ("swapped " if forms[cls][0] else "") + ("hrr" if forms[cls][1] else "plain"),
             "gflops_sparse": sparse[cls] * qps / 1e9, "gflops_dense": dense[cls] * qps / 1e9,
             "frac_fp64_peak_sparse": sparse[cls] * qps / 1e9 / FP64_PEAK_GFLOPS,
             "frac_fp64_peak_dense": dense[cls] * qps / 1e9 / FP64_PEAK_GFLOPS}

@@ -199,6 +199,13 @@ int eri_batch_noalloc(eri_class_t cls, const eri_basis_t* basis,
  * NULL.  With ERI_PLAN_STORE it writes the integrals to `out` (out_len >=
  * eri_plan_info's out_len): job j (see eri_plan_job) at offset out_off, in
  * the list-form layout of eri_batch for its own class and quartet order.
+ * eri_plan_coulomb -- the same replay digesting into the Coulomb matrix:
+ * J[u][v] = sum over all (l, s) of (uv|ls) D[l][s] for every Cartesian
+ * function pair (u, v) of the basis, each unique screened quartet standing
+ * for its distinct images under the 8 permutations of its indices (J is
+ * overwritten, [nbf][nbf] device, symmetric).  D must be symmetric.  This
+ * is a consumer of the integrals in the sense of Section 3.1: no integral is
+ * stored.  Plans created with ERI_PLAN_STORE return ERI_EPLAN.
  * eri_plan_set_budget -- bound each CTA of later executions to `cycles`
  * SM clock cycles (0 = no bound); a CTA over budget stops taking work and
  * the execution reports ERI_ETIMEOUT through eri_plan_status, which
@@ -214,12 +221,41 @@ typedef struct eri_plan eri_plan_t;
 int eri_plan_create(const eri_basis_t* basis, double threshold, int flags, void* stream, eri_plan_t** plan);
 int eri_plan_execute(eri_plan_t* plan, const double* D, int32_t nbf, double* energy,
                      double* out, int64_t out_len, void* stream);
+int eri_plan_coulomb(eri_plan_t* plan, const double* D, int32_t nbf, double* J, void* stream);
 int eri_plan_set_budget(eri_plan_t* plan, int64_t cycles);
 int eri_plan_status(eri_plan_t* plan, void* stream);
 int eri_plan_info(eri_plan_t* plan, int64_t* nquartets, int32_t* njobs, int64_t* nitems, int64_t* out_len);
 int eri_plan_job(eri_plan_t* plan, int32_t job, eri_class_t* cls, int64_t* nq, int64_t* out_off,
                  int32_t* quartet_shells);
 int eri_plan_destroy(eri_plan_t* plan);
+
+/*
+ * eri_last_form -- the form the calling thread's last successful eri_batch
+ * launch ran (measurement support: operation counts depend on it).
+ * *swapped = 1 when the kernel took the caller's ket as the side it
+ * transforms last; *hrr = 1 when the transforms ran on the (e0| functions
+ * with l_a <= |e| <= l_a + l_b (and likewise |f0) on the other side),
+ * followed by the horizontal recursions (a, b + 1_i) = (a + 1_i, b) +
+ * (A_i - B_i)(a, b) on the contracted integrals.  The form is chosen by an
+ * operation-count model, or, from the first batch of at least 16384
+ * quartets of a (class, K_bra, K_ket, precision) signature on, by timing the
+ * cheapest plain and recursion forms on that batch.  Both arguments are HOST
+ * pointers.  Returns ERI_EINVAL before the thread's first eri_batch launch.
+ * The paper transforms the ket first and has no recursion form (Section 3.2.2).
+ */
+int eri_last_form(int32_t* swapped, int32_t* hrr);
+
+/*
+ * eri_set_forms -- restrict the forms later eri_batch calls (all threads)
+ * may choose from: bit 0 plain, bit 1 plain with the sides swapped, bit 2
+ * recursion form, bit 3 recursion form swapped; 0 restores all four.  A
+ * class for which no allowed form is feasible uses the feasible ones.
+ * Returns the previous mask, or ERI_EINVAL for a mask outside 0..15.  For
+ * tests and measurements of one form; the results agree to round-off.
+ */
+#define ERI_FORM_PLAIN 0x3
+#define ERI_FORM_HRR 0xC
+int eri_set_forms(int32_t mask);
 
 /*
  * eri_last_status -- synchronises `stream` and returns ERI_OK or the first

@@ -17,6 +17,9 @@ from .binding import (  # noqa: F401
     ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE,
     ERI_NOALLOC_SCRATCH_BYTES,
     eri_last_status,
+    eri_last_form,
+    eri_set_forms,
+    ERI_FORM_PLAIN, ERI_FORM_HRR,
     eri_finalize,
     eri_profile_enable,
     eri_profile_read,

@@ -43,9 +43,10 @@ class eri_basis_t(ctypes.Structure):
 EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
            "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc", "eri_plan_create",
            "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
-           "eri_plan_destroy"]
+           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
+ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
 PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS = 0, 1, 2, 3
 
 
@@ -62,6 +63,8 @@ def lib() -> ctypes.CDLL:
             L.eri_batch_grad.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P, I64,
                                          P, P, P]
             L.eri_last_status.argtypes = [P]
+            L.eri_last_form.argtypes = [P, P]
+            L.eri_set_forms.argtypes = [ctypes.c_int32]
             L.eri_error_string.argtypes = [I]
             L.eri_error_string.restype = ctypes.c_char_p
             L.eri_finalize.argtypes = []
@@ -70,6 +73,7 @@ def lib() -> ctypes.CDLL:
             L.eri_batch_noalloc.restype = I
             L.eri_plan_create.argtypes = [ctypes.POINTER(eri_basis_t), ctypes.c_double, I, P, ctypes.POINTER(P)]
             L.eri_plan_execute.argtypes = [P, P, ctypes.c_int32, P, P, I64, P]
+            L.eri_plan_coulomb.argtypes = [P, P, ctypes.c_int32, P, P]
             L.eri_plan_set_budget.argtypes = [P, I64]
             L.eri_plan_status.argtypes = [P, P]
             L.eri_plan_info.argtypes = [P, P, P, P, P]
@@ -195,6 +199,22 @@ def eri_last_status(stream=None) -> int:
     return lib().eri_last_status(_stream(stream))
 
 
+def eri_set_forms(mask: int) -> int:
+    """Restrict eri_batch's forms (ERI_FORM_PLAIN, ERI_FORM_HRR, or 0 = all); returns the previous mask."""
+    code = lib().eri_set_forms(int(mask))
+    if code < 0:
+        _check(code, "eri_set_forms")
+    return code
+
+
+def eri_last_form() -> tuple:
+    """(swapped, hrr) of this thread's last eri_batch launch."""
+    sw = ctypes.c_int32()
+    hrr = ctypes.c_int32()
+    _check(lib().eri_last_form(ctypes.byref(sw), ctypes.byref(hrr)), "eri_last_form")
+    return bool(sw.value), bool(hrr.value)
+
+
 def eri_finalize() -> int:
     return lib().eri_finalize()
 
@@ -269,6 +289,14 @@ class Plan:
         nbf = D.shape[0] if D is not None else 0
         _check(lib().eri_plan_execute(self.ptr, _ptr(D), nbf, _ptr(energy), _ptr(out),
                                       out.numel() if out is not None else 0, _stream(stream)), "eri_plan_execute")
+
+    def coulomb(self, D: torch.Tensor, J: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """J_uv = sum_ls (uv|ls) D_ls over every quartet of the plan and its permutation images."""
+        D = D.contiguous()
+        if J is None:
+            J = torch.empty_like(D)
+        _check(lib().eri_plan_coulomb(self.ptr, _ptr(D), D.shape[0], _ptr(J), _stream(stream)), "eri_plan_coulomb")
+        return J
 
     def set_budget(self, cycles: int):
         _check(lib().eri_plan_set_budget(self.ptr, int(cycles)), "eri_plan_set_budget")

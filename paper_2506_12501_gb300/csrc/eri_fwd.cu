@@ -20,6 +20,7 @@
 //     then coalesced stores of the quartet-fastest output.
 // Every FP64 operation of the path runs in these kernels.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -262,6 +263,19 @@ int max_smem_optin()
 // ---------------------------------------------------------------------------
 static int odd_up(int n) { return n | 1; }
 
+// Ping-pong buffers of the epilogue's horizontal recursions: level g of the
+// combined sequence (ket levels 0..ld, then bra levels 1..lb) lives in
+// buffer g % 2; *A and *B are the largest even and odd level (doubles).
+static void hrr_buffers(const ClassTables& ct, int TQ, size_t* A, size_t* B)
+{
+    *A = *B = 0;
+    for (int g = 0; g <= ct.ld + ct.lb; ++g) {
+        const size_t n = g <= ct.ld ? (size_t)TQ * ct.nab * ct.kn[g] : (size_t)TQ * ct.ncd_f * ct.bn[g - ct.ld];
+        size_t& m = (g & 1) ? *B : *A;
+        m = std::max(m, n);
+    }
+}
+
 bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp)
 {
     size_t off = 0;
@@ -270,24 +284,44 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
         off += (nd + 1) & ~size_t(1);  // keep 16-byte alignment
         return (int)o;
     };
+    auto even = [](size_t nd) { return (nd + 1) & ~size_t(1); };
     tp->TQ = TQ;
     tp->IC = IC;
     tp->e_smem = e_smem;
     tp->sEbS = e_smem ? odd_up(KB * ct.Tab) : 0;
     tp->sEkS = e_smem ? odd_up(KK * ct.Tcd) : 0;
+    size_t r_need = (size_t)TQ * IC * KK * ct.nhl;
+    size_t hA = 0, hB = 0;
+    if (ct.hrr) {
+        // the recursion buffers alias every staging region before the tables
+        // (E, pair scalars, R, X are dead in the epilogue); grow R if short
+        hrr_buffers(ct, TQ, &hA, &hB);
+        const size_t staged = even((size_t)TQ * tp->sEbS) + even((size_t)TQ * tp->sEkS) +
+                              even((size_t)TQ * KB * PS_N) + even((size_t)TQ * KK * PS_N) + even(r_need) +
+                              even((size_t)TQ * ct.nhb * ct.ncd);
+        const size_t need = even(hA) + even(hB);
+        if (staged < need) r_need += need - staged;
+    }
+    {
+        // the Coulomb digestion of plans stages the tile's values there too
+        const size_t staged = even((size_t)TQ * tp->sEbS) + even((size_t)TQ * tp->sEkS) +
+                              even((size_t)TQ * KB * PS_N) + even((size_t)TQ * KK * PS_N) + even(r_need) +
+                              even((size_t)TQ * ct.nhb * ct.ncd);
+        const size_t need = even((size_t)TQ * ct.nab * ct.ncd);
+        if (TQ * ct.nab * ct.ncd <= kNT * kNACC && staged < need) r_need += need - staged;
+    }
     tp->o_Eb = take((size_t)TQ * tp->sEbS);
     tp->o_Ek = take((size_t)TQ * tp->sEkS);
     tp->o_Pb = take((size_t)TQ * KB * PS_N);
     tp->o_Pk = take((size_t)TQ * KK * PS_N);
-    size_t r_need = (size_t)TQ * IC * KK * ct.nhl;
-    if (ct.hrr)  // the recursion buffers of the epilogue reuse this region
-        r_need = std::max(r_need, (size_t)TQ * ((size_t)ct.nab * ct.ncd + (size_t)ct.nab * ct.nkI +
-                                               (size_t)ct.ncd_f * ct.nbI));
     tp->o_R = take(r_need);
     tp->o_X = take((size_t)TQ * ct.nhb * ct.ncd);
+    tp->o_hB = (int)even(hA);
     const size_t tab_bytes = 4 * (ct.nab + ct.ncd + 2) + 2 * (ct.Tab + ct.Tcd + ct.nhb * ct.nhk);
     tp->o_tab = take((tab_bytes + 7) / 8);
     tp->o_q = take((size_t)TQ * 2);
+    tp->o_geo = take(ct.hrr ? (size_t)TQ * 6 : 0);
+    tp->o_dj = take((size_t)TQ + ct.nab_f);
     tp->bytes = off * 8;
     tp->acc_regs = (TQ * ct.nab * ct.ncd <= kNT * kNACC) ? 1 : 0;
     if (ct.hrr && !tp->acc_regs) return false;
@@ -351,16 +385,48 @@ static size_t align_up(size_t n) { return (n + 255) & ~size_t(255); }
 
 // Prepass + pair tables shared by the forward and adjoint entry points.
 // On success fills the pair tables and the largest K on each centre.
+// Forms eri_batch may use (eri_set_forms): bit o allows form o.
+static std::atomic<int> g_form_mask{0xF};
+
+// Forms chosen by timing, per (device, class, K_bra, K_ket, precision).
+static std::map<std::tuple<int, int, int, int, int, int, int, int>, int> g_forms;
+static std::mutex g_forms_mu;
+
+static std::tuple<int, int, int, int, int, int, int, int> form_key(eri_class_t cls, int KB, int KK, int split)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return std::make_tuple(dev, cls.la, cls.lb, cls.lc, cls.ld, KB, KK, split);
+}
+
+static int lookup_form(eri_class_t cls, int KB, int KK, int split)
+{
+    std::lock_guard<std::mutex> lk(g_forms_mu);
+    auto it = g_forms.find(form_key(cls, KB, KK, split));
+    return it == g_forms.end() ? -1 : it->second;
+}
+
+void remember_form(eri_class_t cls, int KB, int KK, int split, int form)
+{
+    std::lock_guard<std::mutex> lk(g_forms_mu);
+    g_forms[form_key(cls, KB, KK, split)] = form;
+}
+
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
-                  int allow_swap, int* swapped, int split)
+                  int allow_swap, FormChoice* fc, int split)
 {
     int err = ERI_OK;
     const ClassTables* ct = get_class_tables(cls.la, cls.lb, cls.lc, cls.ld, st, &err);
     if (!ct) return err;
     *ct_out = ct;
-    if (swapped) *swapped = 0;
+    const int forced = fc ? fc->form : -1;
+    if (fc) {
+        fc->form = 0;
+        fc->alt = -1;
+        fc->cached = 0;
+    }
     int* status = device_status();
     if (!status) return ERI_ECUDA;
     int32_t* hinfo = host_pinned_i32(8);
@@ -385,10 +451,11 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
     *KB = kmax[0] * kmax[1];
     *KK = kmax[2] * kmax[3];
     if (allow_swap) {
-        // Pick the cheapest of four forms by their FP64 work: which side is
-        // transformed first (Section 3.2.2 transforms the ket first, assuming
-        // it has the lower l) and whether the transforms run on (e0) functions
-        // followed by horizontal recursions in the contracted basis.
+        // Four forms: which side is transformed first (Section 3.2.2
+        // transforms the ket first, assuming it has the lower l) and whether
+        // the transforms run on (e0) functions followed by horizontal
+        // recursions in the contracted basis.  The FP64-work model picks one
+        // unless a form is forced or an earlier timing chose one.
         const ClassTables* opt[4] = {ct, get_class_tables(cls.lc, cls.ld, cls.la, cls.lb, st, &err), nullptr, nullptr};
         if (!opt[1]) return err;
         if (allow_swap > 1) {
@@ -396,9 +463,10 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
             opt[3] = get_class_tables_hrr(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
             if (!opt[2] || !opt[3]) return err;
         }
-        int best = 0;
-        double best_cost = 0;
+        const int64_t nqq = quartets ? nq : nbra * nket;
+        double cost[4];
         for (int o = 0; o < 4; ++o) {
+            cost[o] = -1.0;  // infeasible
             const ClassTables* c = opt[o];
             if (!c) continue;
             const double kb = (o & 1) ? *KK : *KB, kk = (o & 1) ? *KB : *KK;
@@ -406,21 +474,45 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
                 // (f0|e0) must fit the register accumulators and the
                 // recursion buffers of the epilogue the shared memory
                 TilePlan tp;
-                if (c->nab * c->ncd > kNT * kNACC ||
-                    !plan_tiles(*c, (int)kb, (int)kk, quartets ? nq : nbra * nket, &tp))
-                    continue;
+                if (c->nab * c->ncd > kNT * kNACC || !plan_tiles(*c, (int)kb, (int)kk, nqq, &tp)) continue;
             }
-            const double cost = kb * kk * (c->nhb * c->Tcd + 0.5 * c->nhl) + kb * c->ncd * c->Tab +
-                                (c->hrr ? c->nab * c->nks + c->ncd_f * c->nbs : 0);
-            if (o == 0 || cost < best_cost) {
-                best = o;
-                best_cost = cost;
+            cost[o] = kb * kk * (c->nhb * c->Tcd + 0.5 * c->nhl) + kb * c->ncd * c->Tab +
+                      (c->hrr ? c->nab * c->nks + c->ncd_f * c->nbs : 0);
+        }
+        {
+            // the caller's form mask (eri_set_forms), unless it leaves no feasible form
+            const int mask = g_form_mask.load();
+            bool any = false;
+            for (int o = 0; o < 4; ++o) any |= cost[o] >= 0 && (mask >> o & 1);
+            if (any)
+                for (int o = 0; o < 4; ++o)
+                    if (!(mask >> o & 1)) cost[o] = -1.0;
+        }
+        auto cheapest = [&](int lo, int hi) {
+            int b = -1;
+            for (int o = lo; o < hi; ++o)
+                if (cost[o] >= 0 && (b < 0 || cost[o] < cost[b])) b = o;
+            return b;
+        };
+        int best = -1;
+        if (forced >= 0) {
+            if (forced > 3 || cost[forced] < 0) return ERI_EINVAL;
+            best = forced;
+        } else {
+            best = lookup_form(cls, *KB, *KK, split);
+            if (best >= 0 && cost[best] >= 0) {
+                if (fc) fc->cached = 1;
+            } else {
+                best = cheapest(0, 4);
             }
+        }
+        if (fc) {
+            fc->form = best;
+            fc->alt = best >= 2 ? cheapest(0, 2) : cheapest(2, 4);
         }
         ct = opt[best];
         *ct_out = ct;
         if (best & 1) {
-            *swapped = 1;
             cls = eri_class_t{cls.lc, cls.ld, cls.la, cls.lb};
             std::swap(bra, ket);
             std::swap(nbra, nket);
@@ -520,35 +612,20 @@ int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* b
     return ERI_OK;
 }
 
-static void set_tile(FwdArgs& a, const TilePlan& tp)
-{
-    a.TQ = tp.TQ;
-    a.IC = tp.IC;
-    a.e_smem = tp.e_smem;
-    a.acc_regs = tp.acc_regs;
-    a.sEbS = tp.sEbS;
-    a.sEkS = tp.sEkS;
-    a.o_Eb = tp.o_Eb;
-    a.o_Ek = tp.o_Ek;
-    a.o_Pb = tp.o_Pb;
-    a.o_Pk = tp.o_Pk;
-    a.o_R = tp.o_R;
-    a.o_X = tp.o_X;
-    a.o_tab = tp.o_tab;
-    a.o_q = tp.o_q;
-}
-
 // Autotuner of eri_batch: on the first large batch of a (class, form, K_bra,
 // K_ket, precision) signature, time every feasible tile shape (TQ in 1..128 with
 // register accumulation, IC in {K_bra, K_bra/2, 1}, E staged when it fits)
-// on the batch's first kTuneQuartets quartets and remember the fastest.  The
-// trial launches write (part of) `out`; the real launch overwrites it.
+// on the batch's leading quartets (about four waves of tiles, at least
+// kTuneQuartets) and remember the fastest with its time per quartet
+// (eri_batch compares forms by it).  The trial launches write (part
+// of) `out`; the real launch overwrites it.
 constexpr int64_t kTuneMinQuartets = 16384;
 constexpr int64_t kTuneQuartets = 8192;
-static std::map<std::tuple<int, int, int, int, int, int, int, int, int>, TilePlan> g_tuned;
+static std::map<std::tuple<int, int, int, int, int, int, int, int, int>, std::pair<TilePlan, float>> g_tuned;
 static std::mutex g_tuned_mu;
 
-static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cudaStream_t st, TilePlan* best)
+static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cudaStream_t st, TilePlan* best,
+                       float* best_ms_out)
 {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -558,7 +635,8 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
         std::lock_guard<std::mutex> lk(g_tuned_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            *best = it->second;
+            *best = it->second.first;
+            *best_ms_out = it->second.second;
             return true;
         }
     }
@@ -577,22 +655,24 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
             }
         }
     }
-    if (cands.size() < 2) return false;
+    if (cands.empty()) return false;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int64_t nq = std::min(base.nq, kTuneQuartets);
-    double best_ms = 1e300;
+    float best_ms = 3e38f;  // per quartet
     bool ok = false;
     for (const TilePlan& tp : cands) {
         FwdArgs a = base;
         set_tile(a, tp);
-        a.ntiles = (nq + tp.TQ - 1) / tp.TQ;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
             continue;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, tp.bytes);
-        const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)std::max(per_sm, 1) * sm_count());
+        const int64_t slots = (int64_t)std::max(per_sm, 1) * sm_count();
+        // about four waves of tiles (steady state), at least kTuneQuartets quartets
+        const int64_t nq = std::min(base.nq, std::max(kTuneQuartets, 4 * slots * tp.TQ));
+        a.ntiles = (nq + tp.TQ - 1) / tp.TQ;
+        const int64_t grid = std::min<int64_t>(a.ntiles, slots);
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, st);
@@ -604,6 +684,7 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
             cudaGetLastError();
             continue;
         }
+        ms /= (float)nq;
         if (ms < best_ms) {
             best_ms = ms;
             *best = tp;
@@ -614,7 +695,8 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
     cudaEventDestroy(e1);
     if (ok) {
         std::lock_guard<std::mutex> lk(g_tuned_mu);
-        g_tuned[key] = *best;
+        g_tuned[key] = std::make_pair(*best, best_ms);
+        *best_ms_out = best_ms;
     }
     return ok;
 }
@@ -638,6 +720,50 @@ extern "C" int eri_boys(int mmax, const double* T, int64_t n, double* F, void* s
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
 }
 
+// Kernel arguments of one forward batch in form fc (the pair tables pb, pk
+// of that form are built); the tile shape from the planner.
+static int forward_args(const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
+                        const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nqq, double* out,
+                        const ClassTables* ct, const PairTables& pb, const PairTables& pk, int KB, int KK, int swapped,
+                        cudaStream_t st, FwdArgs* a, TilePlan* tp)
+{
+    int err = ERI_OK;
+    const double* boys = get_boys_table(ct->L, st, &err);
+    if (!boys) return err;
+    const RStep* rs = get_rsteps(st, &err);
+    if (!rs) return err;
+    if (!plan_tiles(*ct, KB, KK, nqq, tp)) return ERI_EINVAL;
+    *a = FwdArgs{};
+    a->ct = *ct;
+    a->boys = boys;
+    a->rsteps = rs;
+    a->bra_ps = pb.ps;
+    a->bra_E = pb.E;
+    a->bra_kp = pb.kp;
+    a->ket_ps = pk.ps;
+    a->ket_E = pk.E;
+    a->ket_kp = pk.kp;
+    a->quartets = quartets;
+    a->nq = nqq;
+    a->nbra = nbra;  // original roles: output layout and product-form decoding
+    a->nket = nket;
+    a->swap = swapped;
+    a->nab_o = swapped ? ct->ncd_f : ct->nab_f;
+    a->ncd_o = swapped ? ct->nab_f : ct->ncd_f;
+    a->out = out;
+    a->bra_sh = swapped ? ket_pairs : bra_pairs;  // the kernel's lists
+    a->ket_sh = swapped ? bra_pairs : ket_pairs;
+    a->centres = basis->centres;
+    a->shell_atom = basis->shell_atom;
+    a->KB = KB;
+    a->KK = KK;
+    set_tile(*a, *tp);
+    a->ntiles = (nqq + tp->TQ - 1) / tp->TQ;
+    return ERI_OK;
+}
+
+static thread_local int g_last_form = -1;
+
 extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
                          const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq, double* out,
                          int64_t out_len, int precision, void* stream)
@@ -649,64 +775,58 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     if (nqq == 0 || nbra == 0 || nket == 0) return ERI_OK;
     if (!out) return ERI_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    const int split = precision == ERI_PREC_SPLIT;
+    void (*kern)(FwdArgs) = split ? fwd_kernel_split : fwd_kernel;
     const ClassTables* ct = nullptr;
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
-    int swapped = 0;
-    const int split = precision == ERI_PREC_SPLIT;
-    err = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB, &KK,
-                        kmax, 2, &swapped, split);
-    if (err != ERI_OK) return err;
-    const double* boys = get_boys_table(ct->L, st, &err);
-    if (!boys) return err;
-    const RStep* rs = get_rsteps(st, &err);
-    if (!rs) return err;
+    FormChoice fc;
+    auto prepare = [&](FormChoice* f, FwdArgs* a, TilePlan* tp) {
+        int e = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB,
+                              &KK, kmax, 2, f, split);
+        if (e != ERI_OK) return e;
+        return forward_args(basis, bra_pairs, nbra, ket_pairs, nket, quartets, nqq, out, ct, pb, pk, KB, KK,
+                            f->form & 1, st, a, tp);
+    };
+    FwdArgs a;
     TilePlan tp;
-    if (!plan_tiles(*ct, KB, KK, nqq, &tp)) return ERI_EINVAL;
-    void (*kern)(FwdArgs) = split ? fwd_kernel_split : fwd_kernel;
-    FwdArgs a{};
-    a.ct = *ct;
-    a.boys = boys;
-    a.rsteps = rs;
-    a.bra_ps = pb.ps;
-    a.bra_E = pb.E;
-    a.bra_kp = pb.kp;
-    a.ket_ps = pk.ps;
-    a.ket_E = pk.E;
-    a.ket_kp = pk.kp;
-    a.quartets = quartets;
-    a.nq = nqq;
-    a.nbra = nbra;  // original roles: output layout and product-form decoding
-    a.nket = nket;
-    a.swap = swapped;
-    a.nab_o = swapped ? ct->ncd_f : ct->nab_f;
-    a.ncd_o = swapped ? ct->nab_f : ct->ncd_f;
-    a.out = out;
-    a.bra_sh = swapped ? ket_pairs : bra_pairs;  // the kernel's lists
-    a.ket_sh = swapped ? bra_pairs : ket_pairs;
-    a.centres = basis->centres;
-    a.shell_atom = basis->shell_atom;
-    a.TQ = tp.TQ;
-    a.KB = KB;
-    a.KK = KK;
-    a.IC = tp.IC;
-    a.e_smem = tp.e_smem;
-    a.acc_regs = tp.acc_regs;
-    a.sEbS = tp.sEbS;
-    a.sEkS = tp.sEkS;
-    a.o_Eb = tp.o_Eb;
-    a.o_Ek = tp.o_Ek;
-    a.o_Pb = tp.o_Pb;
-    a.o_Pk = tp.o_Pk;
-    a.o_R = tp.o_R;
-    a.o_X = tp.o_X;
-    a.o_tab = tp.o_tab;
-    a.o_q = tp.o_q;
-    a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
-    // large batches: tile shape from the autotuner (cached per class and signature)
+    err = prepare(&fc, &a, &tp);
+    if (err != ERI_OK) return err;
+    // large batches: tile shape from the autotuner (cached per kernel class,
+    // form and signature); on the first such batch of a signature, the
+    // cheapest plain and horizontal-recursion forms are both timed on the
+    // batch's own leading quartets and the faster is remembered
     if (nqq >= kTuneMinQuartets) {
         TilePlan best;
-        if (tuned_tile(a, kern, split, st, &best)) {
+        float ms = 0.f;
+        bool tuned = tuned_tile(a, kern, split, st, &best, &ms);
+        if (!fc.cached && fc.alt >= 0) {
+            const eri_class_t sig = cls;
+            const int KB0 = (fc.form & 1) ? KK : KB, KK0 = (fc.form & 1) ? KB : KK;  // caller's orientation
+            FormChoice f1;
+            f1.form = fc.alt;
+            FwdArgs a1;
+            TilePlan tp1, best1;
+            float ms1 = 0.f;
+            bool tuned1 = false;
+            if (prepare(&f1, &a1, &tp1) == ERI_OK) tuned1 = tuned_tile(a1, kern, split, st, &best1, &ms1);
+            const bool take_alt = tuned1 && (!tuned || ms1 < ms);
+            remember_form(sig, KB0, KK0, split, take_alt ? f1.form : fc.form);
+            if (take_alt) {
+                fc = f1;
+                a = a1;
+                tp = tp1;
+                best = best1;
+                tuned = tuned1;
+            } else {
+                // rebuild the pair tables of the first form (the workspace was reused)
+                FormChoice f0;
+                f0.form = fc.form;
+                err = prepare(&f0, &a, &tp);
+                if (err != ERI_OK) return err;
+            }
+        }
+        if (tuned) {
             tp = best;
             set_tile(a, tp);
             a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
@@ -722,7 +842,24 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
         ProfScope ps(PROF_FWD, st);
         kern<<<(int)grid, kNT, tp.bytes, st>>>(a);
     }
-    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+    g_last_form = fc.form;
+    return ERI_OK;
+}
+
+extern "C" int eri_set_forms(int32_t mask)
+{
+    if (mask < 0 || mask > 0xF) return ERI_EINVAL;
+    return g_form_mask.exchange(mask ? mask : 0xF);
+}
+
+extern "C" int eri_last_form(int32_t* swapped, int32_t* hrr)
+{
+    if (!swapped || !hrr) return ERI_EINVAL;
+    if (g_last_form < 0) return ERI_EINVAL;
+    *swapped = g_last_form & 1;
+    *hrr = (g_last_form >> 1) & 1;
+    return ERI_OK;
 }
 
 namespace eri {
@@ -810,22 +947,9 @@ int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, 
     a.nab_o = ct.nab_f;
     a.ncd_o = ct.ncd_f;
     a.out = out;
-    a.TQ = tp.TQ;
     a.KB = KB;
     a.KK = KK;
-    a.IC = tp.IC;
-    a.e_smem = tp.e_smem;
-    a.acc_regs = tp.acc_regs;
-    a.sEbS = tp.sEbS;
-    a.sEkS = tp.sEkS;
-    a.o_Eb = tp.o_Eb;
-    a.o_Ek = tp.o_Ek;
-    a.o_Pb = tp.o_Pb;
-    a.o_Pk = tp.o_Pk;
-    a.o_R = tp.o_R;
-    a.o_X = tp.o_X;
-    a.o_tab = tp.o_tab;
-    a.o_q = tp.o_q;
+    set_tile(a, tp);
     a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
     if (cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
         return ERI_ECUDA;

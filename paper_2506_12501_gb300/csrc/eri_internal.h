@@ -67,16 +67,17 @@ struct ClassTables {
     // E_{f,0} and E_{e,0}); after the contraction the recursions
     //   (c, d+1_i) = (c+1_i, d) + (C_i - D_i) (c, d)   on every f row,
     //   (a, b+1_i) = (a+1_i, b) + (A_i - B_i) (a, b)   on every (cd) column
-    // give (ab|cd).  Steps: dst, src1, src2, axis over an intermediate index
-    // space whose first nab (bra) / ncd (ket) entries are the (f0)/(e0) values.
+    // give (ab|cd), one level |d| (|b|) = j at a time.  Level 0 of a side is
+    // its (e0) list in term-list order; level j lists (c, d) with |d| = j and
+    // l1 <= |c| <= l1 + l2 - j, each entry a step (src1, src2, axis) into
+    // level j-1; the last level (j = l2) is in (c, d) component-pair order.
     int hrr;
     int nab_f, ncd_f;             // final component-pair counts
-    int nbI, nkI;                 // intermediates per column (bra) / per row (ket)
-    int nbs, nks;                 // number of steps
-    const int16_t* bsteps;        // [nbs][4]
-    const int16_t* ksteps;        // [nks][4]
-    const int16_t* bout;          // [nab_f] intermediate index of (a, b)
-    const int16_t* kout;          // [ncd_f] intermediate index of (c, d)
+    int nbs, nks;                 // steps over all levels j >= 1
+    int bn[4], kn[4];             // entries of level j (bn[0] = nab, kn[0] = ncd)
+    int boff[4], koff[4];         // first step of level j in bsteps / ksteps
+    const int16_t* bsteps;        // [nbs][3]: src1, src2, axis
+    const int16_t* ksteps;        // [nks][3]
 };
 
 // Primitive-pair scalars written by the pair kernel.
@@ -108,13 +109,24 @@ struct PairTables {
     double* zz;   // adjoint only: [npairs][KS][2] exponents
 };
 
+// Form of a forward batch: bit 0 = sides swapped (the caller's ket is the
+// kernel's bra), bit 1 = horizontal-recursion form.
+struct FormChoice {
+    int form = -1;    // in: a form to force, or -1 (remembered, else modelled); out: the form used
+    int alt = -1;     // out: the modelled-cheapest feasible form of the other kind (plain vs HRR), or -1
+    int cached = 0;   // out: 1 when the form was remembered from an earlier timing
+};
+// Remember the measured-faster form of a (class, K_bra, K_ket, precision) signature.
+void remember_form(eri_class_t cls, int KB, int KK, int split, int form);
+
 // Prepass + pair tables shared by eri_batch and eri_batch_grad.  ldelta > 0
 // also fills the adjoint tables.  Synchronises `st` once (reads the largest
-// contraction degree of each centre).
+// contraction degree of each centre).  allow_swap = 0: the plain form as
+// given; 1: plain or swapped; 2: any of the four forms.
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
-                  int allow_swap, int* swapped, int split = 0);
+                  int allow_swap, FormChoice* fc, int split = 0);
 int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                  int64_t nket, const int64_t* quartets, int64_t nq, double* out, const ClassTables& ct,
                  const double* boys, const RStep* rs, int* dinfo, double* scratch, size_t scratch_doubles,
@@ -129,6 +141,8 @@ struct TilePlan {
     int TQ, IC, e_smem, acc_regs;
     int sEbS, sEkS;
     int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;
+    int o_hB, o_geo;  // horizontal-recursion form: second buffer (the first is at 0), A-B/C-D per quartet
+    int o_dj;         // Coulomb digestion scratch (TQ + nab_f doubles)
     size_t bytes;
 };
 bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best);

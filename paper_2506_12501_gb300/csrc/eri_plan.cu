@@ -21,7 +21,9 @@
 // inter-CTA communication, so nothing waits); it runs the tile body of
 // eri_tile.cuh on each tile of the item and either digests
 //   energy = sum_quartets sum_abcd D_ab D_cd (ab|cd)
-// or stores the integrals (plans created with ERI_PLAN_STORE).  A cycle
+// or the Coulomb matrix J_uv = sum_ls (uv|ls) D_ls (every unique quartet
+// standing for its permutation images; a last kernel symmetrises J), or
+// stores the integrals (plans created with ERI_PLAN_STORE).  A cycle
 // budget (eri_plan_set_budget) bounds the run: a CTA that exceeds it stops
 // popping items and records ERI_ETIMEOUT in the plan's status word.
 #include <algorithm>
@@ -47,6 +49,7 @@ struct PlanParams {
     const double* D;
     int nbf;
     double* energy;
+    double* J;            // Coulomb mode: [nbf][nbf], zeroed, accumulated, then symmetrised
     double* out;          // store mode: base of the plan's output
     int64_t budget;       // clock64 cycles per CTA, 0 = unlimited
     int* counter;
@@ -93,12 +96,34 @@ struct eri_plan {
 
 namespace eri {
 
-__global__ void plan_reset_kernel(PlanParams* p)
+__global__ void plan_reset_kernel(const PlanParams* p)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         p->counter[0] = 0;
         p->status[0] = 0;
         if (p->energy) *p->energy = 0.0;
+    }
+    if (p->J) {
+        const size_t n = (size_t)p->nbf * p->nbf;
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+            p->J[i] = 0.0;
+    }
+}
+
+// J = J' + J'^T in place: each unordered (u, v) by one thread.
+__global__ void plan_finish_kernel(const PlanParams* p)
+{
+    if (!p->J) return;
+    const size_t nbf = (size_t)p->nbf, n = nbf * nbf;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t u = i / nbf, v = i % nbf;
+        if (u < v) {
+            const double t = p->J[u * nbf + v] + p->J[v * nbf + u];
+            p->J[u * nbf + v] = t;
+            p->J[v * nbf + u] = t;
+        } else if (u == v) {
+            p->J[i] *= 2.0;
+        }
     }
 }
 
@@ -136,6 +161,7 @@ __global__ void __launch_bounds__(kNT, 1)
         if (it.job != cur) {
             a = jobs[it.job];
             a.energy = P.energy;
+            a.Jmat = P.J;
             a.D = P.D;
             a.nbf = P.nbf;
             if (P.out) a.out = P.out + (int64_t)(size_t)a.out;  // stored as an offset
@@ -183,24 +209,6 @@ struct TypeTables {
 
 int build_pair_tables_on(const eri_basis_t* basis, const int32_t* d_pairs, int64_t npairs, int l1, int l2, int KS,
                          int T, const uint8_t* fac, int ket, int split, PairTables* out, cudaStream_t st);
-
-static void apply_tile(FwdArgs& a, const TilePlan& tp)
-{
-    a.TQ = tp.TQ;
-    a.IC = tp.IC;
-    a.e_smem = tp.e_smem;
-    a.acc_regs = tp.acc_regs;
-    a.sEbS = tp.sEbS;
-    a.sEkS = tp.sEkS;
-    a.o_Eb = tp.o_Eb;
-    a.o_Ek = tp.o_Ek;
-    a.o_Pb = tp.o_Pb;
-    a.o_Pk = tp.o_Pk;
-    a.o_R = tp.o_R;
-    a.o_X = tp.o_X;
-    a.o_tab = tp.o_tab;
-    a.o_q = tp.o_q;
-}
 
 // Autotuner: time candidate tile shapes of one job on a sample of its own
 // work items (the persistent kernel, digestion into a scratch energy with a
@@ -256,7 +264,7 @@ static bool autotune_job(const FwdArgs& base, const std::vector<WorkItem>& sampl
     bool ok = false;
     for (const TilePlan& tp : cands) {
         FwdArgs a = base;
-        apply_tile(a, tp);
+        set_tile(a, tp);
         cudaMemcpyAsync(d_job, &a, sizeof(a), cudaMemcpyHostToDevice, st);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
             continue;
@@ -519,22 +527,9 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
             a.nab_o = ct->nab_f;
             a.ncd_o = ct->ncd_f;
             a.out = reinterpret_cast<double*>((size_t)J.out_off);  // offset, rebased by the kernel
-            a.TQ = tp.TQ;
             a.KB = KB;
             a.KK = KK;
-            a.IC = tp.IC;
-            a.e_smem = tp.e_smem;
-            a.acc_regs = tp.acc_regs;
-            a.sEbS = tp.sEbS;
-            a.sEkS = tp.sEkS;
-            a.o_Eb = tp.o_Eb;
-            a.o_Ek = tp.o_Ek;
-            a.o_Pb = tp.o_Pb;
-            a.o_Pk = tp.o_Pk;
-            a.o_R = tp.o_R;
-            a.o_X = tp.o_X;
-            a.o_tab = tp.o_tab;
-            a.o_q = tp.o_q;
+            set_tile(a, tp);
             a.mode = 1;
             a.bf_off = d_bf;
             a.bra_sh = d_tpairs[bt];
@@ -570,7 +565,7 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
                 }
             TilePlan best;
             if (autotune_job(J.args, sample, sq, split, zeroD, nbf, scratch, ctr, prm, st, &best)) {
-                apply_tile(J.args, best);
+                set_tile(J.args, best);
                 J.smem = best.bytes;
             }
         }
@@ -614,33 +609,28 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
     return ERI_OK;
 }
 
-extern "C" int eri_plan_execute(eri_plan_t* p, const double* D, int32_t nbf, double* energy, double* out,
-                                int64_t out_len, void* stream)
+// Upload the parameters and replay the plan's graph (captured on the first
+// call: reset, persistent kernel, J symmetrisation; every kernel reads its
+// parameters from d_params, so one graph serves every mode and pointer).
+static int plan_launch(eri_plan_t* p, const PlanParams& prm_in, cudaStream_t st)
 {
-    if (!p) return ERI_EINVAL;
-    const bool store = (p->flags & ERI_PLAN_STORE) != 0;
-    if (store ? (!out || out_len < p->out_len) : (!energy || !D || nbf != p->nbf)) return ERI_EPLAN;
-    if (!store && out) return ERI_EPLAN;
-    cudaStream_t st = (cudaStream_t)stream;
-    PlanParams prm = p->params;
-    prm.D = store ? nullptr : D;
-    prm.nbf = p->nbf;
-    prm.energy = store ? nullptr : energy;
-    prm.out = store ? out : nullptr;
+    PlanParams prm = prm_in;
+    prm.budget = p->params.budget;
     prm.counter = p->d_counter;
     prm.status = p->d_counter + 1;
     p->params = prm;
     if (cudaMemcpyAsync(p->d_params, &p->params, sizeof(PlanParams), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return ERI_ECUDA;
+    const int egrid = 2 * sm_count();
     if (!p->exec) {
-        // capture once: reset + persistent kernel (the parameters are read from d_params)
         cudaStream_t cs;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return ERI_ECUDA;
         auto kern = (p->flags & ERI_PLAN_SPLIT) ? plan_kernel<true> : plan_kernel<false>;
         bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
-            plan_reset_kernel<<<1, 32, 0, cs>>>(p->d_params);
+            plan_reset_kernel<<<egrid, 256, 0, cs>>>(p->d_params);
             kern<<<p->grid, kNT, p->smem, cs>>>(p->d_jobs, p->d_items, p->nitems, p->d_params);
+            plan_finish_kernel<<<egrid, 256, 0, cs>>>(p->d_params);
         }
         cudaGraph_t g = nullptr;
         ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && ok;
@@ -653,8 +643,35 @@ extern "C" int eri_plan_execute(eri_plan_t* p, const double* D, int32_t nbf, dou
     }
     count_launch();
     count_launch();
+    count_launch();
     ProfScope ps(PROF_FWD, st);
     return cudaGraphLaunch(p->exec, st) == cudaSuccess ? ERI_OK : ERI_ECUDA;
+}
+
+extern "C" int eri_plan_execute(eri_plan_t* p, const double* D, int32_t nbf, double* energy, double* out,
+                                int64_t out_len, void* stream)
+{
+    if (!p) return ERI_EINVAL;
+    const bool store = (p->flags & ERI_PLAN_STORE) != 0;
+    if (store ? (!out || out_len < p->out_len) : (!energy || !D || nbf != p->nbf)) return ERI_EPLAN;
+    if (!store && out) return ERI_EPLAN;
+    PlanParams prm{};
+    prm.D = store ? nullptr : D;
+    prm.nbf = p->nbf;
+    prm.energy = store ? nullptr : energy;
+    prm.out = store ? out : nullptr;
+    return plan_launch(p, prm, (cudaStream_t)stream);
+}
+
+extern "C" int eri_plan_coulomb(eri_plan_t* p, const double* D, int32_t nbf, double* J, void* stream)
+{
+    if (!p) return ERI_EINVAL;
+    if ((p->flags & ERI_PLAN_STORE) || !D || !J || nbf != p->nbf) return ERI_EPLAN;
+    PlanParams prm{};
+    prm.D = D;
+    prm.nbf = p->nbf;
+    prm.J = J;
+    return plan_launch(p, prm, (cudaStream_t)stream);
 }
 
 extern "C" int eri_plan_set_budget(eri_plan_t* p, int64_t cycles)

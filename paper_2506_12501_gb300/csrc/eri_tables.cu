@@ -119,23 +119,25 @@ struct ClassEntry {
 static std::map<std::tuple<int, int, int, int, int, int>, ClassEntry> g_classes;
 static std::mutex g_class_mu;
 
-// Horizontal-recursion steps of one side (l1, l2): intermediate index space
-// = level 0 (the (e,0) functions, |e| = l1..l1+l2, in term-list order), then
-// levels j = 1..l2 of (c', d') with |d'| = j, |c'| = l1..l1+l2-j.
+// Horizontal-recursion levels of one side (l1, l2).  Level 0: the (e,0)
+// functions, |e| = l1..l1+l2, in term-list order.  Level j = 1..l2: the
+// pairs (c, d) with |d| = j and l1 <= |c| <= l1+l2-j, c-major, each built from
+// level j-1 as (c + 1_ax, d - 1_ax) + X_ax (c, d - 1_ax), ax the first axis
+// with d_ax > 0.  The last level is therefore in component-pair order.
 struct HrrSide {
-    std::vector<int16_t> steps;  // [n][4]
-    std::vector<int16_t> out;    // [nc(l1) nc(l2)]
-    int nI = 0;
+    std::vector<int16_t> steps;  // [n][3]: src1, src2, axis
+    int n[4] = {0, 0, 0, 0};     // entries per level
+    int off[4] = {0, 0, 0, 0};   // first step of each level
 };
 
 static HrrSide hrr_side(int l1, int l2)
 {
     HrrSide h;
-    std::map<std::array<int, 6>, int> idx;
-    int n = 0;
+    std::vector<std::map<std::array<int, 6>, int>> idx(l2 + 1);
     for (int l = l1; l <= l1 + l2; ++l)
-        for (auto& e : carts(l)) idx[{e[0], e[1], e[2], 0, 0, 0}] = n++;
-    for (int j = 1; j <= l2; ++j)
+        for (auto& e : carts(l)) idx[0][{e[0], e[1], e[2], 0, 0, 0}] = h.n[0]++;
+    for (int j = 1; j <= l2; ++j) {
+        h.off[j] = (int)h.steps.size() / 3;
         for (int l = l1; l <= l1 + l2 - j; ++l)
             for (auto& c : carts(l))
                 for (auto& d : carts(j)) {
@@ -146,16 +148,12 @@ static HrrSide hrr_side(int l1, int l2)
                     s1[ax] += 1;      // (c + 1_ax, d - 1_ax)
                     s1[3 + ax] -= 1;
                     s2[3 + ax] -= 1;  // (c, d - 1_ax)
-                    idx[key] = n;
-                    h.steps.push_back((int16_t)n);
-                    h.steps.push_back((int16_t)idx.at(s1));
-                    h.steps.push_back((int16_t)idx.at(s2));
+                    h.steps.push_back((int16_t)idx[j - 1].at(s1));
+                    h.steps.push_back((int16_t)idx[j - 1].at(s2));
                     h.steps.push_back((int16_t)ax);
-                    ++n;
+                    idx[j][key] = h.n[j]++;
                 }
-    for (auto& c : carts(l1))
-        for (auto& d : carts(l2)) h.out.push_back((int16_t)idx.at({c[0], c[1], c[2], d[0], d[1], d[2]}));
-    h.nI = n;
+    }
     return h;
 }
 
@@ -241,10 +239,14 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
         t.ncd_f = t.ncd;
     }
     HrrSide hb = hrr_side(la, lb), hk = hrr_side(lc, ld);
-    t.nbI = hb.nI;
-    t.nkI = hk.nI;
-    t.nbs = (int)hb.steps.size() / 4;
-    t.nks = (int)hk.steps.size() / 4;
+    t.nbs = (int)hb.steps.size() / 3;
+    t.nks = (int)hk.steps.size() / 3;
+    for (int j = 0; j < 4; ++j) {
+        t.bn[j] = hb.n[j];
+        t.kn[j] = hk.n[j];
+        t.boff[j] = hb.off[j];
+        t.koff[j] = hk.off[j];
+    }
     t.Tab = (int)bp.size();
     t.Tcd = (int)kq.size();
     auto sum_table = [](int n1, int n2, std::vector<int16_t>& out) {
@@ -282,7 +284,6 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
     size_t o_bp = take(bp.size() * 2), o_kq = take(kq.size() * 2), o_pq = take(pq.size() * 2);
     size_t o_pq2b = take(pq2b.size() * 2), o_pq2k = take(pq2k.size() * 2), o_h3 = take(h3.size() * 2);
     size_t o_bst = take(hb.steps.size() * 2 + 2), o_kst = take(hk.steps.size() * 2 + 2);
-    size_t o_bo = take(hb.out.size() * 2), o_ko = take(hk.out.size() * 2);
     size_t o_bf = take(bf.size()), o_kf = take(kf.size());
     std::vector<uint8_t> host(off);
     std::memcpy(host.data() + o_bs, bs.data(), bs.size() * 4);
@@ -295,8 +296,6 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
     std::memcpy(host.data() + o_h3, h3.data(), h3.size() * 2);
     if (!hb.steps.empty()) std::memcpy(host.data() + o_bst, hb.steps.data(), hb.steps.size() * 2);
     if (!hk.steps.empty()) std::memcpy(host.data() + o_kst, hk.steps.data(), hk.steps.size() * 2);
-    std::memcpy(host.data() + o_bo, hb.out.data(), hb.out.size() * 2);
-    std::memcpy(host.data() + o_ko, hk.out.data(), hk.out.size() * 2);
     std::memcpy(host.data() + o_bf, bf.data(), bf.size());
     std::memcpy(host.data() + o_kf, kf.data(), kf.size());
     void* blob = nullptr;
@@ -321,8 +320,6 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
     t.herm3 = (const int16_t*)(b + o_h3);
     t.bsteps = (const int16_t*)(b + o_bst);
     t.ksteps = (const int16_t*)(b + o_kst);
-    t.bout = (const int16_t*)(b + o_bo);
-    t.kout = (const int16_t*)(b + o_ko);
     t.bra_fac = b + o_bf;
     t.ket_fac = b + o_kf;
     ClassEntry& e = g_classes[key];

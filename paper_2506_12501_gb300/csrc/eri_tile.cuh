@@ -61,12 +61,15 @@ struct FwdArgs {
     int e_smem, acc_regs;
     int sEbS, sEkS;           // per-quartet strides of staged E (doubles)
     int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;  // smem offsets (doubles)
+    int o_hB, o_geo;          // horizontal-recursion form: second buffer, A-B and C-D per quartet
+    int o_dj;                 // Coulomb digestion scratch: [TQ] weights, [nab] bra sums
     int64_t ntiles;
     // work-queue mode (plans): one bra pair, consecutive ket pairs
     int mode;                 // 0: list/product batch, 1: ranged (bra rbra, kets rk0..)
     int64_t rbra, rk0, rq0;   // ranged: bra index, first ket index, list index of that quartet
     // digestion (energy = sum W (ab|cd), W_abcd = D_ab D_cd) instead of stores
     double* energy;           // non-null: digest; out is not written
+    double* Jmat;             // non-null (plans): Coulomb digestion into J' [nbf][nbf]; out is not written
     const double* D;          // [nbf][nbf]
     int nbf;
     const int32_t* bf_off;    // [nshell] first Cartesian function of each shell
@@ -76,6 +79,28 @@ struct FwdArgs {
     const double* centres;
     const int32_t* shell_atom;
 };
+
+// Copy a tile shape into the kernel arguments.
+inline void set_tile(FwdArgs& a, const TilePlan& tp)
+{
+    a.TQ = tp.TQ;
+    a.IC = tp.IC;
+    a.e_smem = tp.e_smem;
+    a.acc_regs = tp.acc_regs;
+    a.sEbS = tp.sEbS;
+    a.sEkS = tp.sEkS;
+    a.o_Eb = tp.o_Eb;
+    a.o_Ek = tp.o_Ek;
+    a.o_Pb = tp.o_Pb;
+    a.o_Pk = tp.o_Pk;
+    a.o_R = tp.o_R;
+    a.o_X = tp.o_X;
+    a.o_tab = tp.o_tab;
+    a.o_q = tp.o_q;
+    a.o_hB = tp.o_hB;
+    a.o_geo = tp.o_geo;
+    a.o_dj = tp.o_dj;
+}
 
 struct Strided {
     double* p;
@@ -169,6 +194,64 @@ __device__ __forceinline__ double digest_weight(const FwdArgs& a, int b, int k, 
     const int ia = a.bf_off[a.bra_sh[2 * b]] + ab / ncb, ib = a.bf_off[a.bra_sh[2 * b + 1]] + ab % ncb;
     const int ic = a.bf_off[a.ket_sh[2 * k]] + cd / ncd2, id = a.bf_off[a.ket_sh[2 * k + 1]] + cd % ncd2;
     return a.D[(size_t)ia * a.nbf + ib] * a.D[(size_t)ic * a.nbf + id];
+}
+
+// Coulomb digestion of one tile of a plan work item (one bra pair, the
+// tile's ket pairs).  V[ab][cd][q] (index q + TQ (cd + ncd ab)) holds the
+// tile's contracted integrals.  Every unique shell quartet stands for its
+// distinct images under the 8 index permutations; with s = 1/2 for each of
+// a == b, c == d and (ab) == (cd) (shells), and D symmetric,
+//   J'[a][b] += 2s sum_cd (ab|cd) D[c][d],   J'[c][d] += 2s sum_ab (ab|cd) D[a][b],
+// and J = J' + J'^T afterwards gives J_uv = sum over all (ls) of (uv|ls) D_ls.
+// The bra sums are reduced over the tile in shared memory first (one global
+// atomic per ab), the ket sums take one global atomic per (q, cd).
+static __device__ void digest_coulomb(const FwdArgs& a, const double* V, int nqt, const int* s_q, double* s_dj)
+{
+    const ClassTables& ct = a.ct;
+    const int TQ = a.TQ, nab = ct.nab_f, ncd = ct.ncd_f, tid = threadIdx.x;
+    const int ncb = (ct.lb + 1) * (ct.lb + 2) / 2, ncdd = (ct.ld + 1) * (ct.ld + 2) / 2;
+    double* s_w = s_dj;        // [TQ]
+    double* s_jb = s_dj + TQ;  // [nab]
+    const int b = s_q[0];
+    const int sa = a.bra_sh[2 * b], sb = a.bra_sh[2 * b + 1];
+    const int oa = a.bf_off[sa], ob = a.bf_off[sb];
+    for (int q = tid; q < TQ; q += kNT) {
+        double w = 0.0;
+        if (q < nqt) {
+            const int k = s_q[4 * q + 1];
+            const int sc = a.ket_sh[2 * k], sd = a.ket_sh[2 * k + 1];
+            w = 2.0;
+            if (sa == sb) w *= 0.5;
+            if (sc == sd) w *= 0.5;
+            if ((sa == sc && sb == sd) || (sa == sd && sb == sc)) w *= 0.5;
+        }
+        s_w[q] = w;
+    }
+    for (int i = tid; i < nab; i += kNT) s_jb[i] = 0.0;
+    __syncthreads();
+    for (int item = tid; item < TQ * ncd; item += kNT) {
+        const int q = item % TQ, cd = item / TQ;
+        if (q >= nqt) continue;
+        double sum = 0.0;
+        for (int ab = 0; ab < nab; ++ab)
+            sum = fma(V[q + TQ * (cd + ncd * ab)], a.D[(size_t)(oa + ab / ncb) * a.nbf + ob + ab % ncb], sum);
+        const int k = s_q[4 * q + 1];
+        const int ic = a.bf_off[a.ket_sh[2 * k]] + cd / ncdd, id = a.bf_off[a.ket_sh[2 * k + 1]] + cd % ncdd;
+        atomicAdd(&a.Jmat[(size_t)ic * a.nbf + id], s_w[q] * sum);
+    }
+    for (int item = tid; item < TQ * nab; item += kNT) {
+        const int q = item % TQ, ab = item / TQ;
+        if (q >= nqt) continue;
+        const int k = s_q[4 * q + 1];
+        const int oc = a.bf_off[a.ket_sh[2 * k]], od = a.bf_off[a.ket_sh[2 * k + 1]];
+        double sum = 0.0;
+        for (int cd = 0; cd < ncd; ++cd)
+            sum = fma(V[q + TQ * (cd + ncd * ab)], a.D[(size_t)(oc + cd / ncdd) * a.nbf + od + cd % ncdd], sum);
+        atomicAdd(&s_jb[ab], s_w[q] * sum);
+    }
+    __syncthreads();
+    for (int ab = tid; ab < nab; ab += kNT)
+        atomicAdd(&a.Jmat[(size_t)(oa + ab / ncb) * a.nbf + ob + ab % ncb], s_jb[ab]);
 }
 
 // One tile: quartets q0 .. q0+nqt-1 (the class tables are already staged).
@@ -387,7 +470,16 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     if (a.acc_regs) {
         const int nC = TQ * nab * ncd;
         double esum = 0.0;
-        if (!ct.hrr) {
+        if (!ct.hrr && a.Jmat) {
+            // the values go to shared memory (the staging regions are dead)
+#pragma unroll
+            for (int s = 0; s < kNACC; ++s) {
+                const int item = tid + s * kNT;
+                if (item < nC) sm[item] = acc[s];
+            }
+            __syncthreads();
+            digest_coulomb(a, sm, nqt, s_q, sm + a.o_dj);
+        } else if (!ct.hrr) {
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
                 const int item = tid + s * kNT;
@@ -402,52 +494,68 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 }
             }
         } else {
-            // horizontal recursions on the contracted (f0|e0): rows (ket), then
-            // columns (bra); the buffers reuse the auxiliary-integral region
-            double* sY = sm + a.o_R;                             // [f][e][q]
-            double* sI = sY + (size_t)TQ * nab * ncd;            // [f][q][nkI]
-            double* sJ = sI + (size_t)TQ * nab * ct.nkI;         // [cd][q][nbI]
+            // horizontal recursions on the contracted (f0|e0), one level at a
+            // time over the whole tile, ping-ponging between two buffers that
+            // alias the dead staging regions: ket levels on every f row
+            // ([f][e][q]), then bra levels on every (cd) column ([f][cd][q])
+            double* hbuf[2] = {sm, sm + a.o_hB};
+            double* s_geo = sm + a.o_geo;  // [q][6]: A-B, C-D
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
                 const int item = tid + s * kNT;
-                if (item < nC) sY[item] = acc[s];
+                if (item < nC) hbuf[0][item] = acc[s];
             }
-            __syncthreads();
-            for (int item = tid; item < TQ * nab; item += kNT) {
-                const int q = item % TQ, f = item / TQ;
-                double* I = sI + (size_t)item * ct.nkI;
-                for (int e = 0; e < ncd; ++e) I[e] = sY[((size_t)f * ncd + e) * TQ + q];
-                const int k = s_q[4 * q + 1];
-                const double* C = a.centres + 3 * a.shell_atom[a.ket_sh[2 * k]];
-                const double* D = a.centres + 3 * a.shell_atom[a.ket_sh[2 * k + 1]];
-                const double CD[3] = {C[0] - D[0], C[1] - D[1], C[2] - D[2]};
-                for (int st = 0; st < ct.nks; ++st) {
-                    const int16_t* s4 = ct.ksteps + 4 * st;
-                    I[s4[0]] = fma(CD[s4[3]], I[s4[2]], I[s4[1]]);
-                }
-            }
-            __syncthreads();
-            for (int item = tid; item < TQ * ct.ncd_f; item += kNT) {
-                const int q = item % TQ, cdf = item / TQ;
-                double* J = sJ + (size_t)item * ct.nbI;
-                const int kq = ct.kout[cdf];
-                for (int f = 0; f < nab; ++f) J[f] = sI[((size_t)f * TQ + q) * ct.nkI + kq];
-                const int b = s_q[4 * q];
+            for (int q = tid; q < TQ; q += kNT) {
+                const int b = s_q[4 * q], k = s_q[4 * q + 1];
                 const double* A = a.centres + 3 * a.shell_atom[a.bra_sh[2 * b]];
                 const double* B = a.centres + 3 * a.shell_atom[a.bra_sh[2 * b + 1]];
-                const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-                for (int st = 0; st < ct.nbs; ++st) {
-                    const int16_t* s4 = ct.bsteps + 4 * st;
-                    J[s4[0]] = fma(AB[s4[3]], J[s4[2]], J[s4[1]]);
+                const double* C = a.centres + 3 * a.shell_atom[a.ket_sh[2 * k]];
+                const double* D = a.centres + 3 * a.shell_atom[a.ket_sh[2 * k + 1]];
+                for (int i = 0; i < 3; ++i) {
+                    s_geo[6 * q + i] = A[i] - B[i];
+                    s_geo[6 * q + 3 + i] = C[i] - D[i];
                 }
-                if (q < nqt)
-                    for (int ab = 0; ab < ct.nab_f; ++ab) {
-                        const double v = J[ct.bout[ab]];
-                        if (a.energy)
-                            esum = fma(v, digest_weight(a, b, s_q[4 * q + 1], ab, cdf), esum);
-                        else
-                            a.out[out_index(a, q0 + q, ab, cdf)] = v;
-                    }
+            }
+            __syncthreads();
+            int g = 0;
+            for (int j = 1; j <= ct.ld; ++j, ++g) {
+                const double* src = hbuf[g & 1];
+                double* dst = hbuf[(g + 1) & 1];
+                const int np = ct.kn[j - 1], nn = ct.kn[j];
+                const int16_t* st = ct.ksteps + 3 * ct.koff[j];
+                for (int item = tid; item < TQ * nab * nn; item += kNT) {
+                    const int q = item % TQ, r = item / TQ, o = r % nn, f = r / nn;
+                    const int16_t* s3 = st + 3 * o;
+                    const double* row = src + (size_t)f * np * TQ + q;
+                    dst[item] = fma(s_geo[6 * q + 3 + s3[2]], row[s3[1] * TQ], row[s3[0] * TQ]);
+                }
+                __syncthreads();
+            }
+            const int ncf = ct.ncd_f;
+            for (int j = 1; j <= ct.lb; ++j, ++g) {
+                const double* src = hbuf[g & 1];
+                double* dst = hbuf[(g + 1) & 1];
+                const int16_t* st = ct.bsteps + 3 * ct.boff[j];
+                for (int item = tid; item < TQ * ncf * ct.bn[j]; item += kNT) {
+                    const int q = item % TQ, r = item / TQ, cd = r % ncf, o = r / ncf;
+                    const int16_t* s3 = st + 3 * o;
+                    const double* col = src + (size_t)cd * TQ + q;
+                    dst[item] = fma(s_geo[6 * q + s3[2]], col[(size_t)s3[1] * ncf * TQ], col[(size_t)s3[0] * ncf * TQ]);
+                }
+                __syncthreads();
+            }
+            const double* fin = hbuf[g & 1];  // [ab][cd][q]
+            if (a.Jmat) {
+                digest_coulomb(a, fin, nqt, s_q, sm + a.o_dj);
+            } else {
+                for (int item = tid; item < TQ * ct.nab_f * ncf; item += kNT) {
+                    const int q = item % TQ, r = item / TQ, cd = r % ncf, ab = r / ncf;
+                    if (q >= nqt) continue;
+                    if (a.energy)
+                        esum = fma(fin[item], digest_weight(a, s_q[4 * q], s_q[4 * q + 1], ab, cd), esum);
+                    else
+                        a.out[out_index(a, q0 + q, ab, cd)] = fin[item];
+                }
             }
         }
         if (a.energy) {

@@ -91,8 +91,8 @@ def _form(cls, hrr: bool):
 
 
 def choice(cls, Kbra: int, Kket: int, allow_hrr: bool = True):
-    """The library's choice of form for eri_batch: (swapped, hrr), the cheapest
-    by the same cost model (transform terms, half an operation per R entry,
+    """The library's modelled choice of form for eri_batch (before any timing
+    of forms): (swapped, hrr), the cheapest by the same cost model (transform terms, half an operation per R entry,
     the recursions), the horizontal-recursion form only when its (f0|e0)
     accumulators fit (rows * cols <= 4096)."""
     best, best_cost = None, None
@@ -114,10 +114,14 @@ def swapped(cls, Kbra: int, Kket: int) -> bool:
     return choice(cls, Kbra, Kket)[0]
 
 
-def sparse_flops(cls, Kbra: int, Kket: int, orient: str = "auto", allow_hrr: bool = True) -> int:
-    """FP64 flops of the form the library runs (orient='auto'), or of the
+def sparse_flops(cls, Kbra: int, Kket: int, orient: str = "auto", allow_hrr: bool = True, form=None) -> int:
+    """FP64 flops of one form: `form` = (swapped, hrr) as the library reports
+    it (eri_last_form), else the modelled choice (orient='auto'), else the
     ket-first plain form (orient='as-is')."""
-    sw, hrr = choice(cls, Kbra, Kket, allow_hrr) if orient == "auto" else (False, False)
+    if form is not None:
+        sw, hrr = bool(form[0]), bool(form[1])
+    else:
+        sw, hrr = choice(cls, Kbra, Kket, allow_hrr) if orient == "auto" else (False, False)
     if sw:
         cls = (cls[2], cls[3], cls[0], cls[1])
         Kbra, Kket = Kket, Kbra

@@ -62,6 +62,27 @@ def test_class_sweep_contracted(cuda, sweep_pools, cls):
     assert_close(got, ref, what=str(cls))
 
 
+@pytest.mark.parametrize("cls", synth.all_classes(2))
+def test_every_form_against_oracle(cuda, sweep_pools, cls):
+    """Each of the four forms (plain or side-swapped; full Cartesian pairs or
+    (e0|f0) plus horizontal recursions), forced with eri_set_forms, against
+    the oracle on the same contracted batch."""
+    basis, pools = synth.class_sweep_pools(seed=7, pool=48, K=2)
+    L = sum(cls)
+    nq = 97 if L <= 4 else 29
+    bra, ket, q = synth.class_sweep_batch(pools, cls, seed=8, npairs=40, nq=nq)
+    ref = oracle_blocks(cls, basis, bra, ket, q, prec="d")
+    db = eri.DeviceBasis(basis)
+    try:
+        for form in range(4):
+            eri.eri_set_forms(1 << form)
+            got = gpu_list(cls, basis, bra, ket, q, dbasis=db)
+            assert eri.eri_last_form() == (bool(form & 1), bool(form & 2))
+            assert_close(got, ref, what=f"{cls} form {form}")
+    finally:
+        eri.eri_set_forms(0)
+
+
 @pytest.mark.parametrize("cls", [(0, 0, 0, 0), (1, 0, 1, 0), (2, 1, 1, 0), (2, 2, 2, 2)])
 def test_product_form_layout(cuda, cls):
     """quartets == NULL: every (bra, ket) combination, written in the
@@ -148,11 +169,13 @@ def test_errors_and_degenerate_sizes(cuda):
     assert eri.eri_last_status() == eri.ERI_OK
 
 
-@pytest.mark.parametrize("cls", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 1, 2, 0), (2, 2, 2, 2)])
+@pytest.mark.parametrize("cls", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 1, 2, 0), (2, 0, 1, 2), (1, 1, 1, 2), (2, 2, 2, 2)])
 def test_full_size_sampled(cuda, cls):
     """The class-sweep workload at full size (1e5 quartets per class, pools of
     512 shells, 2048 pairs per side, K = 3), in the launch configuration the
-    benchmark times; 48 sampled quartets against the oracle."""
+    benchmark times (the first call times the cheapest plain and recursion
+    forms and remembers the faster); 48 sampled quartets against the oracle,
+    and a second call runs the remembered form and tile with identical results."""
     basis, pools = synth.class_sweep_pools(seed=0, pool=512, K=3)
     bra, ket, q = synth.class_sweep_batch(pools, cls, seed=0, npairs=2048, nq=100_000)
     db = eri.DeviceBasis(basis)
@@ -166,3 +189,7 @@ def test_full_size_sampled(cuda, cls):
     ref = oracle_blocks(cls, basis, bra, ket, q[sample])
     assert_close(got, ref, what=f"full {cls}")
     assert torch.isfinite(out).all()
+    form = eri.eri_last_form()
+    out2 = eri.eri_batch(cls, db, b, k, qq)
+    assert eri.eri_last_form() == form
+    assert torch.equal(out, out2)

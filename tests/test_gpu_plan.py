@@ -173,3 +173,80 @@ def test_plan_misuse(cuda, tiny):
     with pytest.raises(eri.EriError) as ex:
         store.execute(out=torch.zeros(10, dtype=torch.float64, device=cuda))
     assert ex.value.code == eri.ERI_EPLAN
+
+
+def coulomb_reference(basis, D):
+    """J_uv = sum_ls (uv|ls) D_ls by its plain definition: the oracle's
+    integrals over every ordered shell quartet (no symmetry used)."""
+    off, nbf = bf_offsets(basis)
+    ns = basis.nshell
+    quartets = np.stack(np.meshgrid(*(np.arange(ns),) * 4, indexing="ij"), -1).reshape(-1, 4).astype(np.int32)
+    vals = oracle.eri_quartets(basis, quartets, prec="d", threads=THREADS)
+    sizes = oracle.shellset_size(basis, quartets)
+    pos = np.concatenate([[0], np.cumsum(sizes)])
+    n = (basis.shell_l + 1) * (basis.shell_l + 2) // 2
+    J = np.zeros((nbf, nbf))
+    for i, (a, b, c, d) in enumerate(quartets):
+        blk = vals[pos[i]:pos[i + 1]].reshape(n[a], n[b], n[c], n[d])
+        J[off[a]:off[a] + n[a], off[b]:off[b] + n[b]] += np.einsum(
+            "abcd,cd->ab", blk, D[off[c]:off[c] + n[c], off[d]:off[d] + n[d]])
+    return J
+
+
+def test_plan_coulomb_against_oracle(cuda):
+    """The Coulomb digestion (eri_plan_coulomb) over the plan's unique
+    quartets, expanded by the permutational symmetry, against the plain
+    definition over all ordered quartets (2 atoms, s/p/d shells with K = 6,
+    3, 1: covers a == b, c == d and bra == ket quartets)."""
+    basis = synth.molecule_basis(natom=2, radius=1.6, seed=21)
+    _, nbf = bf_offsets(basis)
+    rng = np.random.default_rng(22)
+    U = rng.uniform(-1, 1, (nbf, nbf))
+    D = np.triu(U) + np.triu(U, 1).T
+    ref = coulomb_reference(basis, D)
+    db = eri.DeviceBasis(basis)
+    Dd = torch.as_tensor(D, device=cuda)
+    plan = eri.Plan(db, threshold=0.0)
+    J = plan.coulomb(Dd)
+    torch.cuda.synchronize()
+    assert plan.status() == eri.ERI_OK
+    got = J.cpu().numpy()
+    assert np.array_equal(got, got.T)
+    scale = float(np.abs(ref).max())
+    assert_close(got, ref, atol=1e-11 * scale, rtol=1e-10, what="J")
+    # the replay re-reads its parameters: J of 2D is 2J, and the energy mode still works
+    J2 = plan.coulomb(2.0 * Dd)
+    # (the atomic additions take another order: entries near zero differ by round-off)
+    assert torch.allclose(J2, 2.0 * J, rtol=1e-12, atol=1e-13 * scale)
+    e = torch.zeros(1, dtype=torch.float64, device=cuda)
+    plan.execute(D=Dd, energy=e)
+    assert plan.status() == eri.ERI_OK and np.isfinite(float(e.item()))
+    # split-precision transforms
+    Js = eri.Plan(db, threshold=0.0, flags=eri.ERI_PLAN_SPLIT).coulomb(Dd).cpu().numpy()
+    assert_close(Js, ref, atol=1e-11 * scale, rtol=1e-10, what="J split")
+
+
+def test_plan_coulomb_screened_and_misuse(cuda):
+    """A screened J differs from the unscreened one by no more than the
+    dropped quartets allow; a store-mode plan or a wrong nbf is refused."""
+    basis = synth.molecule_basis(natom=6, radius=9.0, seed=11)
+    _, nbf = bf_offsets(basis)
+    db = eri.DeviceBasis(basis)
+    D = torch.as_tensor(np.random.default_rng(3).uniform(-1, 1, (nbf, nbf)), device=cuda)
+    D = 0.5 * (D + D.T)
+    thr = 1e-8
+    p1 = eri.Plan(db, threshold=thr)
+    p0 = eri.Plan(db, threshold=0.0)
+    J1 = p1.coulomb(D).cpu().numpy()
+    J0 = p0.coulomb(D).cpu().numpy()
+    dropped = p0.info()["nquartets"] - p1.info()["nquartets"]
+    assert dropped > 0
+    # each dropped element |(ab|cd)| < thr enters at most 8 images with |D| <= 1
+    assert np.abs(J1 - J0).max() <= 8 * dropped * thr * 6 ** 2
+    store = eri.Plan(db, threshold=thr, flags=eri.ERI_PLAN_STORE)
+    with pytest.raises(eri.EriError) as ex:
+        store.coulomb(D)
+    assert ex.value.code == eri.ERI_EPLAN
+    with pytest.raises(eri.EriError) as ex:
+        p1.coulomb(D[:3, :3].contiguous())
+    assert ex.value.code == eri.ERI_EPLAN
