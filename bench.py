@@ -171,14 +171,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("eri_fwd.cu", "eri_tile.cuh", "eri_device.cuh", "eri_internal.h", "eri_tables.cu")
+
+
+def kernel_source_sha():
+    """First 16 hex digits of the SHA-256 of the forward kernel's sources, concatenated."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2506_12501_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic():
     """DRAM traffic per launch of the forward kernel from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "fwd_kernel_class_sweep.md")
-    src = os.path.join(ROOT, "paper_2506_12501_gb300", "csrc", "eri_fwd.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_sha()
     except OSError:
         return None
     m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)

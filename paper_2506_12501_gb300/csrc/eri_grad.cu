@@ -19,6 +19,7 @@
 // memory and added atomically to the gradients (only the order of the
 // additions varies).
 #include <algorithm>
+#include <cmath>
 
 #include "eri_device.cuh"
 #include "eri_internal.h"
@@ -44,7 +45,7 @@ struct GradArgs {
     double* gc;                // [natom][3] or null
     double* ge;                // [nprim] or null
     int TQ, KB, KK, IC;
-    int o_q, o_W, o_Pb, o_Pk, o_Ek, o_A, o_R, o_X, o_T, o_ch;
+    int o_q, o_W, o_Pb, o_Pk, o_Ek, o_A, o_R, o_X, o_T, o_ch, o_che;
     int64_t ntiles;
 };
 
@@ -135,7 +136,7 @@ __device__ __forceinline__ void channel_terms(int l1, int l2, const int qa[3], c
     }
 }
 
-__global__ void __launch_bounds__(kGT, 1) grad_tile_kernel(GradArgs a)
+__global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
 {
     extern __shared__ __align__(16) double sm[];
     const ClassTables& ct = a.ct;
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(kGT, 1) grad_tile_kernel(GradArgs a)
     double* sX = sm + a.o_X;
     double* sT = sm + a.o_T;
     double* sCh = sm + a.o_ch;
+    double* sChE = sm + a.o_che;
     const int ncb = (ct.lb + 1) * (ct.lb + 2) / 2;
 
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(kGT, 1) grad_tile_kernel(GradArgs a)
             sW[idx] = q < nqt ? a.W[g_windex(a, q0 + q, r / ncd, r % ncd)] : 0.0;
         }
         for (int idx = tid; idx < TQ * 8; idx += kGT) sCh[idx] = 0.0;
+        for (int idx = tid; idx < TQ * IC * 2; idx += kGT) sChE[idx] = 0.0;
 
         for (int i0 = 0; i0 < KB; i0 += IC) {
             __syncthreads();
@@ -237,91 +240,115 @@ __global__ void __launch_bounds__(kGT, 1) grad_tile_kernel(GradArgs a)
                 sA[idx] = v;
             }
             __syncthreads();
-            for (int ii = 0; ii < IC && i0 + ii < KB; ++ii) {
-                const int i = i0 + ii;
-                // ---- B': X'[p'][cd] over the raised bra range (four chains)
-                for (int item = tid; item < TQ * nhb2 * ncd; item += kGT) {
-                    const int q = item % TQ, r = item / TQ, p = r % nhb2, cd = r / nhb2;
-                    const double* Ek = sEk + (size_t)q * KK * ct.Tcd;
-                    const double* Rc = sR + (q * IC + ii) * KK;
-                    const int16_t* row = ct.pq2b + (size_t)p * nhk;
-                    const int t0 = ct.ket_start[cd], t1 = ct.ket_start[cd + 1];
-                    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-                    int t = t0;
-                    for (; t + 1 < t1; t += 2) {
-                        const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NI;
-                        const double* Rb = Rc + (size_t)row[ct.ket_q[t + 1]] * NI;
-                        const double* Ea = Ek + t * KK;
-                        const double* Eb = Ea + KK;
-                        int k = 0;
-                        for (; k + 1 < KK; k += 2) {
-                            v0 = fma(Ea[k], Ra[k], v0);
-                            v1 = fma(Ea[k + 1], Ra[k + 1], v1);
-                            v2 = fma(Eb[k], Rb[k], v2);
-                            v3 = fma(Eb[k + 1], Rb[k + 1], v3);
-                        }
-                        if (k < KK) {
-                            v0 = fma(Ea[k], Ra[k], v0);
-                            v2 = fma(Eb[k], Rb[k], v2);
-                        }
+            const int ICe = min(IC, KB - i0);
+            // ---- B': X'[ii][p'][cd][q] over the raised bra range (four chains)
+            for (int item = tid; item < TQ * ICe * nhb2 * ncd; item += kGT) {
+                const int q = item % TQ;
+                int r = item / TQ;
+                const int p = r % nhb2;
+                r /= nhb2;
+                const int cd = r % ncd, ii = r / ncd;
+                const double* Ek = sEk + (size_t)q * KK * ct.Tcd;
+                const double* Rc = sR + (q * IC + ii) * KK;
+                const int16_t* row = ct.pq2b + (size_t)p * nhk;
+                const int t0 = ct.ket_start[cd], t1 = ct.ket_start[cd + 1];
+                double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                int t = t0;
+                for (; t + 1 < t1; t += 2) {
+                    const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NI;
+                    const double* Rb = Rc + (size_t)row[ct.ket_q[t + 1]] * NI;
+                    const double* Ea = Ek + t * KK;
+                    const double* Eb = Ea + KK;
+                    int k = 0;
+                    for (; k + 1 < KK; k += 2) {
+                        v0 = fma(Ea[k], Ra[k], v0);
+                        v1 = fma(Ea[k + 1], Ra[k + 1], v1);
+                        v2 = fma(Eb[k], Rb[k], v2);
+                        v3 = fma(Eb[k + 1], Rb[k + 1], v3);
                     }
-                    if (t < t1) {
-                        const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NI;
-                        const double* Ea = Ek + t * KK;
-                        for (int k = 0; k < KK; ++k) v0 = fma(Ea[k], Ra[k], v0);
+                    if (k < KK) {
+                        v0 = fma(Ea[k], Ra[k], v0);
+                        v2 = fma(Eb[k], Rb[k], v2);
                     }
-                    sX[((size_t)p * ncd + cd) * TQ + q] = (v0 + v1) + (v2 + v3);
                 }
-                __syncthreads();
-                // ---- C'': T[ab][p'] = sum_cd W[ab][cd] X'[p'][cd]
-                for (int item = tid; item < TQ * nab * nhb2; item += kGT) {
-                    const int q = item % TQ, r = item / TQ, p = r % nhb2, ab = r / nhb2;
-                    const double* w = sW + (size_t)q * nab * ncd + (size_t)ab * ncd;
-                    const double* x = sX + (size_t)p * ncd * TQ + q;
-                    double va = 0.0, vb = 0.0;
-                    int cd = 0;
-                    for (; cd + 1 < ncd; cd += 2) {
-                        va = fma(w[cd], x[(size_t)cd * TQ], va);
-                        vb = fma(w[cd + 1], x[(size_t)(cd + 1) * TQ], vb);
-                    }
-                    if (cd < ncd) va = fma(w[cd], x[(size_t)cd * TQ], va);
-                    sT[((size_t)ab * nhb2 + p) * TQ + q] = va + vb;
+                if (t < t1) {
+                    const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NI;
+                    const double* Ea = Ek + t * KK;
+                    for (int k = 0; k < KK; ++k) v0 = fma(Ea[k], Ra[k], v0);
                 }
-                __syncthreads();
-                // ---- D: channel contributions; a thread's items share q = tid % TQ
-                {
-                    double ch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    const int q = tid % TQ;
-                    if (i < s_q[4 * q + 2]) {
-                        const double* A = sA + ((size_t)q * IC + ii) * AX;
-                        for (int item = tid; item < TQ * nab * nhb2; item += kGT) {
-                            const int r = item / TQ, p = r % nhb2, ab = r / nhb2;
-                            int qa[3], qb[3], tt[3];
-                            cart_of(ct.la, ab / ncb, qa);
-                            cart_of(ct.lb, ab % ncb, qb);
-                            herm_of(p, &tt[0], &tt[1], &tt[2]);
-                            if (tt[0] > qa[0] + qb[0] + 2 || tt[1] > qa[1] + qb[1] + 2 || tt[2] > qa[2] + qb[2] + 2)
-                                continue;
-                            channel_terms(ct.la, ct.lb, qa, qb, tt, A, eax, A[3 * eax], A[3 * eax + 1],
-                                          sT[((size_t)ab * nhb2 + p) * TQ + q], ch);
+                sX[(((size_t)ii * nhb2 + p) * ncd + cd) * TQ + q] = (v0 + v1) + (v2 + v3);
+            }
+            __syncthreads();
+            // ---- C'': T[ii][ab][p'][q] = sum_cd W[q][ab][cd] X'[ii][p'][cd][q]
+            for (int item = tid; item < TQ * ICe * nab * nhb2; item += kGT) {
+                const int q = item % TQ;
+                int r = item / TQ;
+                const int p = r % nhb2;
+                r /= nhb2;
+                const int ab = r % nab, ii = r / nab;
+                const double* w = sW + (size_t)q * nab * ncd + (size_t)ab * ncd;
+                const double* x = sX + ((size_t)ii * nhb2 + p) * ncd * TQ + q;
+                double va = 0.0, vb = 0.0;
+                int cd = 0;
+                for (; cd + 1 < ncd; cd += 2) {
+                    va = fma(w[cd], x[(size_t)cd * TQ], va);
+                    vb = fma(w[cd + 1], x[(size_t)(cd + 1) * TQ], vb);
+                }
+                if (cd < ncd) va = fma(w[cd], x[(size_t)cd * TQ], va);
+                sT[item] = va + vb;
+            }
+            __syncthreads();
+            // ---- D: channel contributions.  A thread's items share q = tid % TQ
+            // (TQ divides kGT) and run through the bra primitives in order: the
+            // centre channels stay in registers for the whole tile, the two
+            // exponent channels go to shared memory whenever ii changes.
+            {
+                double ch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                const int q = tid % TQ;
+                int cur = -1;
+                for (int item = tid; item < TQ * ICe * nab * nhb2; item += kGT) {
+                    int r = item / TQ;
+                    const int p = r % nhb2;
+                    r /= nhb2;
+                    const int ab = r % nab, ii = r / nab;
+                    if (ii != cur) {
+                        if (cur >= 0) {
+                            atomicAdd(&sChE[(q * IC + cur) * 2], ch[6]);
+                            atomicAdd(&sChE[(q * IC + cur) * 2 + 1], ch[7]);
                         }
+                        cur = ii;
+                        ch[6] = ch[7] = 0.0;
                     }
+                    if (i0 + ii >= s_q[4 * q + 2]) continue;  // padding bra primitive
+                    int qa[3], qb[3], tt[3];
+                    cart_of(ct.la, ab / ncb, qa);
+                    cart_of(ct.lb, ab % ncb, qb);
+                    herm_of(p, &tt[0], &tt[1], &tt[2]);
+                    if (tt[0] > qa[0] + qb[0] + 2 || tt[1] > qa[1] + qb[1] + 2 || tt[2] > qa[2] + qb[2] + 2) continue;
+                    const double* A = sA + ((size_t)q * IC + ii) * AX;
+                    channel_terms(ct.la, ct.lb, qa, qb, tt, A, eax, A[3 * eax], A[3 * eax + 1], sT[item], ch);
+                }
+                if (cur >= 0) {
+                    atomicAdd(&sChE[(q * IC + cur) * 2], ch[6]);
+                    atomicAdd(&sChE[(q * IC + cur) * 2 + 1], ch[7]);
+                }
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        if (ch[c] != 0.0) atomicAdd(&sCh[q * 8 + c], ch[c]);
+                for (int c = 0; c < 6; ++c)
+                    if (ch[c] != 0.0) atomicAdd(&sCh[q * 8 + c], ch[c]);
+            }
+            __syncthreads();
+            // exponent channels of the chunk's bra primitives
+            for (int idx = tid; idx < TQ * ICe; idx += kGT) {
+                const int q = idx % TQ, ii = idx / TQ, i = i0 + ii;
+                double* e = sChE + (q * IC + ii) * 2;
+                if (q < nqt && i < s_q[4 * q + 2] && a.ge) {
+                    const int sa = a.bra_sh[2 * s_q[4 * q]], sb = a.bra_sh[2 * s_q[4 * q] + 1];
+                    const int K2 = a.shell_K[sb], i1 = i / K2, i2 = i - i1 * K2;
+                    atomicAdd(&a.ge[a.shell_off[sa] + i1], e[0]);
+                    atomicAdd(&a.ge[a.shell_off[sb] + i2], e[1]);
                 }
-                __syncthreads();
-                // exponent channels of bra primitive i
-                for (int q = tid; q < TQ; q += kGT) {
-                    if (q < nqt && i < s_q[4 * q + 2] && a.ge) {
-                        const int sa = a.bra_sh[2 * s_q[4 * q]], sb = a.bra_sh[2 * s_q[4 * q] + 1];
-                        const int K2 = a.shell_K[sb], i1 = i / K2, i2 = i - i1 * K2;
-                        atomicAdd(&a.ge[a.shell_off[sa] + i1], sCh[q * 8 + 6]);
-                        atomicAdd(&a.ge[a.shell_off[sb] + i2], sCh[q * 8 + 7]);
-                    }
-                    sCh[q * 8 + 6] = 0.0;
-                    sCh[q * 8 + 7] = 0.0;
-                }
+                e[0] = 0.0;
+                e[1] = 0.0;
             }
         }
         __syncthreads();
@@ -352,25 +379,49 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int eax, int TQ, 
     a->o_Ek = take((size_t)TQ * KK * ct.Tcd);
     a->o_A = take((size_t)TQ * IC * (3 * eax + 2));
     a->o_R = take((size_t)ct.nhl2 * TQ * IC * KK);
-    a->o_X = take((size_t)ct.nhb2 * ct.ncd * TQ);
-    a->o_T = take((size_t)ct.nab * ct.nhb2 * TQ);
+    a->o_X = take((size_t)ct.nhb2 * ct.ncd * TQ * IC);
+    a->o_T = take((size_t)ct.nab * ct.nhb2 * TQ * IC);
     a->o_ch = take((size_t)TQ * 8);
+    a->o_che = take((size_t)TQ * IC * 2);
     *bytes = off * 8;
     a->TQ = TQ;
     a->IC = IC;
     return *bytes <= (size_t)max_smem_optin();
 }
 
-// Tile shape: the largest TQ (power of two, <= 32) whose items do not exceed
-// a few CTA-widths, then the largest bra-primitive chunk IC that fits.
+// Tile shape (TQ quartets, IC bra primitives per stage pass): the feasible
+// shape with the lowest modelled time per quartet.  Each stage pass costs its
+// rounds of kGT items times the FP64 work of one item, plus a barrier; a
+// tile makes ceil(KB / IC) passes of five stages.
 static bool grad_plan(const ClassTables& ct, int KB, int KK, int eax, int64_t nq, GradArgs* a, size_t* bytes)
 {
+    double best = -1.0;
+    GradArgs pick{};
+    size_t pick_bytes = 0;
     for (int TQ = 32; TQ >= 1; TQ /= 2) {
-        if (TQ > 1 && ((int64_t)TQ * ct.nab * ct.nhb2 > 4 * kGT || TQ > nq)) continue;
-        for (int IC = KB; IC >= 1; IC = IC == 1 ? 0 : (IC + 1) / 2)
-            if (grad_layout(ct, KB, KK, eax, TQ, IC, a, bytes)) return true;
+        if (TQ > 1 && TQ > nq) continue;
+        for (int IC = KB; IC >= 1; IC = IC == 1 ? 0 : (IC + 1) / 2) {
+            GradArgs t = *a;
+            size_t b = 0;
+            if (!grad_layout(ct, KB, KK, eax, TQ, IC, &t, &b)) continue;
+            auto rounds = [](double n) { return std::ceil(n / kGT); };
+            const double kBarrier = 60.0;
+            const double pass = rounds((double)TQ * IC * KK) * (3.0 * ct.nhl2 + 60.0) +
+                                rounds((double)TQ * IC * ct.nhb2 * ct.ncd) * (2.0 * KK * ct.Tcd / ct.ncd + 8.0) +
+                                rounds((double)TQ * IC * ct.nab * ct.nhb2) * (2.0 * ct.ncd + 8.0) +
+                                rounds((double)TQ * IC * ct.nab * ct.nhb2) * 50.0 + 5.0 * kBarrier;
+            const double cost = std::ceil((double)KB / IC) * pass / TQ;
+            if (best < 0 || cost < best) {
+                best = cost;
+                pick = t;
+                pick_bytes = b;
+            }
+        }
     }
-    return false;
+    if (best < 0) return false;
+    *a = pick;
+    *bytes = pick_bytes;
+    return true;
 }
 
 // One launch: the channels of the kernel's bra.  bra/ket are the kernel's
