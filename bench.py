@@ -231,9 +231,10 @@ def run_variants(args, eri, dev):
         return min(ts)
 
     out = {}
+    which = set(args.variants.split(",")) if args.variants else {"split", "adjoint", "batched"}
     # split precision on the high-l workload
     split = {}
-    for cls in [(2, 2, 2, 2), (3, 3, 3, 3), (3, 3, 2, 2)]:
+    for cls in ([(2, 2, 2, 2), (3, 3, 3, 3), (3, 3, 2, 2)] if "split" in which else []):
         for K, nq in ((1, 100_000), (5, args.split_nq_k5)):
             basis, bra, ket, q = synth.split_batch(cls, K=K, seed=0, nq=nq)
             db = eri.DeviceBasis(basis)
@@ -250,10 +251,21 @@ def run_variants(args, eri, dev):
                 "fp64_quartets_per_s": nq / (t64 / 1e3), "split_quartets_per_s": nq / (tsp / 1e3),
                 "max_abs_err_vs_fp64": err, "max_abs_fp64": float(o64.abs().max())}
             del o64, osp
-    out["split"] = split
-    # adjoint: the 16-atom molecule-shaped basis, a sample of every class
+    if split:
+        out["split"] = split
+    if "adjoint" in which:
+        out["adjoint"] = adjoint_variant(args, eri, dev, timed)
+    if "batched" in which:
+        out["batched"] = batched_variant(args, eri, dev, timed)
+    return out
+
+
+def adjoint_variant(args, eri, dev, timed):
+    """The adjoint on the 16-atom molecule-shaped basis, a sample of every class."""
+    import torch
     basis, D, bf_off = synth.adjoint_workload(natom=16, radius=4.4, seed=0)
     pairs, batches = synth.all_unique_quartets(basis)
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees this variant too
     db = eri.DeviceBasis(basis)
     tf = tg = 0.0
     nq_tot = 0
@@ -270,10 +282,15 @@ def run_variants(args, eri, dev):
         tf += timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o), reps=1)
         tg += timed(lambda: eri.eri_batch_grad(cls, db, b, k, qq, Wd, gc, ge), reps=1)
         nq_tot += len(q)
-    out["adjoint"] = {"workload": f"16-atom molecule basis, {len(batches)} classes, <= {args.adjoint_nq} "
-                                  "quartets per class", "quartets": nq_tot, "fwd_ms": tf, "grad_ms": tg,
-                      "grad_over_fwd": tg / tf, "grad_quartets_per_s": nq_tot / (tg / 1e3)}
-    # batched: the screened molecule-shaped workload in one persistent graph launch
+    torch.cuda.profiler.stop()
+    return {"workload": f"16-atom molecule basis, {len(batches)} classes, <= {args.adjoint_nq} "
+                        "quartets per class", "quartets": nq_tot, "fwd_ms": tf, "grad_ms": tg,
+            "grad_over_fwd": tg / tf, "grad_quartets_per_s": nq_tot / (tg / 1e3)}
+
+
+def batched_variant(args, eri, dev, timed):
+    """The screened molecule-shaped workload in one persistent graph launch."""
+    import torch
     mb = synth.molecule_basis(natom=args.molecule_natom, radius=7.0 * (args.molecule_natom / 64) ** (1 / 3), seed=0)
     mdb = eri.DeviceBasis(mb)
     nbf = int(((mb.shell_l + 1) * (mb.shell_l + 2) // 2).sum())
@@ -289,16 +306,16 @@ def run_variants(args, eri, dev):
     t_exec = timed(lambda: plan.execute(D=Dm, energy=e), reps=2)
     J = torch.empty_like(Dm)
     t_j = timed(lambda: plan.coulomb(Dm, J), reps=2)
-    out["batched"] = {"workload": f"{args.molecule_natom} atoms (s x3 K=6,3,1, p x2 K=3,1, d K=1), Schwarz 1e-12, "
-                                  "energy digestion, one persistent graph-captured launch",
-                      "quartets": info["nquartets"], "jobs": info["njobs"], "work_items": info["nitems"],
-                      "create_s": t_create, "execute_ms": t_exec,
-                      "quartets_per_s": info["nquartets"] / (t_exec / 1e3), "energy": float(e.item()),
-                      "coulomb_ms": t_j, "coulomb_quartets_per_s": info["nquartets"] / (t_j / 1e3),
-                      "coulomb_trace_DJ": float((Dm * J).sum().item()),
-                      "status": plan.status()}
+    res = {"workload": f"{args.molecule_natom} atoms (s x3 K=6,3,1, p x2 K=3,1, d K=1), Schwarz 1e-12, "
+                       "energy digestion, one persistent graph-captured launch",
+           "quartets": info["nquartets"], "jobs": info["njobs"], "work_items": info["nitems"],
+           "create_s": t_create, "execute_ms": t_exec,
+           "quartets_per_s": info["nquartets"] / (t_exec / 1e3), "energy": float(e.item()),
+           "coulomb_ms": t_j, "coulomb_quartets_per_s": info["nquartets"] / (t_j / 1e3),
+           "coulomb_trace_DJ": float((Dm * J).sum().item()),
+           "status": plan.status()}
     plan.destroy()
-    return out
+    return res
 
 
 def run_library(args):
@@ -441,7 +458,7 @@ def run_library(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": len(e_ms)}
 
     variants = None
-    if rank == 0 and not args.no_variants and only is None:
+    if rank == 0 and not args.no_variants and (only is None or args.variants):
         variants = run_variants(args, eri, dev)
 
     cpu = None
@@ -484,6 +501,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=18.0, help="seconds of oracle CPU work per reference step")
     ap.add_argument("--only-class", default=None, help="profiling aid: one class, e.g. 2222")
     ap.add_argument("--no-variants", action="store_true", help="skip the split/adjoint/batched measurements")
+    ap.add_argument("--variants", default=None, help="comma list of split,adjoint,batched (default: all)")
     ap.add_argument("--split-nq-k5", type=int, default=10_000)
     ap.add_argument("--adjoint-nq", type=int, default=20_000)
     ap.add_argument("--molecule-natom", type=int, default=16)

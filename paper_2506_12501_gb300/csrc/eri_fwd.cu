@@ -245,6 +245,18 @@ int sm_count()
     return n;
 }
 
+int smem_per_sm()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (n <= 0) n = 64 * 1024;
+    }
+    return n;
+}
+
 int max_smem_optin()
 {
     static int n = 0;
@@ -290,7 +302,7 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     tp->e_smem = e_smem;
     tp->sEbS = e_smem ? odd_up(KB * ct.Tab) : 0;
     tp->sEkS = e_smem ? odd_up(KK * ct.Tcd) : 0;
-    size_t r_need = (size_t)TQ * IC * KK * ct.nhl;
+    size_t r_need = (size_t)((TQ * IC * KK) | 1) * ct.nhl;  // odd row stride
     size_t hA = 0, hB = 0;
     if (ct.hrr) {
         // the recursion buffers alias every staging region before the tables

@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     const int TQ = a.TQ, KB = a.KB, KK = a.KK, IC = a.IC;
     const int nab = ct.nab, ncd = ct.ncd, nhk = ct.nhk, nhb2 = ct.nhb2, nhl2 = ct.nhl2;
     const int L2 = ct.L + 2;
-    const int NI = TQ * IC * KK;
+    const int NI = TQ * IC * KK;  // items of stage A
+    const int NIs = NI | 1;       // R row stride (odd: spreads scattered rows over the banks)
     const int eax = a.pb.eax;
     const int AX = 3 * eax + 2;  // axis tables + the two exponents
     int* s_q = reinterpret_cast<int*>(sm + a.o_q);
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                     double* p;
                     int s;
                     __device__ double& operator[](int e) const { return p[(size_t)e * s]; }
-                } R{sR + item, NI};
+                } R{sR + item, NIs};
                 if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
                     const double* pb = sPb + (q * KB + i) * PS_N;
                     const double* pk = sPk + (q * KK + k) * PS_N;
@@ -255,8 +256,8 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
                 int t = t0;
                 for (; t + 1 < t1; t += 2) {
-                    const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NI;
-                    const double* Rb = Rc + (size_t)row[ct.ket_q[t + 1]] * NI;
+                    const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NIs;
+                    const double* Rb = Rc + (size_t)row[ct.ket_q[t + 1]] * NIs;
                     const double* Ea = Ek + t * KK;
                     const double* Eb = Ea + KK;
                     int k = 0;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                     }
                 }
                 if (t < t1) {
-                    const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NI;
+                    const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NIs;
                     const double* Ea = Ek + t * KK;
                     for (int k = 0; k < KK; ++k) v0 = fma(Ea[k], Ra[k], v0);
                 }
@@ -378,7 +379,7 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int eax, int TQ, 
     a->o_Pk = take((size_t)TQ * KK * PS_N);
     a->o_Ek = take((size_t)TQ * KK * ct.Tcd);
     a->o_A = take((size_t)TQ * IC * (3 * eax + 2));
-    a->o_R = take((size_t)ct.nhl2 * TQ * IC * KK);
+    a->o_R = take((size_t)ct.nhl2 * ((TQ * IC * KK) | 1));
     a->o_X = take((size_t)ct.nhb2 * ct.ncd * TQ * IC);
     a->o_T = take((size_t)ct.nab * ct.nhb2 * TQ * IC);
     a->o_ch = take((size_t)TQ * 8);
@@ -392,8 +393,24 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int eax, int TQ, 
 // Tile shape (TQ quartets, IC bra primitives per stage pass): the feasible
 // shape with the lowest modelled time per quartet.  Each stage pass costs its
 // rounds of kGT items times the FP64 work of one item, plus a barrier; a
-// tile makes ceil(KB / IC) passes of five stages.
+// tile makes ceil(KB / IC) passes of five stages.  Shapes that leave room for
+// two CTAs per SM (so one CTA's barriers overlap the other's work) are
+// preferred whenever one exists.
+static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int eax, int64_t nq, size_t limit, GradArgs* a,
+                             size_t* bytes);
+
 static bool grad_plan(const ClassTables& ct, int KB, int KK, int eax, int64_t nq, GradArgs* a, size_t* bytes)
+{
+    const size_t two_per_sm = (size_t)smem_per_sm() / 2 - 1024;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (grad_plan_within(ct, KB, KK, eax, nq, pass == 0 ? two_per_sm : (size_t)max_smem_optin(), a, bytes))
+            return true;
+    }
+    return false;
+}
+
+static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int eax, int64_t nq, size_t limit, GradArgs* a,
+                             size_t* bytes)
 {
     double best = -1.0;
     GradArgs pick{};
@@ -403,7 +420,7 @@ static bool grad_plan(const ClassTables& ct, int KB, int KK, int eax, int64_t nq
         for (int IC = KB; IC >= 1; IC = IC == 1 ? 0 : (IC + 1) / 2) {
             GradArgs t = *a;
             size_t b = 0;
-            if (!grad_layout(ct, KB, KK, eax, TQ, IC, &t, &b)) continue;
+            if (!grad_layout(ct, KB, KK, eax, TQ, IC, &t, &b) || b > limit) continue;
             auto rounds = [](double n) { return std::ceil(n / kGT); };
             const double kBarrier = 60.0;
             const double pass = rounds((double)TQ * IC * KK) * (3.0 * ct.nhl2 + 60.0) +

@@ -135,6 +135,7 @@ int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* b
                      int64_t nket, const int64_t* quartets, int64_t nq, int64_t len);
 int sm_count();
 int max_smem_optin();
+int smem_per_sm();  // shared memory of one SM (bytes), for occupancy estimates
 
 // Tile shape of the forward kernel for one class (eri_fwd.cu).
 struct TilePlan {

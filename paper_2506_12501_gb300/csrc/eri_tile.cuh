@@ -263,7 +263,8 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     const int tid = threadIdx.x;
     const int TQ = a.TQ, KB = a.KB, KK = a.KK, IC = a.IC;
     const int nhl = ct.nhl, nhb = ct.nhb, nhk = ct.nhk, ncd = ct.ncd, nab = ct.nab;
-    const int NI = TQ * IC * KK;  // R columns
+    const int NI = TQ * IC * KK;  // R columns (items of stage A)
+    const int NIs = NI | 1;       // R row stride: odd, so the scattered rows a warp reads spread over the banks
     const int* s_bstart = reinterpret_cast<const int*>(sm + a.o_tab);
     const int* s_kstart = s_bstart + nab + 1;
     const int16_t* s_bp = reinterpret_cast<const int16_t*>(s_kstart + ncd + 1);
@@ -321,7 +322,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
         for (int item = tid; item < NI; item += kNT) {
             const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
             const int i = i0 + ii;
-            Strided R{sR + item, NI};
+            Strided R{sR + item, NIs};
             if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
                 const double* pb = sPb + (q * KB + i) * PS_N;
                 const double* pk = sPk + (q * KK + k) * PS_N;
@@ -358,7 +359,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             for (int item = tid; item < nB; item += kNT) {
                 const int q = item % TQ, r = item / TQ, p = r % nhb, cd = r / nhb;
                 const double* Ek = a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd;
-                const double* Rc = sR + (q * IC + ii) * KK;  // + e * NI + k
+                const double* Rc = sR + (q * IC + ii) * KK;  // + e * NIs + k
                 const int16_t* pqrow = s_pq + p * nhk;
                 const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
                 // terms outer, ket primitives inner: one p+q lookup per term
@@ -370,8 +371,8 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
                     int t = t0;
                     for (; t + 1 < t1; t += 2) {
-                        const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NI;
-                        const double* Rb = Rc + (size_t)pqrow[s_kq[t + 1]] * NI;
+                        const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NIs;
+                        const double* Rb = Rc + (size_t)pqrow[s_kq[t + 1]] * NIs;
                         const double* Ea = Ek + t * KK;
                         const double* Eb2 = Ea + KK;
                         int k = 0;
@@ -387,7 +388,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                         }
                     }
                     if (t < t1) {
-                        const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NI;
+                        const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NIs;
                         const double* Ea = Ek + t * KK;
                         int k = 0;
                         for (; k + 1 < KK; k += 2) {
@@ -401,8 +402,8 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     float S[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
                     int t = t0;
                     for (; t + 1 < t1; t += 2) {
-                        const float2* Ra = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NI);
-                        const float2* Rb = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t + 1]] * NI);
+                        const float2* Ra = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NIs);
+                        const float2* Rb = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t + 1]] * NIs);
                         const float2* Ea = reinterpret_cast<const float2*>(Ek + t * KK);
                         const float2* Eb2 = Ea + KK;
                         int k = 0;
@@ -418,7 +419,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                         }
                     }
                     if (t < t1) {
-                        const float2* Ra = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NI);
+                        const float2* Ra = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NIs);
                         const float2* Ea = reinterpret_cast<const float2*>(Ek + t * KK);
                         int k = 0;
                         for (; k + 1 < KK; k += 2) {
