@@ -306,6 +306,8 @@ def batched_variant(args, eri, dev, timed):
     t_exec = timed(lambda: plan.execute(D=Dm, energy=e), reps=2)
     J = torch.empty_like(Dm)
     t_j = timed(lambda: plan.coulomb(Dm, J), reps=2)
+    K = torch.empty_like(Dm)
+    t_jk = timed(lambda: plan.jk(Dm, J=J, K=K), reps=2)
     res = {"workload": f"{args.molecule_natom} atoms (s x3 K=6,3,1, p x2 K=3,1, d K=1), Schwarz 1e-12, "
                        "energy digestion, one persistent graph-captured launch",
            "quartets": info["nquartets"], "jobs": info["njobs"], "work_items": info["nitems"],
@@ -313,6 +315,8 @@ def batched_variant(args, eri, dev, timed):
            "quartets_per_s": info["nquartets"] / (t_exec / 1e3), "energy": float(e.item()),
            "coulomb_ms": t_j, "coulomb_quartets_per_s": info["nquartets"] / (t_j / 1e3),
            "coulomb_trace_DJ": float((Dm * J).sum().item()),
+           "jk_ms": t_jk, "jk_quartets_per_s": info["nquartets"] / (t_jk / 1e3),
+           "exchange_trace_DK": float((Dm * K).sum().item()),
            "status": plan.status()}
     plan.destroy()
     return res

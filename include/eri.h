@@ -206,6 +206,9 @@ int eri_batch_noalloc(eri_class_t cls, const eri_basis_t* basis,
  * overwritten, [nbf][nbf] device, symmetric).  D must be symmetric.  This
  * is a consumer of the integrals in the sense of Section 3.1: no integral is
  * stored.  Plans created with ERI_PLAN_STORE return ERI_EPLAN.
+ * eri_plan_jk -- J as above and/or the exchange matrix
+ * K[u][l] = sum over all (v, s) of (uv|ls) D[v][s], in one replay (either
+ * output may be NULL, not both; they must not alias).  Same conditions.
  * eri_plan_set_budget -- bound each CTA of later executions to `cycles`
  * SM clock cycles (0 = no bound); a CTA over budget stops taking work and
  * the execution reports ERI_ETIMEOUT through eri_plan_status, which
@@ -222,6 +225,7 @@ int eri_plan_create(const eri_basis_t* basis, double threshold, int flags, void*
 int eri_plan_execute(eri_plan_t* plan, const double* D, int32_t nbf, double* energy,
                      double* out, int64_t out_len, void* stream);
 int eri_plan_coulomb(eri_plan_t* plan, const double* D, int32_t nbf, double* J, void* stream);
+int eri_plan_jk(eri_plan_t* plan, const double* D, int32_t nbf, double* J, double* K, void* stream);
 int eri_plan_set_budget(eri_plan_t* plan, int64_t cycles);
 int eri_plan_status(eri_plan_t* plan, void* stream);
 int eri_plan_info(eri_plan_t* plan, int64_t* nquartets, int32_t* njobs, int64_t* nitems, int64_t* out_len);

@@ -43,7 +43,7 @@ class eri_basis_t(ctypes.Structure):
 EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
            "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc", "eri_plan_create",
            "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
-           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb"]
+           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
             L.eri_plan_create.argtypes = [ctypes.POINTER(eri_basis_t), ctypes.c_double, I, P, ctypes.POINTER(P)]
             L.eri_plan_execute.argtypes = [P, P, ctypes.c_int32, P, P, I64, P]
             L.eri_plan_coulomb.argtypes = [P, P, ctypes.c_int32, P, P]
+            L.eri_plan_jk.argtypes = [P, P, ctypes.c_int32, P, P, P]
             L.eri_plan_set_budget.argtypes = [P, I64]
             L.eri_plan_status.argtypes = [P, P]
             L.eri_plan_info.argtypes = [P, P, P, P, P]
@@ -297,6 +298,19 @@ class Plan:
             J = torch.empty_like(D)
         _check(lib().eri_plan_coulomb(self.ptr, _ptr(D), D.shape[0], _ptr(J), _stream(stream)), "eri_plan_coulomb")
         return J
+
+    def jk(self, D: torch.Tensor, want_j: bool = True, want_k: bool = True, J: torch.Tensor | None = None,
+           K: torch.Tensor | None = None, stream=None):
+        """(J, K) in one replay: J_uv = sum_ls (uv|ls) D_ls, K_ul = sum_vs (uv|ls) D_vs (None where not wanted)."""
+        D = D.contiguous()
+        if want_j and J is None:
+            J = torch.empty_like(D)
+        if want_k and K is None:
+            K = torch.empty_like(D)
+        J = J if want_j else None
+        K = K if want_k else None
+        _check(lib().eri_plan_jk(self.ptr, _ptr(D), D.shape[0], _ptr(J), _ptr(K), _stream(stream)), "eri_plan_jk")
+        return J, K
 
     def set_budget(self, cycles: int):
         _check(lib().eri_plan_set_budget(self.ptr, int(cycles)), "eri_plan_set_budget")

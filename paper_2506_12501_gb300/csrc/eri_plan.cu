@@ -21,9 +21,10 @@
 // inter-CTA communication, so nothing waits); it runs the tile body of
 // eri_tile.cuh on each tile of the item and either digests
 //   energy = sum_quartets sum_abcd D_ab D_cd (ab|cd)
-// or the Coulomb matrix J_uv = sum_ls (uv|ls) D_ls (every unique quartet
-// standing for its permutation images; a last kernel symmetrises J), or
-// stores the integrals (plans created with ERI_PLAN_STORE).  A cycle
+// or the Coulomb and exchange matrices J_uv = sum_ls (uv|ls) D_ls and
+// K_ul = sum_vs (uv|ls) D_vs (every unique quartet standing for its
+// permutation images; a last kernel symmetrises them), or stores the
+// integrals (plans created with ERI_PLAN_STORE).  A cycle
 // budget (eri_plan_set_budget) bounds the run: a CTA that exceeds it stops
 // popping items and records ERI_ETIMEOUT in the plan's status word.
 #include <algorithm>
@@ -50,6 +51,7 @@ struct PlanParams {
     int nbf;
     double* energy;
     double* J;            // Coulomb mode: [nbf][nbf], zeroed, accumulated, then symmetrised
+    double* K;            // exchange mode: likewise
     double* out;          // store mode: base of the plan's output
     int64_t budget;       // clock64 cycles per CTA, 0 = unlimited
     int* counter;
@@ -103,26 +105,28 @@ __global__ void plan_reset_kernel(const PlanParams* p)
         p->status[0] = 0;
         if (p->energy) *p->energy = 0.0;
     }
-    if (p->J) {
-        const size_t n = (size_t)p->nbf * p->nbf;
-        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-            p->J[i] = 0.0;
-    }
+    const size_t n = (size_t)p->nbf * p->nbf;
+    for (double* M : {p->J, p->K})
+        if (M)
+            for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+                M[i] = 0.0;
 }
 
-// J = J' + J'^T in place: each unordered (u, v) by one thread.
+// J = J' + J'^T and K = K' + K'^T in place: each unordered (u, v) by one thread.
 __global__ void plan_finish_kernel(const PlanParams* p)
 {
-    if (!p->J) return;
     const size_t nbf = (size_t)p->nbf, n = nbf * nbf;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t u = i / nbf, v = i % nbf;
-        if (u < v) {
-            const double t = p->J[u * nbf + v] + p->J[v * nbf + u];
-            p->J[u * nbf + v] = t;
-            p->J[v * nbf + u] = t;
-        } else if (u == v) {
-            p->J[i] *= 2.0;
+    for (double* M : {p->J, p->K}) {
+        if (!M) continue;
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            const size_t u = i / nbf, v = i % nbf;
+            if (u < v) {
+                const double t = M[u * nbf + v] + M[v * nbf + u];
+                M[u * nbf + v] = t;
+                M[v * nbf + u] = t;
+            } else if (u == v) {
+                M[i] *= 2.0;
+            }
         }
     }
 }
@@ -162,6 +166,7 @@ __global__ void __launch_bounds__(kNT, 1)
             a = jobs[it.job];
             a.energy = P.energy;
             a.Jmat = P.J;
+            a.Kmat = P.K;
             a.D = P.D;
             a.nbf = P.nbf;
             if (P.out) a.out = P.out + (int64_t)(size_t)a.out;  // stored as an offset
@@ -663,15 +668,22 @@ extern "C" int eri_plan_execute(eri_plan_t* p, const double* D, int32_t nbf, dou
     return plan_launch(p, prm, (cudaStream_t)stream);
 }
 
-extern "C" int eri_plan_coulomb(eri_plan_t* p, const double* D, int32_t nbf, double* J, void* stream)
+extern "C" int eri_plan_jk(eri_plan_t* p, const double* D, int32_t nbf, double* J, double* K, void* stream)
 {
     if (!p) return ERI_EINVAL;
-    if ((p->flags & ERI_PLAN_STORE) || !D || !J || nbf != p->nbf) return ERI_EPLAN;
+    if ((p->flags & ERI_PLAN_STORE) || !D || (!J && !K) || nbf != p->nbf || (J && J == K)) return ERI_EPLAN;
     PlanParams prm{};
     prm.D = D;
     prm.nbf = p->nbf;
     prm.J = J;
+    prm.K = K;
     return plan_launch(p, prm, (cudaStream_t)stream);
+}
+
+extern "C" int eri_plan_coulomb(eri_plan_t* p, const double* D, int32_t nbf, double* J, void* stream)
+{
+    if (!J) return p ? ERI_EPLAN : ERI_EINVAL;
+    return eri_plan_jk(p, D, nbf, J, nullptr, stream);
 }
 
 extern "C" int eri_plan_set_budget(eri_plan_t* p, int64_t cycles)

@@ -70,6 +70,7 @@ struct FwdArgs {
     // digestion (energy = sum W (ab|cd), W_abcd = D_ab D_cd) instead of stores
     double* energy;           // non-null: digest; out is not written
     double* Jmat;             // non-null (plans): Coulomb digestion into J' [nbf][nbf]; out is not written
+    double* Kmat;             // non-null (plans): exchange digestion into K' [nbf][nbf]; out is not written
     const double* D;          // [nbf][nbf]
     int nbf;
     const int32_t* bf_off;    // [nshell] first Cartesian function of each shell
@@ -252,6 +253,78 @@ static __device__ void digest_coulomb(const FwdArgs& a, const double* V, int nqt
     __syncthreads();
     for (int ab = tid; ab < nab; ab += kNT)
         atomicAdd(&a.Jmat[(size_t)(oa + ab / ncb) * a.nbf + ob + ab % ncb], s_jb[ab]);
+}
+
+// Exchange digestion of one tile of a plan work item, from the same V as
+// digest_coulomb.  With s as there (1/2 per coincident shell pair or pair
+// of pairs), every unique quartet adds
+//   K'[a][c] += s sum_bd (ab|cd) D[b][d],   K'[b][c] += s sum_ad (ab|cd) D[a][d],
+//   K'[a][d] += s sum_bc (ab|cd) D[b][c],   K'[b][d] += s sum_ac (ab|cd) D[a][c],
+// (its images with the bra and ket exchanged are the transposes), and
+// K = K' + K'^T afterwards gives K_ul = sum over all (vs) of (uv|ls) D_vs.
+// One global atomic per (quartet, target element).
+static __device__ void digest_exchange(const FwdArgs& a, const double* V, int nqt, const int* s_q, double* s_dj)
+{
+    const ClassTables& ct = a.ct;
+    const int TQ = a.TQ, ncd = ct.ncd_f, tid = threadIdx.x;
+    const int na = (ct.la + 1) * (ct.la + 2) / 2, nb = (ct.lb + 1) * (ct.lb + 2) / 2;
+    const int nc = (ct.lc + 1) * (ct.lc + 2) / 2, nd = (ct.ld + 1) * (ct.ld + 2) / 2;
+    double* s_w = s_dj;  // [TQ]
+    const int b0 = s_q[0];
+    const int sa = a.bra_sh[2 * b0], sb = a.bra_sh[2 * b0 + 1];
+    const int oa = a.bf_off[sa], ob = a.bf_off[sb];
+    const double* D = a.D;
+    const size_t n = (size_t)a.nbf;
+    __syncthreads();  // the Coulomb digestion may still read s_dj
+    for (int q = tid; q < TQ; q += kNT) {
+        double w = 0.0;
+        if (q < nqt) {
+            const int k = s_q[4 * q + 1];
+            const int sc = a.ket_sh[2 * k], sd = a.ket_sh[2 * k + 1];
+            w = 1.0;
+            if (sa == sb) w *= 0.5;
+            if (sc == sd) w *= 0.5;
+            if ((sa == sc && sb == sd) || (sa == sd && sb == sc)) w *= 0.5;
+        }
+        s_w[q] = w;
+    }
+    __syncthreads();
+    const int n0 = na * nc, n1 = n0 + nb * nc, n2 = n1 + na * nd, n3 = n2 + nb * nd;
+    for (int item = tid; item < TQ * n3; item += kNT) {
+        const int q = item % TQ, r = item / TQ;
+        if (q >= nqt) continue;
+        const int k = s_q[4 * q + 1];
+        const int oc = a.bf_off[a.ket_sh[2 * k]], od = a.bf_off[a.ket_sh[2 * k + 1]];
+        const double* Vq = V + q;  // V[ab][cd] at Vq[TQ * (cd + ncd * ab)]
+        double sum = 0.0;
+        size_t tgt;
+        if (r < n0) {  // (a, c): over b, d
+            const int x = r / nc, y = r % nc;
+            for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nd; ++j)
+                    sum = fma(Vq[TQ * ((y * nd + j) + ncd * (x * nb + i))], D[(ob + i) * n + od + j], sum);
+            tgt = (oa + x) * n + oc + y;
+        } else if (r < n1) {  // (b, c): over a, d
+            const int x = (r - n0) / nc, y = (r - n0) % nc;
+            for (int i = 0; i < na; ++i)
+                for (int j = 0; j < nd; ++j)
+                    sum = fma(Vq[TQ * ((y * nd + j) + ncd * (i * nb + x))], D[(oa + i) * n + od + j], sum);
+            tgt = (ob + x) * n + oc + y;
+        } else if (r < n2) {  // (a, d): over b, c
+            const int x = (r - n1) / nd, y = (r - n1) % nd;
+            for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nc; ++j)
+                    sum = fma(Vq[TQ * ((j * nd + y) + ncd * (x * nb + i))], D[(ob + i) * n + oc + j], sum);
+            tgt = (oa + x) * n + od + y;
+        } else {  // (b, d): over a, c
+            const int x = (r - n2) / nd, y = (r - n2) % nd;
+            for (int i = 0; i < na; ++i)
+                for (int j = 0; j < nc; ++j)
+                    sum = fma(Vq[TQ * ((j * nd + y) + ncd * (i * nb + x))], D[(oa + i) * n + oc + j], sum);
+            tgt = (ob + x) * n + od + y;
+        }
+        atomicAdd(&a.Kmat[tgt], s_w[q] * sum);
+    }
 }
 
 // One tile: quartets q0 .. q0+nqt-1 (the class tables are already staged).
@@ -471,7 +544,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     if (a.acc_regs) {
         const int nC = TQ * nab * ncd;
         double esum = 0.0;
-        if (!ct.hrr && a.Jmat) {
+        if (!ct.hrr && (a.Jmat || a.Kmat)) {
             // the values go to shared memory (the staging regions are dead)
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
@@ -479,7 +552,8 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 if (item < nC) sm[item] = acc[s];
             }
             __syncthreads();
-            digest_coulomb(a, sm, nqt, s_q, sm + a.o_dj);
+            if (a.Jmat) digest_coulomb(a, sm, nqt, s_q, sm + a.o_dj);
+            if (a.Kmat) digest_exchange(a, sm, nqt, s_q, sm + a.o_dj);
         } else if (!ct.hrr) {
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
@@ -546,8 +620,9 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 __syncthreads();
             }
             const double* fin = hbuf[g & 1];  // [ab][cd][q]
-            if (a.Jmat) {
-                digest_coulomb(a, fin, nqt, s_q, sm + a.o_dj);
+            if (a.Jmat || a.Kmat) {
+                if (a.Jmat) digest_coulomb(a, fin, nqt, s_q, sm + a.o_dj);
+                if (a.Kmat) digest_exchange(a, fin, nqt, s_q, sm + a.o_dj);
             } else {
                 for (int item = tid; item < TQ * ct.nab_f * ncf; item += kNT) {
                     const int q = item % TQ, r = item / TQ, cd = r % ncf, ab = r / ncf;

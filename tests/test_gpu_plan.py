@@ -178,6 +178,13 @@ def test_plan_misuse(cuda, tiny):
 def coulomb_reference(basis, D):
     """J_uv = sum_ls (uv|ls) D_ls by its plain definition: the oracle's
     integrals over every ordered shell quartet (no symmetry used)."""
+    return jk_reference(basis, D)[0]
+
+
+def jk_reference(basis, D):
+    """(J, K) by their plain definitions, J_uv = sum_ls (uv|ls) D_ls and
+    K_ul = sum_vs (uv|ls) D_vs, from the oracle's integrals over every
+    ordered shell quartet (no symmetry used)."""
     off, nbf = bf_offsets(basis)
     ns = basis.nshell
     quartets = np.stack(np.meshgrid(*(np.arange(ns),) * 4, indexing="ij"), -1).reshape(-1, 4).astype(np.int32)
@@ -186,11 +193,16 @@ def coulomb_reference(basis, D):
     pos = np.concatenate([[0], np.cumsum(sizes)])
     n = (basis.shell_l + 1) * (basis.shell_l + 2) // 2
     J = np.zeros((nbf, nbf))
+    K = np.zeros((nbf, nbf))
+
+    def sl(x):
+        return slice(off[x], off[x] + n[x])
+
     for i, (a, b, c, d) in enumerate(quartets):
         blk = vals[pos[i]:pos[i + 1]].reshape(n[a], n[b], n[c], n[d])
-        J[off[a]:off[a] + n[a], off[b]:off[b] + n[b]] += np.einsum(
-            "abcd,cd->ab", blk, D[off[c]:off[c] + n[c], off[d]:off[d] + n[d]])
-    return J
+        J[sl(a), sl(b)] += np.einsum("abcd,cd->ab", blk, D[sl(c), sl(d)])
+        K[sl(a), sl(c)] += np.einsum("abcd,bd->ac", blk, D[sl(b), sl(d)])
+    return J, K
 
 
 def test_plan_coulomb_against_oracle(cuda):
@@ -249,4 +261,36 @@ def test_plan_coulomb_screened_and_misuse(cuda):
     assert ex.value.code == eri.ERI_EPLAN
     with pytest.raises(eri.EriError) as ex:
         p1.coulomb(D[:3, :3].contiguous())
+    assert ex.value.code == eri.ERI_EPLAN
+
+
+def test_plan_exchange_against_oracle(cuda):
+    """The exchange digestion (eri_plan_jk) against the plain definition
+    K_ul = sum_vs (uv|ls) D_vs over all ordered quartets, alone and together
+    with J in one replay; split-precision transforms too."""
+    basis = synth.molecule_basis(natom=2, radius=1.6, seed=21)
+    _, nbf = bf_offsets(basis)
+    rng = np.random.default_rng(23)
+    U = rng.uniform(-1, 1, (nbf, nbf))
+    D = np.triu(U) + np.triu(U, 1).T
+    Jref, Kref = jk_reference(basis, D)
+    db = eri.DeviceBasis(basis)
+    Dd = torch.as_tensor(D, device=cuda)
+    plan = eri.Plan(db, threshold=0.0)
+    sj, sk = float(np.abs(Jref).max()), float(np.abs(Kref).max())
+    J, K = plan.jk(Dd)
+    torch.cuda.synchronize()
+    assert plan.status() == eri.ERI_OK
+    assert_close(J.cpu().numpy(), Jref, atol=1e-11 * sj, rtol=1e-10, what="J (jk)")
+    Kh = K.cpu().numpy()
+    assert np.array_equal(Kh, Kh.T)
+    assert_close(Kh, Kref, atol=1e-11 * sk, rtol=1e-10, what="K (jk)")
+    _, K1 = plan.jk(Dd, want_j=False)
+    assert_close(K1.cpu().numpy(), Kref, atol=1e-11 * sk, rtol=1e-10, what="K alone")
+    J1, _ = plan.jk(Dd, want_k=False)
+    assert_close(J1.cpu().numpy(), Jref, atol=1e-11 * sj, rtol=1e-10, what="J alone")
+    _, Ks = eri.Plan(db, threshold=0.0, flags=eri.ERI_PLAN_SPLIT).jk(Dd, want_j=False)
+    assert_close(Ks.cpu().numpy(), Kref, atol=1e-11 * sk, rtol=1e-10, what="K split")
+    with pytest.raises(eri.EriError) as ex:
+        plan.jk(Dd, want_j=False, want_k=False)
     assert ex.value.code == eri.ERI_EPLAN
