@@ -302,6 +302,13 @@ def batched_variant(args, eri, dev, timed):
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     info = plan.info()
+    # FP64 operations of the plan's jobs (plain forms, each job's own orientation)
+    from paper_2506_12501_gb300 import opcount
+    flops = 0.0
+    for j in range(info["njobs"]):
+        cls, nq, _, _ = plan.job(j)
+        kb, kk = plan.job_degrees(j)
+        flops += nq * opcount.sparse_flops(cls, kb, kk, form=(False, False))
     e = torch.zeros(1, dtype=torch.float64, device=dev)
     t_exec = timed(lambda: plan.execute(D=Dm, energy=e), reps=2)
     J = torch.empty_like(Dm)
@@ -313,6 +320,8 @@ def batched_variant(args, eri, dev, timed):
            "quartets": info["nquartets"], "jobs": info["njobs"], "work_items": info["nitems"],
            "create_s": t_create, "execute_ms": t_exec,
            "quartets_per_s": info["nquartets"] / (t_exec / 1e3), "energy": float(e.item()),
+           "gflops_sparse": flops / (t_exec / 1e3) / 1e9,
+           "frac_fp64_peak_sparse": flops / (t_exec / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
            "coulomb_ms": t_j, "coulomb_quartets_per_s": info["nquartets"] / (t_j / 1e3),
            "coulomb_trace_DJ": float((Dm * J).sum().item()),
            "jk_ms": t_jk, "jk_quartets_per_s": info["nquartets"] / (t_jk / 1e3),

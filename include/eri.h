@@ -216,6 +216,8 @@ int eri_batch_noalloc(eri_class_t cls, const eri_basis_t* basis,
  * eri_plan_info / eri_plan_job -- sizes; job j's class, quartet count,
  * output offset, and (if quartet_shells is a HOST buffer of 4*nq ints)
  * its quartets as shell indices (a, b, c, d) in output order.
+ * eri_plan_job_degrees -- job j's pair contraction degrees K_a K_b and
+ * K_c K_d in the order of its class (HOST pointers; for operation counts).
  */
 typedef struct eri_plan eri_plan_t;
 #define ERI_PLAN_STORE 1
@@ -231,6 +233,7 @@ int eri_plan_status(eri_plan_t* plan, void* stream);
 int eri_plan_info(eri_plan_t* plan, int64_t* nquartets, int32_t* njobs, int64_t* nitems, int64_t* out_len);
 int eri_plan_job(eri_plan_t* plan, int32_t job, eri_class_t* cls, int64_t* nq, int64_t* out_off,
                  int32_t* quartet_shells);
+int eri_plan_job_degrees(eri_plan_t* plan, int32_t job, int32_t* kbra, int32_t* kket);
 int eri_plan_destroy(eri_plan_t* plan);
 
 /*

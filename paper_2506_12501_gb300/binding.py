@@ -43,7 +43,7 @@ class eri_basis_t(ctypes.Structure):
 EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
            "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc", "eri_plan_create",
            "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
-           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk"]
+           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
             L.eri_plan_info.argtypes = [P, P, P, P, P]
             L.eri_plan_job.argtypes = [P, ctypes.c_int32, P, P, P, P]
             L.eri_plan_destroy.argtypes = [P]
+            L.eri_plan_job_degrees.argtypes = [P, ctypes.c_int32, P, P]
             for f in ("eri_plan_create", "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status",
                       "eri_plan_info", "eri_plan_job", "eri_plan_destroy"):
                 getattr(L, f).restype = I
@@ -311,6 +312,13 @@ class Plan:
         K = K if want_k else None
         _check(lib().eri_plan_jk(self.ptr, _ptr(D), D.shape[0], _ptr(J), _ptr(K), _stream(stream)), "eri_plan_jk")
         return J, K
+
+    def job_degrees(self, j: int):
+        """(K_a K_b, K_c K_d) of job j, in the order of its class."""
+        kb = ctypes.c_int32()
+        kk = ctypes.c_int32()
+        _check(lib().eri_plan_job_degrees(self.ptr, int(j), ctypes.byref(kb), ctypes.byref(kk)), "eri_plan_job_degrees")
+        return kb.value, kk.value
 
     def set_budget(self, cycles: int):
         _check(lib().eri_plan_set_budget(self.ptr, int(cycles)), "eri_plan_set_budget")

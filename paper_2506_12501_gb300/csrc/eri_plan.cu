@@ -735,6 +735,14 @@ extern "C" int eri_plan_job(eri_plan_t* p, int32_t j, eri_class_t* cls, int64_t*
     return ERI_OK;
 }
 
+extern "C" int eri_plan_job_degrees(eri_plan_t* p, int32_t j, int32_t* kbra, int32_t* kket)
+{
+    if (!p || j < 0 || j >= (int32_t)p->jobs.size() || !kbra || !kket) return ERI_EINVAL;
+    *kbra = p->jobs[j].args.KB;
+    *kket = p->jobs[j].args.KK;
+    return ERI_OK;
+}
+
 extern "C" int eri_plan_destroy(eri_plan_t* p)
 {
     if (!p) return ERI_OK;

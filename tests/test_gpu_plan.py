@@ -61,6 +61,9 @@ def test_plan_store_matches_oracle(cuda, tiny):
     seen = set()
     for j in range(info["njobs"]):
         cls, nq, off, shells = plan.job(j, with_quartets=True)
+        kb, kk = plan.job_degrees(j)
+        a0, b0, c0, d0 = shells[0]
+        assert (kb, kk) == (basis.shell_K[a0] * basis.shell_K[b0], basis.shell_K[c0] * basis.shell_K[d0])
         nab, ncd = nc(cls[0]) * nc(cls[1]), nc(cls[2]) * nc(cls[3])
         got = host[off:off + nq * nab * ncd].reshape(nab * ncd, nq).T
         ref = oracle.eri_quartets(basis, shells, prec="d", threads=THREADS).reshape(nq, nab * ncd)

@@ -26,6 +26,31 @@ def test_f_classes_fp64_against_oracle(cuda, cls):
     assert_close(got, ref, what=f"fp64 {cls}")
 
 
+@pytest.mark.parametrize("cls", F_CLASSES)
+def test_f_classes_every_form(cuda, cls):
+    """Each of the four forms forced on the f-shell classes (FP64 and split
+    transforms), against the oracle.  Where the recursion form is infeasible
+    (its (f0|e0) block exceeds the register accumulators or its buffers
+    shared memory) the library falls back to a feasible form."""
+    L = sum(cls)
+    nq = 10 if L >= 10 else 24
+    basis, bra, ket, q = synth.split_batch(cls, K=1, seed=200 + L, nq=nq, pool=16, npairs=8)
+    ref = oracle_blocks(cls, basis, bra, ket, q, prec="d")
+    db = eri.DeviceBasis(basis)
+    try:
+        for form in range(4):
+            eri.eri_set_forms(1 << form)
+            for prec in (eri.ERI_PREC_FP64, eri.ERI_PREC_SPLIT):
+                got = gpu_list(cls, basis, bra, ket, q, precision=prec, dbasis=db)
+                ran = eri.eri_last_form()
+                if not (form & 2):
+                    assert ran == (bool(form & 1), False)
+                assert_close(got, ref, atol=1e-10 if prec == eri.ERI_PREC_SPLIT else 1e-11,
+                             what=f"{cls} form {form} ran {ran} prec {prec}")
+    finally:
+        eri.eri_set_forms(0)
+
+
 @pytest.mark.parametrize("cls,K,nq", [((2, 2, 2, 2), 1, 2000), ((3, 3, 3, 3), 1, 300), ((3, 3, 2, 2), 1, 1000),
                                       ((2, 2, 2, 2), 5, 60), ((3, 3, 3, 3), 5, 8), ((3, 3, 2, 2), 5, 20)])
 def test_split_against_fp64_path(cuda, cls, K, nq):
