@@ -8,8 +8,11 @@ the CUDA library never touches it.
 (arXiv 2506.12501, Section 2.1) built twice from one source: ``long double``
 (``ld``) and ``double`` (``d``).  ``os_oracle.c`` is an independent
 Obara-Saika recursion used to pin the MD oracle on small inputs.
+``solid.py`` holds the real solid harmonics (closed form) and the 3-centre
+integrals as 4-centre integrals with a unit second bra function.
 """
 from . import oracle  # noqa: F401
+from . import solid  # noqa: F401
 from .oracle import (  # noqa: F401
     build,
     lib,
