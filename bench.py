@@ -231,7 +231,7 @@ def run_variants(args, eri, dev):
         return min(ts)
 
     out = {}
-    which = set(args.variants.split(",")) if args.variants else {"split", "adjoint", "batched"}
+    which = set(args.variants.split(",")) if args.variants else {"split", "adjoint", "batched", "threecentre"}
     # split precision on the high-l workload
     split = {}
     for cls in ([(2, 2, 2, 2), (3, 3, 3, 3), (3, 3, 2, 2)] if "split" in which else []):
@@ -257,7 +257,40 @@ def run_variants(args, eri, dev):
         out["adjoint"] = adjoint_variant(args, eri, dev, timed)
     if "batched" in which:
         out["batched"] = batched_variant(args, eri, dev, timed)
+    if "threecentre" in which:
+        out["threecentre"] = three_centre_variant(args, eri, dev, timed)
     return out
+
+
+def three_centre_variant(args, eri, dev, timed):
+    """3-centre integrals (x|cd), x a real solid harmonic: uncontracted
+    auxiliary shells lx <= 3 against the class-sweep orbital pairs (K = 3),
+    1e5 triples per class; the form (side order) each class ran and its FP64
+    operation count give GFLOP/s and the fraction of the FP64 peak."""
+    import torch
+    from paper_2506_12501_gb300 import opcount
+    basis, orb, aux = synth.three_centre_pools(seed=0, pool=512)
+    db = eri.DeviceBasis(basis)
+    per, tot_ms, tot_flops, tot_n = {}, 0.0, 0.0, 0
+    for lx in range(4):
+        nterms = int(np.count_nonzero(np.abs(eri.solid_harmonics(lx)) > 1e-14))
+        for lc, ld in ((0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)):
+            x, ket, t = synth.three_centre_batch(orb, aux, (lx, lc, ld), seed=0, nt=args.three_nt)
+            xd, kd, td = (torch.as_tensor(v, device=dev) for v in (x, ket, t))
+            o = torch.empty(len(t) * (2 * lx + 1) * eri.nc(lc) * eri.nc(ld), dtype=torch.float64, device=dev)
+            ms = timed(lambda: eri.eri_batch3(lx, lc, ld, db, xd, kd, td, pure=True, out=o), reps=2)
+            sw, _ = eri.eri_last_form()
+            f = opcount.sparse_flops3((lx, lc, ld), 1, 9, True, sw, nterms) * len(t)
+            per[f"{lx}{lc}{ld}"] = {"ms": ms, "form": "swapped" if sw else "plain",
+                                    "triples_per_s": len(t) / (ms / 1e3), "gflops_sparse": f / (ms / 1e3) / 1e9}
+            tot_ms += ms
+            tot_flops += f
+            tot_n += len(t)
+    return {"workload": f"x real solid harmonics lx <= 3 (K = 1, exponents 10^U(-1,1)) x orbital pairs l <= 2 "
+                        f"(K = 3), 24 classes x {args.three_nt} triples",
+            "triples": tot_n, "ms": tot_ms, "triples_per_s": tot_n / (tot_ms / 1e3),
+            "gflops_sparse": tot_flops / (tot_ms / 1e3) / 1e9,
+            "frac_fp64_peak_sparse": tot_flops / (tot_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, "per_class": per}
 
 
 def adjoint_variant(args, eri, dev, timed):
@@ -514,10 +547,11 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=18.0, help="seconds of oracle CPU work per reference step")
     ap.add_argument("--only-class", default=None, help="profiling aid: one class, e.g. 2222")
     ap.add_argument("--no-variants", action="store_true", help="skip the split/adjoint/batched measurements")
-    ap.add_argument("--variants", default=None, help="comma list of split,adjoint,batched (default: all)")
+    ap.add_argument("--variants", default=None, help="comma list of split,adjoint,batched,threecentre (default: all)")
     ap.add_argument("--split-nq-k5", type=int, default=10_000)
     ap.add_argument("--adjoint-nq", type=int, default=20_000)
     ap.add_argument("--molecule-natom", type=int, default=16)
+    ap.add_argument("--three-nt", type=int, default=100_000, help="triples per 3-centre class")
     ap.add_argument("--nq", type=int, default=NQ_PER_CLASS, help="quartets per class")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -138,6 +138,42 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
                    double* grad_centres, double* grad_exps, void* stream);
 
 /*
+ * eri_batch3 -- 3-centre integrals
+ *   (x|cd) = int int phi_x(r1) |r1 - r2|^-1 phi_c(r2) phi_d(r2) dr1 dr2
+ * of one class (lx | lc ld) for a batch: x from a list of single shells
+ * (e.g. a density-fitting basis), cd from ket pairs as in eri_batch.
+ *   x_shells: [nx] shell indices of angular momentum lx (DEVICE).
+ *   triples:  NULL => every (x, ket) combination; else [nt][2] (x index,
+ *             ket index), int64 (DEVICE).
+ *   pure:     1 => x is a real solid harmonic (2 lx + 1 components,
+ *             m = -lx..lx, Racah normalisation: S_l0(0,0,1) = 1, and
+ *             S_lm over the unit sphere has norm 4 pi / (2l + 1)), whose
+ *             transform uses only the terminal Hermite functions of order lx
+ *             (Section 3.2.3); 0 => Cartesian x (nc(lx) components).
+ *   out:      list form out[t + nt*(x*ncd + cd)]; product form
+ *             out[i + nx*(x + nxc*(cd + ncd*k))], nxc the x component count.
+ * The batch runs as the 4-centre kernel on (x 1|cd), 1 being the unit
+ * function (an s Gaussian of exponent 0, coefficient 1), in the cheaper of
+ * the two side orders.  precision as in eri_batch.  Synchronises `stream`
+ * once.  Errors: ERI_EINVAL (l out of range, bad pointers, out_len too
+ * small, a shell index out of range), ERI_ECLASS (an x shell's l is not lx
+ * or a ket shell's l disagrees), ERI_ECUDA, ERI_ENOMEM.
+ */
+/*
+ * eri_solid_harmonics -- the real solid harmonics eri_batch3 uses, as
+ * Cartesian coefficients: S_lm = sum_a out[(m+l)*nc(l) + a] x^ax y^ay z^az,
+ * m = -l..l, a in the library's Cartesian order.  out is a HOST buffer of
+ * (2l+1) nc(l) doubles; no GPU work.  ERI_EINVAL for l outside 0..ERI_LMAX.
+ */
+int eri_solid_harmonics(int32_t l, double* out);
+
+int eri_batch3(int32_t lx, int32_t lc, int32_t ld, const eri_basis_t* basis,
+               const int32_t* x_shells, int64_t nx,
+               const int32_t* ket_pairs, int64_t nket,
+               const int64_t* triples, int64_t nt, int32_t pure,
+               double* out, int64_t out_len, int precision, void* stream);
+
+/*
  * eri_batch_noalloc -- the same integrals as eri_batch (FP64, list or
  * product form, same layout and errors), for callers that may not allocate
  * memory: the paper has no counterpart of this entry point.

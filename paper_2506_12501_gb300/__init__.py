@@ -12,6 +12,8 @@ from .binding import (  # noqa: F401
     eri_boys,
     eri_batch,
     eri_batch_grad,
+    eri_batch3,
+    solid_harmonics,
     eri_batch_noalloc,
     Plan,
     ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE,

@@ -43,7 +43,7 @@ class eri_basis_t(ctypes.Structure):
 EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
            "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc", "eri_plan_create",
            "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
-           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees"]
+           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees", "eri_batch3", "eri_solid_harmonics"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
@@ -60,6 +60,9 @@ def lib() -> ctypes.CDLL:
             P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
             L.eri_boys.argtypes = [I, P, I64, P, P]
             L.eri_batch.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P, I64, I, P]
+            L.eri_solid_harmonics.argtypes = [ctypes.c_int32, P]
+            L.eri_batch3.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(eri_basis_t), P,
+                                     I64, P, I64, P, I64, ctypes.c_int32, P, I64, I, P]
             L.eri_batch_grad.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P, I64,
                                          P, P, P]
             L.eri_last_status.argtypes = [P]
@@ -178,6 +181,34 @@ def eri_batch(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pairs: torch
                            _ptr(quartets), nq if nq is not None else 0, _ptr(out), out.numel(), precision,
                            _stream(stream))
     _check(code, "eri_batch")
+    return out
+
+
+def solid_harmonics(l: int):
+    """[2l+1][nc(l)] Cartesian coefficients of the library's real solid harmonics (host)."""
+    import numpy as np
+    out = np.zeros((2 * l + 1, nc(l)), dtype=np.float64)
+    _check(lib().eri_solid_harmonics(int(l), ctypes.c_void_p(out.ctypes.data)), "eri_solid_harmonics")
+    return out
+
+
+def eri_batch3(lx: int, lc: int, ld: int, basis: DeviceBasis, x_shells: torch.Tensor, ket_pairs: torch.Tensor,
+               triples: torch.Tensor | None = None, pure: bool = True, out: torch.Tensor | None = None,
+               precision: int = ERI_PREC_FP64, stream=None) -> torch.Tensor:
+    """3-centre shellsets (x|cd) of class (lx | lc ld) (see include/eri.h for the layout)."""
+    nx, nket = x_shells.shape[0], ket_pairs.shape[0]
+    nt = triples.shape[0] if triples is not None else None
+    ncx = 2 * lx + 1 if pure else nc(lx)
+    n = (nt if nt is not None else nx * nket) * ncx * nc(lc) * nc(ld)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=x_shells.device)
+    if n == 0:
+        return out
+    b = basis.struct()
+    code = lib().eri_batch3(lx, lc, ld, ctypes.byref(b), _ptr(x_shells), nx, _ptr(ket_pairs), nket, _ptr(triples),
+                            nt if nt is not None else 0, 1 if pure else 0, _ptr(out), out.numel(), precision,
+                            _stream(stream))
+    _check(code, "eri_batch3")
     return out
 
 

@@ -47,7 +47,8 @@ struct PrepassArgs {
     const int64_t* quartets;
     int64_t nq;
     int l[4];
-    int* info;  // [0..3] max K per centre, [4] error
+    int unit_b;  // 1: every bra pair's second shell is -1, the unit function (3-centre)
+    int* info;   // [0..3] max K per centre, [4] error
 };
 
 __device__ __forceinline__ void set_err(int* p, int code) { atomicCAS(p, 0, code); }
@@ -62,6 +63,11 @@ __global__ void prepass_kernel(PrepassArgs a)
             if (i >= np) continue;
             for (int c = 0; c < 2; ++c) {
                 const int32_t s = pr[2 * i + c];
+                if (a.unit_b && side == 0 && c == 1) {
+                    if (s != -1) set_err(&a.info[4], DEV_EINDEX);
+                    atomicMax(&a.info[1], 1);
+                    continue;
+                }
                 if (s < 0 || s >= a.nshell) {
                     set_err(&a.info[4], DEV_EINDEX);
                     continue;
@@ -109,6 +115,7 @@ struct PairArgs {
     double* zz;             // [npairs][KS][2]: the two exponents
     int split;              // 1: E products stored as float pairs (hi, lo) in the double slots
     int hrr;                // 1: terms of E_{e,0}, |e| = l1..l1+l2 (horizontal-recursion form)
+    const double* scale;    // [T] per-term factors (solid-harmonic side), or null
 };
 
 constexpr int kEax = (kLmax + 3) * (kLmax + 3) * (2 * kLmax + 5);  // per-axis E table bound (adjoint shifts)
@@ -119,8 +126,10 @@ __global__ void pair_kernel(PairArgs a)
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = g / a.KS;
         const int s = (int)(g - j * a.KS);
+        // s2 = -1: the unit function (exponent 0, coefficient 1) of a 3-centre
+        // bra; its centre is immaterial and taken as the first shell's
         const int s1 = a.pairs[2 * j], s2 = a.pairs[2 * j + 1];
-        const int K1 = a.shell_K[s1], K2 = a.shell_K[s2];
+        const int K1 = a.shell_K[s1], K2 = s2 < 0 ? 1 : a.shell_K[s2];
         if (s == 0) a.kprim[j] = K1 * K2;
         if (s >= K1 * K2) {  // padding slot: finite zeros, never contributes
             for (int t = 0; t < a.T; ++t) a.E[((size_t)j * a.T + t) * a.KS + s] = 0.0;
@@ -135,10 +144,11 @@ __global__ void pair_kernel(PairArgs a)
             continue;
         }
         const int i1 = s / K2, i2 = s - i1 * K2;
-        const int p1 = a.shell_off[s1] + i1, p2 = a.shell_off[s2] + i2;
-        const double z1 = a.exps[p1], z2 = a.exps[p2];
+        const int p1 = a.shell_off[s1] + i1, p2 = s2 < 0 ? -1 : a.shell_off[s2] + i2;
+        const double z1 = a.exps[p1], z2 = s2 < 0 ? 0.0 : a.exps[p2];
+        const double c2 = s2 < 0 ? 1.0 : a.coefs[p2];
         const double* A = a.centres + 3 * a.shell_atom[s1];
-        const double* B = a.centres + 3 * a.shell_atom[s2];
+        const double* B = s2 < 0 ? A : a.centres + 3 * a.shell_atom[s2];
         const double p = z1 + z2;
         const double invp = 1.0 / p;
         const double inv2p = 0.5 * invp;
@@ -152,7 +162,7 @@ __global__ void pair_kernel(PairArgs a)
         }
         // K_AB c_1 c_2 carried by the x-axis bootstrap E_00^0 (Eq. E2-000),
         // 1 on y and z: the products E^x E^y E^z are unchanged.
-        const double e00x = a.coefs[p1] * a.coefs[p2] * exp(-z1 * z2 * invp * AB2);
+        const double e00x = a.coefs[p1] * c2 * exp(-z1 * z2 * invp * AB2);
         const int ext = a.ax ? 2 : 0;
         // largest raised indices: the adjoint raises both by 2; the
         // horizontal-recursion form needs E_{i,0} for i <= l1 + l2
@@ -195,6 +205,7 @@ __global__ void pair_kernel(PairArgs a)
                 lq += tt;
             }
             double v = E[0][idx[0]] * E[1][idx[1]] * E[2][idx[2]];
+            if (a.scale) v *= a.scale[t];
             if (a.ket && (lq & 1)) v = -v;
             if (a.split)
                 reinterpret_cast<float2*>(Eout)[(size_t)t * a.KS] = split_f64(v);
@@ -401,36 +412,42 @@ static size_t align_up(size_t n) { return (n + 255) & ~size_t(255); }
 static std::atomic<int> g_form_mask{0xF};
 
 // Forms chosen by timing, per (device, class, K_bra, K_ket, precision).
-static std::map<std::tuple<int, int, int, int, int, int, int, int>, int> g_forms;
+static std::map<std::tuple<int, int, int, int, int, int, int, int, int>, int> g_forms;
 static std::mutex g_forms_mu;
 
-static std::tuple<int, int, int, int, int, int, int, int> form_key(eri_class_t cls, int KB, int KK, int split)
+static std::tuple<int, int, int, int, int, int, int, int, int> form_key(eri_class_t cls, int KB, int KK, int split,
+                                                                        int kind)
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    return std::make_tuple(dev, cls.la, cls.lb, cls.lc, cls.ld, KB, KK, split);
+    return std::make_tuple(dev, cls.la, cls.lb, cls.lc, cls.ld, KB, KK, split, kind);
 }
 
-static int lookup_form(eri_class_t cls, int KB, int KK, int split)
+static int lookup_form(eri_class_t cls, int KB, int KK, int split, int kind)
 {
     std::lock_guard<std::mutex> lk(g_forms_mu);
-    auto it = g_forms.find(form_key(cls, KB, KK, split));
+    auto it = g_forms.find(form_key(cls, KB, KK, split, kind));
     return it == g_forms.end() ? -1 : it->second;
 }
 
-void remember_form(eri_class_t cls, int KB, int KK, int split, int form)
+void remember_form(eri_class_t cls, int KB, int KK, int split, int kind, int form)
 {
     std::lock_guard<std::mutex> lk(g_forms_mu);
-    g_forms[form_key(cls, KB, KK, split)] = form;
+    g_forms[form_key(cls, KB, KK, split, kind)] = form;
 }
 
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
-                  int allow_swap, FormChoice* fc, int split)
+                  int allow_swap, FormChoice* fc, int split, int kind)
 {
     int err = ERI_OK;
-    const ClassTables* ct = get_class_tables(cls.la, cls.lb, cls.lc, cls.ld, st, &err);
+    // kind 2: the caller's bra side (x, unit) is a solid harmonic
+    auto tables = [&](int la, int lb, int lc, int ld, int x_first) {
+        return kind == 2 ? get_class_tables_pure(la, lb, lc, ld, x_first ? 1 : 2, st, &err)
+                         : get_class_tables(la, lb, lc, ld, st, &err);
+    };
+    const ClassTables* ct = tables(cls.la, cls.lb, cls.lc, cls.ld, 1);
     if (!ct) return err;
     *ct_out = ct;
     const int forced = fc ? fc->form : -1;
@@ -448,7 +465,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
     if (cudaMemsetAsync(dinfo, 0, 5 * sizeof(int), st) != cudaSuccess) return ERI_ECUDA;
     PrepassArgs pa{basis->shell_l, basis->shell_K, basis->nshell, bra, nbra, ket, nket, quartets,
                    quartets ? nq : (int64_t)0,
-                   {cls.la, cls.lb, cls.lc, cls.ld}, dinfo};
+                   {cls.la, cls.lb, cls.lc, cls.ld}, kind > 0 ? 1 : 0, dinfo};
     const int64_t n = std::max(std::max(nbra, nket), quartets ? nq : (int64_t)0);
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
     {
@@ -468,9 +485,9 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         // the transforms run on (e0) functions followed by horizontal
         // recursions in the contracted basis.  The FP64-work model picks one
         // unless a form is forced or an earlier timing chose one.
-        const ClassTables* opt[4] = {ct, get_class_tables(cls.lc, cls.ld, cls.la, cls.lb, st, &err), nullptr, nullptr};
+        const ClassTables* opt[4] = {ct, tables(cls.lc, cls.ld, cls.la, cls.lb, 0), nullptr, nullptr};
         if (!opt[1]) return err;
-        if (allow_swap > 1) {
+        if (allow_swap > 1 && kind == 0) {
             opt[2] = get_class_tables_hrr(cls.la, cls.lb, cls.lc, cls.ld, st, &err);
             opt[3] = get_class_tables_hrr(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
             if (!opt[2] || !opt[3]) return err;
@@ -488,7 +505,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
                 TilePlan tp;
                 if (c->nab * c->ncd > kNT * kNACC || !plan_tiles(*c, (int)kb, (int)kk, nqq, &tp)) continue;
             }
-            cost[o] = kb * kk * (c->nhb * c->Tcd + 0.5 * c->nhl) + kb * c->ncd * c->Tab +
+            cost[o] = kb * kk * ((c->nhb - c->pb0) * c->Tcd + 0.5 * c->nhl) + kb * c->ncd * c->Tab +
                       (c->hrr ? c->nab * c->nks + c->ncd_f * c->nbs : 0);
         }
         {
@@ -511,7 +528,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
             if (forced > 3 || cost[forced] < 0) return ERI_EINVAL;
             best = forced;
         } else {
-            best = lookup_form(cls, *KB, *KK, split);
+            best = lookup_form(cls, *KB, *KK, split, kind);
             if (best >= 0 && cost[best] >= 0) {
                 if (fc) fc->cached = 1;
             } else {
@@ -586,6 +603,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         p.zz = t.zz;
         p.split = split;
         p.hrr = ct->hrr;
+        p.scale = side ? ct->ket_scale : ct->bra_scale;
         const int64_t tot = p.npairs * p.KS;
         const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
         ProfScope ps(PROF_PAIR, st);
@@ -633,7 +651,7 @@ int check_batch_args(eri_class_t cls, const eri_basis_t* basis, const int32_t* b
 // of) `out`; the real launch overwrites it.
 constexpr int64_t kTuneMinQuartets = 16384;
 constexpr int64_t kTuneQuartets = 8192;
-static std::map<std::tuple<int, int, int, int, int, int, int, int, int>, std::pair<TilePlan, float>> g_tuned;
+static std::map<std::tuple<int, int, int, int, int, int, int, int, int, int>, std::pair<TilePlan, float>> g_tuned;
 static std::mutex g_tuned_mu;
 
 static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cudaStream_t st, TilePlan* best,
@@ -642,7 +660,7 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
     int dev = 0;
     cudaGetDevice(&dev);
     const ClassTables& ct = base.ct;
-    const auto key = std::make_tuple(dev, ct.la, ct.lb, ct.lc, ct.ld, ct.hrr, base.KB, base.KK, split);
+    const auto key = std::make_tuple(dev, ct.la, ct.lb, ct.lc, ct.ld, ct.hrr, ct.pure, base.KB, base.KK, split);
     {
         std::lock_guard<std::mutex> lk(g_tuned_mu);
         auto it = g_tuned.find(key);
@@ -776,18 +794,14 @@ static int forward_args(const eri_basis_t* basis, const int32_t* bra_pairs, int6
 
 static thread_local int g_last_form = -1;
 
-extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
-                         const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq, double* out,
-                         int64_t out_len, int precision, void* stream)
+// One forward batch of any kind (0: 4-centre; 1, 2: 3-centre with the unit
+// function as the second bra shell, Cartesian or solid-harmonic x): form
+// choice, pair tables, tile shape, launch.  Arguments already validated.
+static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
+                       const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq, double* out,
+                       int split, int kind, cudaStream_t st)
 {
-    int err = check_batch_args(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, out_len);
-    if (err != ERI_OK) return err;
-    if (precision != ERI_PREC_FP64 && precision != ERI_PREC_SPLIT) return ERI_EINVAL;
     const int64_t nqq = quartets ? nq : nbra * nket;
-    if (nqq == 0 || nbra == 0 || nket == 0) return ERI_OK;
-    if (!out) return ERI_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int split = precision == ERI_PREC_SPLIT;
     void (*kern)(FwdArgs) = split ? fwd_kernel_split : fwd_kernel;
     const ClassTables* ct = nullptr;
     PairTables pb{}, pk{};
@@ -795,14 +809,14 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     FormChoice fc;
     auto prepare = [&](FormChoice* f, FwdArgs* a, TilePlan* tp) {
         int e = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB,
-                              &KK, kmax, 2, f, split);
+                              &KK, kmax, kind ? 1 : 2, f, split, kind);
         if (e != ERI_OK) return e;
         return forward_args(basis, bra_pairs, nbra, ket_pairs, nket, quartets, nqq, out, ct, pb, pk, KB, KK,
                             f->form & 1, st, a, tp);
     };
     FwdArgs a;
     TilePlan tp;
-    err = prepare(&fc, &a, &tp);
+    int err = prepare(&fc, &a, &tp);
     if (err != ERI_OK) return err;
     // large batches: tile shape from the autotuner (cached per kernel class,
     // form and signature); on the first such batch of a signature, the
@@ -823,7 +837,7 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
             bool tuned1 = false;
             if (prepare(&f1, &a1, &tp1) == ERI_OK) tuned1 = tuned_tile(a1, kern, split, st, &best1, &ms1);
             const bool take_alt = tuned1 && (!tuned || ms1 < ms);
-            remember_form(sig, KB0, KK0, split, take_alt ? f1.form : fc.form);
+            remember_form(sig, KB0, KK0, split, kind, take_alt ? f1.form : fc.form);
             if (take_alt) {
                 fc = f1;
                 a = a1;
@@ -859,6 +873,61 @@ extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_
     return ERI_OK;
 }
 
+extern "C" int eri_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
+                         const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq, double* out,
+                         int64_t out_len, int precision, void* stream)
+{
+    int err = check_batch_args(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, out_len);
+    if (err != ERI_OK) return err;
+    if (precision != ERI_PREC_FP64 && precision != ERI_PREC_SPLIT) return ERI_EINVAL;
+    const int64_t nqq = quartets ? nq : nbra * nket;
+    if (nqq == 0 || nbra == 0 || nket == 0) return ERI_OK;
+    if (!out) return ERI_EINVAL;
+    return run_forward(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, out,
+                       precision == ERI_PREC_SPLIT, 0, (cudaStream_t)stream);
+}
+
+extern "C" int eri_solid_harmonics(int32_t l, double* out)
+{
+    if (l < 0 || l > ERI_LMAX || !out) return ERI_EINVAL;
+    solid_harmonic_table(l, out);
+    return ERI_OK;
+}
+
+__global__ void unit_pairs_kernel(const int32_t* __restrict__ x, int64_t n, int32_t* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        out[2 * i] = x[i];
+        out[2 * i + 1] = -1;
+    }
+}
+
+extern "C" int eri_batch3(int32_t lx, int32_t lc, int32_t ld, const eri_basis_t* basis, const int32_t* x_shells,
+                          int64_t nx, const int32_t* ket_pairs, int64_t nket, const int64_t* triples, int64_t nt,
+                          int32_t pure, double* out, int64_t out_len, int precision, void* stream)
+{
+    const eri_class_t cls{lx, 0, lc, ld};
+    if (pure != 0 && pure != 1) return ERI_EINVAL;
+    // the pair-list checks of eri_batch (x shells stand in for the bra pairs)
+    int err = check_batch_args(cls, basis, x_shells, nx, ket_pairs, nket, triples, nt, INT64_MAX);
+    if (err != ERI_OK) return err;
+    if (precision != ERI_PREC_FP64 && precision != ERI_PREC_SPLIT) return ERI_EINVAL;
+    const int64_t ntt = triples ? nt : nx * nket;
+    const int64_t ncx = pure ? 2 * lx + 1 : host_nc(lx);
+    if (out_len < ntt * ncx * host_nc(lc) * host_nc(ld)) return ERI_EINVAL;
+    if (ntt == 0 || nx == 0 || nket == 0) return ERI_OK;
+    if (!out) return ERI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t* pairs = (int32_t*)aux_workspace(sizeof(int32_t) * 2 * (size_t)nx, &err);
+    if (!pairs) return err;
+    const int grid = (int)std::min<int64_t>((nx + 255) / 256, 4 * sm_count());
+    unit_pairs_kernel<<<std::max(grid, 1), 256, 0, st>>>(x_shells, nx, pairs);
+    if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+    count_launch();
+    return run_forward(cls, basis, pairs, nx, ket_pairs, nket, triples, nt, out, precision == ERI_PREC_SPLIT,
+                       pure ? 2 : 1, st);
+}
+
 extern "C" int eri_set_forms(int32_t mask)
 {
     if (mask < 0 || mask > 0xF) return ERI_EINVAL;
@@ -888,7 +957,7 @@ int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, 
 {
     if (cudaMemsetAsync(dinfo, 0, 5 * sizeof(int), st) != cudaSuccess) return ERI_ECUDA;
     PrepassArgs pa{basis->shell_l, basis->shell_K, basis->nshell, bra, nbra, ket, nket, quartets,
-                   quartets ? nq : (int64_t)0, {cls.la, cls.lb, cls.lc, cls.ld}, dinfo};
+                   quartets ? nq : (int64_t)0, {cls.la, cls.lb, cls.lc, cls.ld}, 0, dinfo};
     const int64_t n = std::max(std::max(nbra, nket), quartets ? nq : (int64_t)0);
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
     count_launch();

@@ -71,6 +71,15 @@ struct ClassTables {
     // its (e0) list in term-list order; level j lists (c, d) with |d| = j and
     // l1 <= |c| <= l1 + l2 - j, each entry a step (src1, src2, axis) into
     // level j-1; the last level (j = l2) is in (c, d) component-pair order.
+    // Solid-harmonic side (3-centre integrals): pure = 1 makes the kernel
+    // bra (la, lb = 0) a real solid harmonic, pure = 2 the kernel ket
+    // (lc, ld = 0).  Its rows are m = -l..l (2l+1 of them) and its terms
+    // only the terminal Hermite functions |t| = l, each E product scaled by
+    // the Cartesian coefficient of the harmonic (Section 3.2.3).
+    int pure;
+    int pb0;                      // first bra Hermite function the transforms need
+    const double* bra_scale;      // [Tab] per-term factors, or null
+    const double* ket_scale;      // [Tcd]
     int hrr;
     int nab_f, ncd_f;             // final component-pair counts
     int nbs, nks;                 // steps over all levels j >= 1
@@ -90,6 +99,10 @@ enum { DEV_OK = 0, DEV_ECLASS = 1, DEV_EINDEX = 2, DEV_EK = 3, DEV_ETIMEOUT = 4 
 struct HostClassTables;
 const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t s, int* err);
 const ClassTables* get_class_tables_hrr(int la, int lb, int lc, int ld, cudaStream_t s, int* err);
+// pure: 1 = the (la, lb = 0) side a solid harmonic, 2 = the (lc, ld = 0) side
+const ClassTables* get_class_tables_pure(int la, int lb, int lc, int ld, int pure, cudaStream_t s, int* err);
+// Real solid harmonics (Racah normalisation) as [2l+1][nc(l)] Cartesian coefficients.
+void solid_harmonic_table(int l, double* out);
 const double* get_boys_table(int L, cudaStream_t s, int* err);    // rows of F_{L+k}(T_j)/k!, plus exp
 const double* get_boys_master(cudaStream_t s, int* err);          // rows of F_0..F_kBoysMtab and exp
 const RStep* get_rsteps(cudaStream_t s, int* err);                 // recursion step table (device)
@@ -117,16 +130,19 @@ struct FormChoice {
     int cached = 0;   // out: 1 when the form was remembered from an earlier timing
 };
 // Remember the measured-faster form of a (class, K_bra, K_ket, precision) signature.
-void remember_form(eri_class_t cls, int KB, int KK, int split, int form);
+void remember_form(eri_class_t cls, int KB, int KK, int split, int kind, int form);
 
-// Prepass + pair tables shared by eri_batch and eri_batch_grad.  ldelta > 0
-// also fills the adjoint tables.  Synchronises `st` once (reads the largest
-// contraction degree of each centre).  allow_swap = 0: the plain form as
-// given; 1: plain or swapped; 2: any of the four forms.
+// Prepass + pair tables shared by eri_batch, eri_batch3 and eri_batch_grad.
+// ldelta > 0 also fills the adjoint tables.  Synchronises `st` once (reads
+// the largest contraction degree of each centre).  allow_swap = 0: the plain
+// form as given; 1: plain or swapped; 2: any of the four forms.  kind = 0:
+// 4-centre; 1: 3-centre (the caller's bra pairs are (x, -1), -1 standing for
+// the unit function, an s Gaussian of exponent 0 and coefficient 1);
+// 2: 3-centre with x a real solid harmonic.
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
-                  int allow_swap, FormChoice* fc, int split = 0);
+                  int allow_swap, FormChoice* fc, int split = 0, int kind = 0);
 int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                  int64_t nket, const int64_t* quartets, int64_t nq, double* out, const ClassTables& ct,
                  const double* boys, const RStep* rs, int* dinfo, double* scratch, size_t scratch_doubles,
@@ -162,6 +178,7 @@ void count_launch();
 
 // Device workspace (grows, cached per process; calls on one device serialise)
 void* workspace(size_t bytes, int* err);
+void* aux_workspace(size_t bytes, int* err);  // a second cached buffer (3-centre pair lists)
 int* device_status();   // device error word
 int32_t* host_pinned_i32(int n);
 

@@ -116,7 +116,7 @@ struct ClassEntry {
     ClassTables t;
     void* blob = nullptr;
 };
-static std::map<std::tuple<int, int, int, int, int, int>, ClassEntry> g_classes;
+static std::map<std::tuple<int, int, int, int, int, int, int>, ClassEntry> g_classes;
 static std::mutex g_class_mu;
 
 // Horizontal-recursion levels of one side (l1, l2).  Level 0: the (e,0)
@@ -157,24 +157,92 @@ static HrrSide hrr_side(int l1, int l2)
     return h;
 }
 
-static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int hrr, cudaStream_t s, int* err);
+// Real regular solid harmonics S_lm (Racah normalisation, m = -l..l) as
+// polynomials in x, y, z, built by the recursions in l
+//   S_{l+1,+(l+1)} = sqrt(2^d (2l+1)/(2l+2)) (x S_{l,l} - (1-d) y S_{l,-l}),
+//   S_{l+1,-(l+1)} = sqrt(2^d (2l+1)/(2l+2)) (y S_{l,l} + (1-d) x S_{l,-l}),   d = [l == 0],
+//   S_{l+1,m} = ((2l+1) z S_{l,m} - sqrt((l+m)(l-m)) r^2 S_{l-1,m}) / sqrt((l+m+1)(l-m+1)),
+// from S_00 = 1; out[(m+l) * nc(l) + Cartesian index] (x^l first).
+void solid_harmonic_table(int l, double* out)
+{
+    using Poly = std::map<std::array<int, 3>, long double>;
+    auto mul = [](const Poly& P, int axis) {
+        Poly R;
+        for (auto& kv : P) {
+            auto e = kv.first;
+            ++e[axis];
+            R[e] += kv.second;
+        }
+        return R;
+    };
+    auto axpy = [](Poly& Y, long double a, const Poly& X) {
+        for (auto& kv : X) Y[kv.first] += a * kv.second;
+    };
+    std::vector<std::vector<Poly>> S(l + 1);  // S[k][m + k]
+    S[0].assign(1, Poly{{{0, 0, 0}, 1.0L}});
+    for (int k = 0; k < l; ++k) {
+        S[k + 1].assign(2 * k + 3, Poly{});
+        const long double d = k == 0 ? 1.0L : 0.0L;
+        const long double f = sqrtl(powl(2.0L, d) * (2 * k + 1) / (long double)(2 * k + 2));
+        const Poly& Skk = S[k][2 * k];
+        const Poly& Skm = S[k][0];
+        Poly top = mul(Skk, 0), bot = mul(Skk, 1);
+        if (k > 0) {
+            axpy(top, -1.0L, mul(Skm, 1));
+            axpy(bot, 1.0L, mul(Skm, 0));
+        }
+        for (auto& kv : top) S[k + 1][2 * k + 2][kv.first] = f * kv.second;
+        for (auto& kv : bot) S[k + 1][0][kv.first] = f * kv.second;
+        for (int m = -k; m <= k; ++m) {
+            Poly P;
+            axpy(P, (long double)(2 * k + 1), mul(S[k][m + k], 2));
+            if (k >= 1 && std::abs(m) <= k - 1) {
+                const Poly& Q = S[k - 1][m + k - 1];
+                const long double c = -sqrtl((long double)(k + m) * (k - m));
+                for (int ax = 0; ax < 3; ++ax) axpy(P, c, mul(mul(Q, ax), ax));
+            }
+            const long double den = sqrtl((long double)(k + m + 1) * (k - m + 1));
+            for (auto& kv : P) S[k + 1][m + k + 1][kv.first] = kv.second / den;
+        }
+    }
+    const auto cs = carts(l);
+    const int nc = (int)cs.size();
+    for (int m = 0; m <= 2 * l; ++m)
+        for (int i = 0; i < nc; ++i) {
+            auto it = S[l][m].find({cs[i][0], cs[i][1], cs[i][2]});
+            out[m * nc + i] = it == S[l][m].end() ? 0.0 : (double)it->second;
+        }
+}
+
+static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int hrr, int pure, cudaStream_t s,
+                                            int* err);
 
 const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t s, int* err)
 {
-    return class_tables_impl(la, lb, lc, ld, 0, s, err);
+    return class_tables_impl(la, lb, lc, ld, 0, 0, s, err);
 }
 
 const ClassTables* get_class_tables_hrr(int la, int lb, int lc, int ld, cudaStream_t s, int* err)
 {
-    return class_tables_impl(la, lb, lc, ld, 1, s, err);
+    return class_tables_impl(la, lb, lc, ld, 1, 0, s, err);
 }
 
-static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int hrr, cudaStream_t s, int* err)
+const ClassTables* get_class_tables_pure(int la, int lb, int lc, int ld, int pure, cudaStream_t s, int* err)
+{
+    if ((pure == 1 && lb != 0) || (pure == 2 && ld != 0) || pure < 1 || pure > 2) {
+        *err = ERI_EINVAL;
+        return nullptr;
+    }
+    return class_tables_impl(la, lb, lc, ld, 0, pure, s, err);
+}
+
+static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int hrr, int pure, cudaStream_t s,
+                                            int* err)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_class_mu);
-    auto key = std::make_tuple(dev, la, lb, lc, ld, hrr);
+    auto key = std::make_tuple(dev, la, lb, lc, ld, hrr, pure);
     auto it = g_classes.find(key);
     if (it != g_classes.end()) return &it->second.t;
 
@@ -220,10 +288,48 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
                 start.push_back((int)herm.size());
             }
     };
+    // a solid-harmonic side (l1, l2 = 0): row m holds the terminal Hermite
+    // functions t = a, |a| = l1, of the Cartesians a in S_{l1 m}, each E
+    // product (E_{a_i,0}^{a_i}) scaled by the coefficient of x^a in S_{l1 m}
+    auto build_terms_pure = [](int l1, std::vector<int>& start, std::vector<int16_t>& herm,
+                               std::vector<uint8_t>& fac, std::vector<double>& scale) {
+        const auto cs = carts(l1);
+        const int nc = (int)cs.size();
+        std::vector<double> T((size_t)(2 * l1 + 1) * nc);
+        solid_harmonic_table(l1, T.data());
+        start.push_back(0);
+        for (int m = 0; m <= 2 * l1; ++m) {
+            for (int i = 0; i < nc; ++i) {
+                const double c = T[(size_t)m * nc + i];
+                if (std::fabs(c) < 1e-14) continue;
+                herm.push_back((int16_t)herm_index(cs[i][0], cs[i][1], cs[i][2]));
+                for (int x = 0; x < 3; ++x) fac.push_back((uint8_t)(cs[i][x] * (l1 + 1) + cs[i][x]));
+                scale.push_back(c);
+            }
+            start.push_back((int)herm.size());
+        }
+    };
     std::vector<int> bs, ks;
     std::vector<int16_t> bp, kq, pq;
     std::vector<uint8_t> bf, kf;
-    if (hrr) {
+    std::vector<double> bsc, ksc;
+    t.pure = pure;
+    t.pb0 = 0;
+    if (pure) {
+        if (pure == 1) {
+            build_terms_pure(la, bs, bp, bf, bsc);
+            build_terms(lc, ld, ks, kq, kf);
+            t.nab = 2 * la + 1;
+            t.pb0 = host_nh(la - 1);  // only the Hermite functions of order la
+        } else {
+            build_terms(la, lb, bs, bp, bf);
+            build_terms_pure(lc, ks, kq, kf, ksc);
+            t.ncd = 2 * lc + 1;
+        }
+        t.hrr = 0;
+        t.nab_f = t.nab;
+        t.ncd_f = t.ncd;
+    } else if (hrr) {
         build_terms_hrr(la, lb, bs, bp, bf);
         build_terms_hrr(lc, ld, ks, kq, kf);
         t.hrr = 1;
@@ -284,8 +390,11 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
     size_t o_bp = take(bp.size() * 2), o_kq = take(kq.size() * 2), o_pq = take(pq.size() * 2);
     size_t o_pq2b = take(pq2b.size() * 2), o_pq2k = take(pq2k.size() * 2), o_h3 = take(h3.size() * 2);
     size_t o_bst = take(hb.steps.size() * 2 + 2), o_kst = take(hk.steps.size() * 2 + 2);
+    size_t o_bsc = take(bsc.size() * 8), o_ksc = take(ksc.size() * 8);
     size_t o_bf = take(bf.size()), o_kf = take(kf.size());
     std::vector<uint8_t> host(off);
+    if (!bsc.empty()) std::memcpy(host.data() + o_bsc, bsc.data(), bsc.size() * 8);
+    if (!ksc.empty()) std::memcpy(host.data() + o_ksc, ksc.data(), ksc.size() * 8);
     std::memcpy(host.data() + o_bs, bs.data(), bs.size() * 4);
     std::memcpy(host.data() + o_ks, ks.data(), ks.size() * 4);
     std::memcpy(host.data() + o_bp, bp.data(), bp.size() * 2);
@@ -322,6 +431,8 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
     t.ksteps = (const int16_t*)(b + o_kst);
     t.bra_fac = b + o_bf;
     t.ket_fac = b + o_kf;
+    t.bra_scale = bsc.empty() ? nullptr : (const double*)(b + o_bsc);
+    t.ket_scale = ksc.empty() ? nullptr : (const double*)(b + o_ksc);
     ClassEntry& e = g_classes[key];
     e.t = t;
     e.blob = blob;
@@ -405,6 +516,8 @@ const double* get_boys_table(int L, cudaStream_t s, int* err)
 struct DevState {
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    void* aux = nullptr;
+    size_t aux_bytes = 0;
     int* status = nullptr;
 };
 static std::map<int, DevState> g_dev;
@@ -431,6 +544,29 @@ void* workspace(size_t bytes, int* err)
     }
     d.ws_bytes = want;
     return d.ws;
+}
+
+void* aux_workspace(size_t bytes, int* err)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevState& d = g_dev[dev];
+    if (bytes <= d.aux_bytes) return d.aux;
+    if (d.aux) {
+        cudaDeviceSynchronize();
+        cudaFree(d.aux);
+        d.aux = nullptr;
+        d.aux_bytes = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&d.aux, want) != cudaSuccess) {
+        cudaGetLastError();
+        *err = ERI_ENOMEM;
+        return nullptr;
+    }
+    d.aux_bytes = want;
+    return d.aux;
 }
 
 int* device_status()
@@ -474,6 +610,7 @@ void release_all()
         auto it = g_dev.find(dev);
         if (it != g_dev.end()) {
             if (it->second.ws) cudaFree(it->second.ws);
+            if (it->second.aux) cudaFree(it->second.aux);
             if (it->second.status) cudaFree(it->second.status);
             g_dev.erase(it);
         }

@@ -428,9 +428,12 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
         for (int ii = 0; ii < IC && i0 + ii < KB; ++ii) {
             const int i = i0 + ii;
             // ---- B: ket transform + ket contraction
-            const int nB = TQ * nhb * ncd;
+            // only the bra Hermite functions the bra transform reads (all of
+            // them, or those of order la for a solid-harmonic bra)
+            const int nhbu = nhb - ct.pb0;
+            const int nB = TQ * nhbu * ncd;
             for (int item = tid; item < nB; item += kNT) {
-                const int q = item % TQ, r = item / TQ, p = r % nhb, cd = r / nhb;
+                const int q = item % TQ, r = item / TQ, p = ct.pb0 + r % nhbu, cd = r / nhbu;
                 const double* Ek = a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd;
                 const double* Rc = sR + (q * IC + ii) * KK;  // + e * NIs + k
                 const int16_t* pqrow = s_pq + p * nhk;

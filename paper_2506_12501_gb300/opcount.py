@@ -139,3 +139,25 @@ def dense_flops(cls, Kbra: int, Kket: int) -> int:
     ncd = nc(lc) * nc(ld)
     per_prim = 50 + 3 * (math.comb(L + 4, 4) - (L + 1)) + 2 * nh(la + lb) * nh(lc + ld) * ncd
     return Kbra * Kket * per_prim + Kbra * 2 * nh(la + lb) * nc(la) * nc(lb) * ncd
+
+
+def sparse_flops3(cls3, Kx: int, Kket: int, pure: bool, swapped: bool, pure_terms: int = 0) -> int:
+    """FP64 flops of one 3-centre triple (x|cd) = (x 1|cd), 1 the unit
+    function, in the form the library ran: swapped = False transforms the cd
+    ket first over the x side's Hermite functions (only those of order lx for
+    a solid-harmonic x), swapped = True transforms x first.  pure_terms: the
+    number of nonzero Cartesian coefficients of the lx solid harmonics."""
+    lx, lc, ld = cls3
+    L = lx + lc + ld
+    tx = pure_terms if pure else terms(lx, 0)
+    nx = 2 * lx + 1 if pure else nc(lx)
+    tcd, ncd = terms(lc, ld), nc(lc) * nc(ld)
+    if not swapped:
+        kb, kk = Kx, Kket
+        ket = 2 * (nc(lx) if pure else nh(lx)) * tcd
+        bra = 2 * ncd * tx + nx * ncd
+    else:
+        kb, kk = Kket, Kx
+        ket = 2 * nh(lc + ld) * tx
+        bra = 2 * nx * tcd + ncd * nx
+    return kb * kk * (prim_quartet_flops(L) + ket) + kb * bra

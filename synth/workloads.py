@@ -27,6 +27,7 @@ __all__ = [
     "config1_pp_primitive", "class_sweep_pools", "class_sweep_batch", "all_classes",
     "molecule_geometry", "molecule_basis", "adjoint_workload", "split_batch",
     "small_random_batch", "unique_pairs", "class_batches", "all_unique_quartets", "density_weights",
+    "three_centre_pools", "three_centre_batch",
 ]
 
 
@@ -154,6 +155,44 @@ def class_sweep_batch(pools, cls, seed: int = 0, npairs: int = 2048, nq: int = 1
     ket = np.stack([rng.choice(pools[lc], npairs), rng.choice(pools[ld], npairs)], axis=1).astype(np.int32)
     quartets = np.stack([rng.integers(0, npairs, nq), rng.integers(0, npairs, nq)], axis=1).astype(np.int64)
     return bra, ket, quartets
+
+
+def three_centre_pools(seed: int = 0, lxmax: int = 3, lmax: int = 2, pool: int = 512, K: int = 3,
+                       cube: float = 12.0):
+    """The 3-centre workload: the class-sweep pools of orbital shells (l <= lmax,
+    K even-tempered primitives) plus, per l <= lxmax, ``pool`` uncontracted
+    auxiliary shells (K = 1, exponent log-uniform in [0.1, 10], as in
+    density-fitting bases), all on their own centres in a ``cube``-bohr box.
+    Returns (basis, orbital pools {l: shells}, auxiliary pools {l: shells})."""
+    rng = np.random.default_rng([seed, 3])
+    nob = (lmax + 1) * pool
+    nax = (lxmax + 1) * pool
+    centres = rng.uniform(0.0, cube, size=(nob + nax, 3))
+    shells = []
+    for l in range(lmax + 1):
+        for i in range(pool):
+            e = np.array([0.2 * 3.0 ** k for k in range(K)])
+            w = rng.uniform(0.5, 1.0, size=K)
+            shells.append((l * pool + i, l, list(e), list(w * norm_coef(e, l))))
+    for l in range(lxmax + 1):
+        for i in range(pool):
+            e = 10.0 ** rng.uniform(-1.0, 1.0, size=1)
+            shells.append((nob + l * pool + i, l, list(e), list(norm_coef(e, l))))
+    basis = basis_from_shells(centres, shells)
+    orb = {l: np.arange(l * pool, (l + 1) * pool, dtype=np.int32) for l in range(lmax + 1)}
+    aux = {l: np.arange(nob + l * pool, nob + (l + 1) * pool, dtype=np.int32) for l in range(lxmax + 1)}
+    return basis, orb, aux
+
+
+def three_centre_batch(orb, aux, cls3, seed: int = 0, nx: int = 2048, npairs: int = 2048, nt: int = 100_000):
+    """List-form 3-centre batch of class ``cls3`` = (lx, lc, ld): x shells,
+    ket pairs and (x index, ket index) triples drawn from the pools."""
+    lx, lc, ld = cls3
+    rng = np.random.default_rng([seed, 7, lx, lc, ld])
+    x = rng.choice(aux[lx], nx).astype(np.int32)
+    ket = np.stack([rng.choice(orb[lc], npairs), rng.choice(orb[ld], npairs)], axis=1).astype(np.int32)
+    t = np.stack([rng.integers(0, nx, nt), rng.integers(0, npairs, nt)], axis=1).astype(np.int64)
+    return x, ket, t
 
 
 def split_batch(cls, K: int, seed: int = 0, nq: int = 100_000, pool: int = 512, npairs: int = 2048):

@@ -53,3 +53,17 @@ def test_kernels_compiled_for_sm103a():
     """Every translation unit is compiled with -gencode arch=compute_103a,code=sm_103a."""
     from paper_2506_12501_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_solid_harmonic_tables_agree_without_gpu():
+    """The library builds its real solid harmonics by recursion in l (host
+    code, no GPU work); the oracle writes them from their closed form.  The
+    two independent constructions agree to round-off."""
+    import numpy as np
+
+    import oracle
+    import paper_2506_12501_gb300 as eri
+    for l in range(4):
+        assert np.allclose(eri.solid_harmonics(l), oracle.solid.c2s(l), rtol=0, atol=1e-14), l
+    with pytest.raises(eri.EriError):
+        eri.solid_harmonics(4)
