@@ -58,7 +58,9 @@ enum {
 enum {
     ERI_PREC_FP64 = 0,  /* everything in FP64 */
     ERI_PREC_SPLIT = 1  /* transforms in FP32 hi+lo split products with FP64
-                           accumulation; Boys, R and prefactors stay FP64 */
+                           accumulation; Boys, R and prefactors stay FP64;
+                           plain (side-swapped or not) forms only, since the
+                           horizontal recursion would magnify their rounding */
 };
 
 typedef struct {
@@ -160,7 +162,25 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
  * or a ket shell's l disagrees), ERI_ECUDA, ERI_ENOMEM.
  */
 /*
- * eri_solid_harmonics -- the real solid harmonics eri_batch3 uses, as
+ * eri_batch_sph -- the same batch as eri_batch with every centre in real
+ * solid harmonics (the functions of eri_solid_harmonics, m = -l..l): each
+ * shellset has (2la+1)(2lb+1)(2lc+1)(2ld+1) integrals,
+ * (ma mb|mc md) = sum C^a_ma C^b_mb C^c_mc C^d_md (ab|cd), laid out as in
+ * eri_batch with ab = (ma+la)(2lb+1) + (mb+lb) and likewise cd.  The
+ * transforms run on Cartesians (in any of the four forms); the mapping to
+ * solid harmonics is applied to the contracted block in the kernel's
+ * epilogue, so only the smaller solid-harmonic block is stored (the paper
+ * fuses these coefficients into its H matrices, Section 2.1).  Arguments,
+ * errors and synchronisation as in eri_batch.
+ */
+int eri_batch_sph(eri_class_t cls, const eri_basis_t* basis,
+                  const int32_t* bra_pairs, int64_t nbra,
+                  const int32_t* ket_pairs, int64_t nket,
+                  const int64_t* quartets, int64_t nq,
+                  double* out, int64_t out_len, int precision, void* stream);
+
+/*
+ * eri_solid_harmonics -- the real solid harmonics eri_batch3 and eri_batch_sph use, as
  * Cartesian coefficients: S_lm = sum_a out[(m+l)*nc(l) + a] x^ax y^ay z^az,
  * m = -l..l, a in the library's Cartesian order.  out is a HOST buffer of
  * (2l+1) nc(l) doubles; no GPU work.  ERI_EINVAL for l outside 0..ERI_LMAX.

@@ -13,6 +13,7 @@ from .binding import (  # noqa: F401
     eri_batch,
     eri_batch_grad,
     eri_batch3,
+    eri_batch_sph,
     solid_harmonics,
     eri_batch_noalloc,
     Plan,

@@ -43,7 +43,7 @@ class eri_basis_t(ctypes.Structure):
 EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
            "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc", "eri_plan_create",
            "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
-           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees", "eri_batch3", "eri_solid_harmonics"]
+           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees", "eri_batch3", "eri_solid_harmonics", "eri_batch_sph"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
             L.eri_boys.argtypes = [I, P, I64, P, P]
             L.eri_batch.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P, I64, I, P]
             L.eri_solid_harmonics.argtypes = [ctypes.c_int32, P]
+            L.eri_batch_sph.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P, I64, I, P]
             L.eri_batch3.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(eri_basis_t), P,
                                      I64, P, I64, P, I64, ctypes.c_int32, P, I64, I, P]
             L.eri_batch_grad.argtypes = [eri_class_t, ctypes.POINTER(eri_basis_t), P, I64, P, I64, P, I64, P, I64,
@@ -181,6 +182,26 @@ def eri_batch(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pairs: torch
                            _ptr(quartets), nq if nq is not None else 0, _ptr(out), out.numel(), precision,
                            _stream(stream))
     _check(code, "eri_batch")
+    return out
+
+
+def eri_batch_sph(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pairs: torch.Tensor,
+                  quartets: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                  precision: int = ERI_PREC_FP64, stream=None) -> torch.Tensor:
+    """Shellsets of class ``cls`` with every centre in real solid harmonics (see include/eri.h)."""
+    nbra, nket = bra_pairs.shape[0], ket_pairs.shape[0]
+    nq = quartets.shape[0] if quartets is not None else None
+    ns = (2 * cls[0] + 1) * (2 * cls[1] + 1) * (2 * cls[2] + 1) * (2 * cls[3] + 1)
+    n = (nq if nq is not None else nbra * nket) * ns
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=bra_pairs.device)
+    if n == 0:
+        return out
+    b = basis.struct()
+    code = lib().eri_batch_sph(eri_class_t(*cls), ctypes.byref(b), _ptr(bra_pairs), nbra, _ptr(ket_pairs), nket,
+                               _ptr(quartets), nq if nq is not None else 0, _ptr(out), out.numel(), precision,
+                               _stream(stream))
+    _check(code, "eri_batch_sph")
     return out
 
 

@@ -81,6 +81,37 @@ __device__ __forceinline__ void boys_eval(int L, double T, const double* __restr
 // so every source is read before it is overwritten).
 // FP64 cost: one multiply per entry, plus one FMA where the coefficient
 // e_i - 1 is nonzero.
+// The same recursion for one primitive quartet shared by the 32 lanes of a
+// warp (every lane holds the same base, X, Y, Z): each level is rewritten in
+// chunks of 32 entries, highest first; a chunk's lanes read their sources
+// (always of lower index) before any of them writes.  All lanes must call it.
+template <typename RPtr>
+__device__ __forceinline__ void r_recursion_warp(int L, const double* base, double X, double Y, double Z,
+                                                 const RStep* __restrict__ st, RPtr R, int lane)
+{
+    if (lane == 0) R[0] = base[L];
+    __syncwarp();
+    for (int n = L - 1; n >= 0; --n) {
+        const int N = L - n;
+        const int top = (N + 1) * (N + 2) * (N + 3) / 6;  // Nh(N)
+        for (int c0 = top - 1; c0 >= 1; c0 -= 32) {
+            const int e = c0 - lane;
+            double v = 0.0;
+            if (e >= 1) {
+                const RStep s = st[e];
+                const double x = s.axis == 0 ? X : (s.axis == 1 ? Y : Z);
+                v = x * R[s.src1];
+                if (s.coef) v = fma(s.coefd, R[s.src2], v);
+            }
+            __syncwarp();
+            if (e >= 1) R[e] = v;
+            __syncwarp();
+        }
+        if (lane == 0) R[0] = base[n];
+        __syncwarp();
+    }
+}
+
 template <typename RPtr>
 __device__ __forceinline__ void r_recursion(int L, const double* base, double X, double Y, double Z,
                                             const RStep* __restrict__ st, RPtr R)

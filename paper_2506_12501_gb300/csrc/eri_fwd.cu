@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -48,8 +49,33 @@ struct PrepassArgs {
     int64_t nq;
     int l[4];
     int unit_b;  // 1: every bra pair's second shell is -1, the unit function (3-centre)
-    int* info;   // [0..3] max K per centre, [4] error
+    int* info;   // [0..3] max K per centre, [4] error, [5..6] recursion risk (float bits)
+    // recursion risk (risk = 1): per pair (2|A-B|)^l2 max_ij exp(-mu_ij |A-B|^2),
+    // the factor by which the horizontal recursion can magnify the pair's
+    // rounding relative to its integrals; the largest over bra (ket) pairs
+    int risk;
+    const double* centres;
+    const int32_t* shell_atom;
+    const int32_t* shell_off;
+    const double* exps;
 };
+
+// (2|A-B|)^l2 max over primitive pairs of exp(-z1 z2 / (z1 + z2) |A-B|^2)
+__device__ float pair_recursion_risk(const PrepassArgs& a, int s1, int s2, int l2)
+{
+    if (l2 == 0) return 1.0f;
+    const double* A = a.centres + 3 * a.shell_atom[s1];
+    const double* B = a.centres + 3 * a.shell_atom[s2];
+    const double d2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
+    double mu = 1e300;
+    for (int i = 0; i < a.shell_K[s1]; ++i)
+        for (int j = 0; j < a.shell_K[s2]; ++j) {
+            const double z1 = a.exps[a.shell_off[s1] + i], z2 = a.exps[a.shell_off[s2] + j];
+            mu = fmin(mu, z1 * z2 / (z1 + z2));
+        }
+    const double amp = pow(2.0 * sqrt(d2), (double)l2);
+    return (float)fmin(amp * exp(-mu * d2), 3.0e38);
+}
 
 __device__ __forceinline__ void set_err(int* p, int code) { atomicCAS(p, 0, code); }
 
@@ -79,6 +105,16 @@ __global__ void prepass_kernel(PrepassArgs a)
                     continue;
                 }
                 atomicMax(&a.info[2 * side + c], K);
+            }
+            if (a.risk) {
+                const int s1 = pr[2 * i], s2 = pr[2 * i + 1];
+                if (s1 >= 0 && s1 < a.nshell && s2 >= 0 && s2 < a.nshell) {
+                    const int K1 = a.shell_K[s1], K2 = a.shell_K[s2];
+                    if (K1 >= 1 && K1 <= kKmax && K2 >= 1 && K2 <= kKmax) {
+                        const float r = pair_recursion_risk(a, s1, s2, a.l[2 * side + 1]);
+                        atomicMax(&a.info[5 + side], __float_as_int(r));  // r >= 0: int order = float order
+                    }
+                }
             }
         }
         if (a.quartets && i < a.nq) {
@@ -315,10 +351,16 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     tp->sEkS = e_smem ? odd_up(KK * ct.Tcd) : 0;
     size_t r_need = (size_t)((TQ * IC * KK) | 1) * ct.nhl;  // odd row stride
     size_t hA = 0, hB = 0;
-    if (ct.hrr) {
-        // the recursion buffers alias every staging region before the tables
-        // (E, pair scalars, R, X are dead in the epilogue); grow R if short
-        hrr_buffers(ct, TQ, &hA, &hB);
+    if (ct.hrr || ct.sph) {
+        // the recursion (and solid-harmonic) buffers alias every staging
+        // region before the tables (E, pair scalars, R, X are dead in the
+        // epilogue); grow R if short
+        if (ct.hrr) hrr_buffers(ct, TQ, &hA, &hB);
+        if (ct.sph) {  // each solid-harmonic step reads one buffer and writes the other
+            const size_t nf = (size_t)TQ * ct.nab_f * ct.ncd_f;
+            hA = std::max(hA, nf);
+            hB = std::max(hB, nf);
+        }
         const size_t staged = even((size_t)TQ * tp->sEbS) + even((size_t)TQ * tp->sEkS) +
                               even((size_t)TQ * KB * PS_N) + even((size_t)TQ * KK * PS_N) + even(r_need) +
                               even((size_t)TQ * ct.nhb * ct.ncd);
@@ -408,6 +450,10 @@ static size_t align_up(size_t n) { return (n + 255) & ~size_t(255); }
 
 // Prepass + pair tables shared by the forward and adjoint entry points.
 // On success fills the pair tables and the largest K on each centre.
+// Largest product of bra and ket recursion risks for which the recursion
+// forms are offered (see prepass_kernel): 1.1e-16 x 900 x O(10) ~ 1e-12.
+constexpr double kRecursionRisk = 900.0;
+
 // Forms eri_batch may use (eri_set_forms): bit o allows form o.
 static std::atomic<int> g_form_mask{0xF};
 
@@ -443,11 +489,13 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
 {
     int err = ERI_OK;
     // kind 2: the caller's bra side (x, unit) is a solid harmonic
-    auto tables = [&](int la, int lb, int lc, int ld, int x_first) {
-        return kind == 2 ? get_class_tables_pure(la, lb, lc, ld, x_first ? 1 : 2, st, &err)
-                         : get_class_tables(la, lb, lc, ld, st, &err);
+    // kind 3: solid-harmonic output on every centre (plain or recursion form)
+    auto tables = [&](int la, int lb, int lc, int ld, int x_first, int hrr) {
+        if (kind == 2) return get_class_tables_pure(la, lb, lc, ld, x_first ? 1 : 2, st, &err);
+        if (kind == 3) return get_class_tables_sph(la, lb, lc, ld, hrr, st, &err);
+        return hrr ? get_class_tables_hrr(la, lb, lc, ld, st, &err) : get_class_tables(la, lb, lc, ld, st, &err);
     };
-    const ClassTables* ct = tables(cls.la, cls.lb, cls.lc, cls.ld, 1);
+    const ClassTables* ct = tables(cls.la, cls.lb, cls.lc, cls.ld, 1, 0);
     if (!ct) return err;
     *ct_out = ct;
     const int forced = fc ? fc->form : -1;
@@ -462,10 +510,11 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
     if (!hinfo) return ERI_ENOMEM;
     // info lives in the status block (slots 8..12), separate from the error word
     int* dinfo = status + 8;
-    if (cudaMemsetAsync(dinfo, 0, 5 * sizeof(int), st) != cudaSuccess) return ERI_ECUDA;
+    if (cudaMemsetAsync(dinfo, 0, 7 * sizeof(int), st) != cudaSuccess) return ERI_ECUDA;
     PrepassArgs pa{basis->shell_l, basis->shell_K, basis->nshell, bra, nbra, ket, nket, quartets,
                    quartets ? nq : (int64_t)0,
-                   {cls.la, cls.lb, cls.lc, cls.ld}, kind > 0 ? 1 : 0, dinfo};
+                   {cls.la, cls.lb, cls.lc, cls.ld}, (kind == 1 || kind == 2) ? 1 : 0, dinfo,
+                   allow_swap > 1 ? 1 : 0, basis->centres, basis->shell_atom, basis->shell_off, basis->exps};
     const int64_t n = std::max(std::max(nbra, nket), quartets ? nq : (int64_t)0);
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
     {
@@ -473,7 +522,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         prepass_kernel<<<std::max(grid, 1), 256, 0, st>>>(pa);
     }
     if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
-    if (cudaMemcpyAsync(hinfo, dinfo, 5 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ERI_ECUDA;
+    if (cudaMemcpyAsync(hinfo, dinfo, 7 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ERI_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return ERI_ECUDA;
     if (hinfo[4] != 0) return dev_err_to_code(hinfo[4]);
     for (int c = 0; c < 4; ++c) kmax[c] = hinfo[c];
@@ -485,11 +534,19 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         // the transforms run on (e0) functions followed by horizontal
         // recursions in the contracted basis.  The FP64-work model picks one
         // unless a form is forced or an earlier timing chose one.
-        const ClassTables* opt[4] = {ct, tables(cls.lc, cls.ld, cls.la, cls.lb, 0), nullptr, nullptr};
+        const ClassTables* opt[4] = {ct, tables(cls.lc, cls.ld, cls.la, cls.lb, 0, 0), nullptr, nullptr};
         if (!opt[1]) return err;
-        if (allow_swap > 1 && kind == 0) {
-            opt[2] = get_class_tables_hrr(cls.la, cls.lb, cls.lc, cls.ld, st, &err);
-            opt[3] = get_class_tables_hrr(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
+        // The recursion forms must keep their magnified rounding, about
+        // 1.1e-16 x (bra risk) x (ket risk) x the integrals' scale, well
+        // inside the 1e-11 absolute bar: they are offered only while the
+        // product of the largest pair risks stays below kRecursionRisk.
+        float rb, rk;
+        std::memcpy(&rb, &hinfo[5], 4);
+        std::memcpy(&rk, &hinfo[6], 4);
+        const bool hrr_ok = (double)rb * (double)rk <= kRecursionRisk;
+        if (allow_swap > 1 && (kind == 0 || kind == 3) && hrr_ok) {
+            opt[2] = tables(cls.la, cls.lb, cls.lc, cls.ld, 1, 1);
+            opt[3] = tables(cls.lc, cls.ld, cls.la, cls.lb, 0, 1);
             if (!opt[2] || !opt[3]) return err;
         }
         const int64_t nqq = quartets ? nq : nbra * nket;
@@ -778,8 +835,9 @@ static int forward_args(const eri_basis_t* basis, const int32_t* bra_pairs, int6
     a->nbra = nbra;  // original roles: output layout and product-form decoding
     a->nket = nket;
     a->swap = swapped;
-    a->nab_o = swapped ? ct->ncd_f : ct->nab_f;
-    a->ncd_o = swapped ? ct->nab_f : ct->ncd_f;
+    const int nab_out = ct->sph ? ct->nab_s : ct->nab_f, ncd_out = ct->sph ? ct->ncd_s : ct->ncd_f;
+    a->nab_o = swapped ? ncd_out : nab_out;
+    a->ncd_o = swapped ? nab_out : ncd_out;
     a->out = out;
     a->bra_sh = swapped ? ket_pairs : bra_pairs;  // the kernel's lists
     a->ket_sh = swapped ? bra_pairs : ket_pairs;
@@ -807,9 +865,14 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
     FormChoice fc;
+    // The recursion forms are FP64 only: the horizontal recursion multiplies
+    // the (e0|f0) values by powers of A-B and C-D, which magnifies the split
+    // transforms' rounding (about 1e-14 of those larger values) past the
+    // 1e-10 bar when the centres are far apart.  3-centre batches have none.
+    const int allow = (kind == 1 || kind == 2 || split) ? 1 : 2;
     auto prepare = [&](FormChoice* f, FwdArgs* a, TilePlan* tp) {
         int e = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB,
-                              &KK, kmax, kind ? 1 : 2, f, split, kind);
+                              &KK, kmax, allow, f, split, kind);
         if (e != ERI_OK) return e;
         return forward_args(basis, bra_pairs, nbra, ket_pairs, nket, quartets, nqq, out, ct, pb, pk, KB, KK,
                             f->form & 1, st, a, tp);
@@ -894,6 +957,22 @@ extern "C" int eri_solid_harmonics(int32_t l, double* out)
     return ERI_OK;
 }
 
+extern "C" int eri_batch_sph(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
+                             const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq,
+                             double* out, int64_t out_len, int precision, void* stream)
+{
+    int err = check_batch_args(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, INT64_MAX);
+    if (err != ERI_OK) return err;
+    if (precision != ERI_PREC_FP64 && precision != ERI_PREC_SPLIT) return ERI_EINVAL;
+    const int64_t nqq = quartets ? nq : nbra * nket;
+    const int64_t ns = (int64_t)(2 * cls.la + 1) * (2 * cls.lb + 1) * (2 * cls.lc + 1) * (2 * cls.ld + 1);
+    if (out_len < nqq * ns) return ERI_EINVAL;
+    if (nqq == 0 || nbra == 0 || nket == 0) return ERI_OK;
+    if (!out) return ERI_EINVAL;
+    return run_forward(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, out,
+                       precision == ERI_PREC_SPLIT, 3, (cudaStream_t)stream);
+}
+
 __global__ void unit_pairs_kernel(const int32_t* __restrict__ x, int64_t n, int32_t* __restrict__ out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -957,7 +1036,8 @@ int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, 
 {
     if (cudaMemsetAsync(dinfo, 0, 5 * sizeof(int), st) != cudaSuccess) return ERI_ECUDA;
     PrepassArgs pa{basis->shell_l, basis->shell_K, basis->nshell, bra, nbra, ket, nket, quartets,
-                   quartets ? nq : (int64_t)0, {cls.la, cls.lb, cls.lc, cls.ld}, 0, dinfo};
+                   quartets ? nq : (int64_t)0, {cls.la, cls.lb, cls.lc, cls.ld}, 0, dinfo, 0,
+                   nullptr, nullptr, nullptr, nullptr};
     const int64_t n = std::max(std::max(nbra, nket), quartets ? nq : (int64_t)0);
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
     count_launch();

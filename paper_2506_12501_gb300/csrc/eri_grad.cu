@@ -199,8 +199,11 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
 
         for (int i0 = 0; i0 < KB; i0 += IC) {
             __syncthreads();
-            // ---- A: auxiliary integrals up to order L+2 for (q, i0+ii, k)
-            for (int item = tid; item < NI; item += kGT) {
+            // ---- A: auxiliary integrals up to order L+2 for (q, i0+ii, k);
+            // with few items a warp shares each item's recursion
+            const bool coop = NI * 4 < kGT;
+            const int lane = tid & 31;
+            for (int item = coop ? tid >> 5 : tid; item < NI; item += coop ? kGT / 32 : kGT) {
                 const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
                 const int i = i0 + ii;
                 struct S {
@@ -224,9 +227,12 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                         base[n] *= f;
                         f *= m2rho;
                     }
-                    r_recursion(L2, base, X, Y, Z, a.rsteps, R);
+                    if (coop)
+                        r_recursion_warp(L2, base, X, Y, Z, a.rsteps, R, lane);
+                    else
+                        r_recursion(L2, base, X, Y, Z, a.rsteps, R);
                 } else {
-                    for (int e = 0; e < nhl2; ++e) R[e] = 0.0;
+                    for (int e = coop ? lane : 0; e < nhl2; e += coop ? 32 : 1) R[e] = 0.0;
                 }
             }
             // axis tables and exponents of the chunk's bra primitives

@@ -77,6 +77,12 @@ struct ClassTables {
     // only the terminal Hermite functions |t| = l, each E product scaled by
     // the Cartesian coefficient of the harmonic (Section 3.2.3).
     int pure;
+    // Solid-harmonic output (4-centre): the epilogue maps the contracted
+    // Cartesian block to real solid harmonics on every centre, one index at
+    // a time, with c2s[i] = [2l+1][nc(l)] of centre i (null for l = 0).
+    int sph;
+    int nab_s, ncd_s;             // (2la+1)(2lb+1), (2lc+1)(2ld+1)
+    const double* c2s[4];
     int pb0;                      // first bra Hermite function the transforms need
     const double* bra_scale;      // [Tab] per-term factors, or null
     const double* ket_scale;      // [Tcd]
@@ -101,6 +107,8 @@ const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t
 const ClassTables* get_class_tables_hrr(int la, int lb, int lc, int ld, cudaStream_t s, int* err);
 // pure: 1 = the (la, lb = 0) side a solid harmonic, 2 = the (lc, ld = 0) side
 const ClassTables* get_class_tables_pure(int la, int lb, int lc, int ld, int pure, cudaStream_t s, int* err);
+// Tables of the solid-harmonic output form (plain or recursion form).
+const ClassTables* get_class_tables_sph(int la, int lb, int lc, int ld, int hrr, cudaStream_t s, int* err);
 // Real solid harmonics (Racah normalisation) as [2l+1][nc(l)] Cartesian coefficients.
 void solid_harmonic_table(int l, double* out);
 const double* get_boys_table(int L, cudaStream_t s, int* err);    // rows of F_{L+k}(T_j)/k!, plus exp
@@ -138,7 +146,8 @@ void remember_form(eri_class_t cls, int KB, int KK, int split, int kind, int for
 // form as given; 1: plain or swapped; 2: any of the four forms.  kind = 0:
 // 4-centre; 1: 3-centre (the caller's bra pairs are (x, -1), -1 standing for
 // the unit function, an s Gaussian of exponent 0 and coefficient 1);
-// 2: 3-centre with x a real solid harmonic.
+// 2: 3-centre with x a real solid harmonic; 3: 4-centre with solid-harmonic
+// output on every centre.
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],

@@ -215,7 +215,7 @@ void solid_harmonic_table(int l, double* out)
 }
 
 static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int hrr, int pure, cudaStream_t s,
-                                            int* err);
+                                            int* err, int sph = 0);
 
 const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t s, int* err)
 {
@@ -225,6 +225,11 @@ const ClassTables* get_class_tables(int la, int lb, int lc, int ld, cudaStream_t
 const ClassTables* get_class_tables_hrr(int la, int lb, int lc, int ld, cudaStream_t s, int* err)
 {
     return class_tables_impl(la, lb, lc, ld, 1, 0, s, err);
+}
+
+const ClassTables* get_class_tables_sph(int la, int lb, int lc, int ld, int hrr, cudaStream_t s, int* err)
+{
+    return class_tables_impl(la, lb, lc, ld, hrr, 0, s, err, 1);
 }
 
 const ClassTables* get_class_tables_pure(int la, int lb, int lc, int ld, int pure, cudaStream_t s, int* err)
@@ -237,12 +242,12 @@ const ClassTables* get_class_tables_pure(int la, int lb, int lc, int ld, int pur
 }
 
 static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int hrr, int pure, cudaStream_t s,
-                                            int* err)
+                                            int* err, int sph)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_class_mu);
-    auto key = std::make_tuple(dev, la, lb, lc, ld, hrr, pure);
+    auto key = std::make_tuple(dev, la, lb, lc, ld, hrr, pure * 2 + sph);
     auto it = g_classes.find(key);
     if (it != g_classes.end()) return &it->second.t;
 
@@ -390,9 +395,24 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
     size_t o_bp = take(bp.size() * 2), o_kq = take(kq.size() * 2), o_pq = take(pq.size() * 2);
     size_t o_pq2b = take(pq2b.size() * 2), o_pq2k = take(pq2k.size() * 2), o_h3 = take(h3.size() * 2);
     size_t o_bst = take(hb.steps.size() * 2 + 2), o_kst = take(hk.steps.size() * 2 + 2);
+    // solid-harmonic output: the four centres' coefficient tables
+    const int ls[4] = {la, lb, lc, ld};
+    std::vector<double> c2s[4];
+    size_t o_c2s[4] = {0, 0, 0, 0};
+    t.sph = sph;
+    t.nab_s = (2 * la + 1) * (2 * lb + 1);
+    t.ncd_s = (2 * lc + 1) * (2 * ld + 1);
+    for (int i = 0; i < 4; ++i) {
+        if (!sph || ls[i] == 0) continue;
+        c2s[i].resize((size_t)(2 * ls[i] + 1) * host_nc(ls[i]));
+        solid_harmonic_table(ls[i], c2s[i].data());
+        o_c2s[i] = take(c2s[i].size() * 8);
+    }
     size_t o_bsc = take(bsc.size() * 8), o_ksc = take(ksc.size() * 8);
     size_t o_bf = take(bf.size()), o_kf = take(kf.size());
     std::vector<uint8_t> host(off);
+    for (int i = 0; i < 4; ++i)
+        if (!c2s[i].empty()) std::memcpy(host.data() + o_c2s[i], c2s[i].data(), c2s[i].size() * 8);
     if (!bsc.empty()) std::memcpy(host.data() + o_bsc, bsc.data(), bsc.size() * 8);
     if (!ksc.empty()) std::memcpy(host.data() + o_ksc, ksc.data(), ksc.size() * 8);
     std::memcpy(host.data() + o_bs, bs.data(), bs.size() * 4);
@@ -431,6 +451,7 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
     t.ksteps = (const int16_t*)(b + o_kst);
     t.bra_fac = b + o_bf;
     t.ket_fac = b + o_kf;
+    for (int i = 0; i < 4; ++i) t.c2s[i] = c2s[i].empty() ? nullptr : (const double*)(b + o_c2s[i]);
     t.bra_scale = bsc.empty() ? nullptr : (const double*)(b + o_bsc);
     t.ket_scale = ksc.empty() ? nullptr : (const double*)(b + o_ksc);
     ClassEntry& e = g_classes[key];

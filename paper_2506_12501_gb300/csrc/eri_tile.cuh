@@ -327,6 +327,48 @@ static __device__ void digest_exchange(const FwdArgs& a, const double* V, int nq
     }
 }
 
+// One index of the contracted block mapped to solid harmonics:
+// out[(o nout + m) inner + i] = sum_k M[m][k] in[(o nin + k) inner + i].
+static __device__ void contract_index(const double* in, double* out, const double* __restrict__ M, int outer,
+                                      int nin, int nout, int inner)
+{
+    for (int item = threadIdx.x; item < outer * nout * inner; item += kNT) {
+        const int i = item % inner, r = item / inner, m = r % nout, o = r / nout;
+        const double* row = M + m * nin;
+        const double* src = in + (size_t)o * nin * inner + i;
+        double v = 0.0;
+        for (int k = 0; k < nin; ++k) {
+            const double c = row[k];
+            if (c != 0.0) v = fma(c, src[(size_t)k * inner], v);
+        }
+        out[item] = v;
+    }
+    __syncthreads();
+}
+
+// Solid-harmonic output: the Cartesian block [ab][cd][q] in buf[cur] becomes
+// [ma mb][mc md][q] (m = -l..l on every centre), one centre at a time,
+// alternating between buf[0] and buf[1]; returns the final buffer.
+static __device__ const double* to_solid_harmonics(const FwdArgs& a, double* const buf[2], int cur)
+{
+    const ClassTables& ct = a.ct;
+    const int TQ = a.TQ;
+    const int na = (ct.la + 1) * (ct.la + 2) / 2, nb = (ct.lb + 1) * (ct.lb + 2) / 2;
+    const int nc = (ct.lc + 1) * (ct.lc + 2) / 2, nd = (ct.ld + 1) * (ct.ld + 2) / 2;
+    const int sa = 2 * ct.la + 1, sb = 2 * ct.lb + 1, sc = 2 * ct.lc + 1, sd = 2 * ct.ld + 1;
+    // (outer, nin, nout, inner) of the four steps: a, b, then c, d
+    const int steps[4][4] = {{1, na, sa, nb * nc * nd * TQ},
+                             {sa, nb, sb, nc * nd * TQ},
+                             {sa * sb, nc, sc, nd * TQ},
+                             {sa * sb * sc, nd, sd, TQ}};
+    for (int i = 0; i < 4; ++i) {
+        if (!ct.c2s[i]) continue;  // l = 0: the identity
+        contract_index(buf[cur], buf[cur ^ 1], ct.c2s[i], steps[i][0], steps[i][1], steps[i][2], steps[i][3]);
+        cur ^= 1;
+    }
+    return buf[cur];
+}
+
 // One tile: quartets q0 .. q0+nqt-1 (the class tables are already staged).
 // s_red: one shared double for the digestion sum.
 template <bool SPLIT>
@@ -392,10 +434,15 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     for (int i0 = 0; i0 < KB; i0 += IC) {
         __syncthreads();
         // ---- A: auxiliary integrals of the primitive quartets (q, i0+ii, k)
-        for (int item = tid; item < NI; item += kNT) {
+        // few items (small tiles of high-l classes with K = 1): a warp shares
+        // each item's recursion instead of leaving most threads idle
+        const bool coop = NI * 4 < kNT;
+        const int lane = tid & 31;
+        for (int item = coop ? tid >> 5 : tid; item < NI; item += coop ? kNT / 32 : kNT) {
             const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
             const int i = i0 + ii;
             Strided R{sR + item, NIs};
+            const int e0 = coop ? lane : 0, de = coop ? 32 : 1;
             if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
                 const double* pb = sPb + (q * KB + i) * PS_N;
                 const double* pk = sPk + (q * KK + k) * PS_N;
@@ -413,15 +460,18 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     base[n] *= f;
                     f *= m2rho;
                 }
-                r_recursion(ct.L, base, X, Y, Z, a.rsteps, R);
+                if (coop)
+                    r_recursion_warp(ct.L, base, X, Y, Z, a.rsteps, R, lane);
+                else
+                    r_recursion(ct.L, base, X, Y, Z, a.rsteps, R);
                 if (SPLIT)  // each entry becomes its (hi, lo) float pair, in place
-                    for (int e = 0; e < nhl; ++e) {
+                    for (int e = e0; e < nhl; e += de) {
                         double& slot = R[e];
                         const float2 f = split_f64(slot);
                         reinterpret_cast<float2&>(slot) = f;
                     }
             } else {
-                for (int e = 0; e < nhl; ++e) R[e] = 0.0;
+                for (int e = e0; e < nhl; e += de) R[e] = 0.0;
             }
         }
         __syncthreads();
@@ -547,7 +597,20 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     if (a.acc_regs) {
         const int nC = TQ * nab * ncd;
         double esum = 0.0;
-        if (!ct.hrr && (a.Jmat || a.Kmat)) {
+        if (!ct.hrr && ct.sph) {
+            double* buf[2] = {sm, sm + a.o_hB};
+#pragma unroll
+            for (int s = 0; s < kNACC; ++s) {
+                const int item = tid + s * kNT;
+                if (item < nC) buf[0][item] = acc[s];
+            }
+            __syncthreads();
+            const double* fin = to_solid_harmonics(a, buf, 0);
+            for (int item = tid; item < TQ * ct.nab_s * ct.ncd_s; item += kNT) {
+                const int q = item % TQ, r = item / TQ, cd = r % ct.ncd_s, ab = r / ct.ncd_s;
+                if (q < nqt) a.out[out_index(a, q0 + q, ab, cd)] = fin[item];
+            }
+        } else if (!ct.hrr && (a.Jmat || a.Kmat)) {
             // the values go to shared memory (the staging regions are dead)
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
@@ -623,7 +686,13 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 __syncthreads();
             }
             const double* fin = hbuf[g & 1];  // [ab][cd][q]
-            if (a.Jmat || a.Kmat) {
+            if (ct.sph) {
+                const double* fs = to_solid_harmonics(a, hbuf, g & 1);
+                for (int item = tid; item < TQ * ct.nab_s * ct.ncd_s; item += kNT) {
+                    const int q = item % TQ, r = item / TQ, cd = r % ct.ncd_s, ab = r / ct.ncd_s;
+                    if (q < nqt) a.out[out_index(a, q0 + q, ab, cd)] = fs[item];
+                }
+            } else if (a.Jmat || a.Kmat) {
                 if (a.Jmat) digest_coulomb(a, fin, nqt, s_q, sm + a.o_dj);
                 if (a.Kmat) digest_exchange(a, fin, nqt, s_q, sm + a.o_dj);
             } else {

@@ -51,12 +51,13 @@ def test_f_classes_every_form(cuda, cls):
         eri.eri_set_forms(0)
 
 
-@pytest.mark.parametrize("cls,K,nq", [((2, 2, 2, 2), 1, 2000), ((3, 3, 3, 3), 1, 300), ((3, 3, 2, 2), 1, 1000),
-                                      ((2, 2, 2, 2), 5, 60), ((3, 3, 3, 3), 5, 8), ((3, 3, 2, 2), 5, 20)])
+@pytest.mark.parametrize("cls,K,nq", [((2, 2, 2, 2), 1, 4000), ((3, 3, 3, 3), 1, 1000), ((3, 3, 2, 2), 1, 3000),
+                                      ((2, 2, 2, 2), 5, 600), ((3, 3, 3, 3), 5, 40), ((3, 3, 2, 2), 5, 300)])
 def test_split_against_fp64_path(cuda, cls, K, nq):
     """The split-precision form stays within 1e-10 absolute of the FP64 form on
-    the high-l workload (K = 1 and K = 5 per shell)."""
-    basis, bra, ket, q = synth.split_batch(cls, K=K, seed=100 + K, nq=nq, pool=64, npairs=48)
+    the high-l workload (K = 1 and K = 5 per shell), with the benchmark's
+    spread of centres (512-shell pools in a 12-bohr cube, 2048 pairs)."""
+    basis, bra, ket, q = synth.split_batch(cls, K=K, seed=100 + K, nq=nq, pool=512, npairs=2048)
     f64 = gpu_list(cls, basis, bra, ket, q)
     spl = gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT)
     err = np.abs(spl - f64)
@@ -84,3 +85,31 @@ def test_split_low_l_contracted(cuda, cls):
     f64 = gpu_list(cls, basis, bra, ket, q)
     spl = gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT)
     assert_close(spl, f64, atol=1e-10, rtol=0.0, what=f"split sweep {cls}")
+
+
+def test_recursion_form_accuracy_guard(cuda):
+    """The horizontal-recursion forms magnify rounding by about
+    (2|A-B|)^l_b (2|C-D|)^l_d for pairs whose prefactor is not negligible.  On
+    the high-l workload (exponents down to 0.05, centres up to 20 bohr apart)
+    the library must refuse them, even when forced, and the FP64 result must
+    stay at the parity bar against the oracle on a sample; on the class-sweep
+    geometry a forced recursion form still runs."""
+    cls = (3, 3, 2, 2)
+    basis, bra, ket, q = synth.split_batch(cls, K=5, seed=0, nq=2000)
+    db = eri.DeviceBasis(basis)
+    try:
+        eri.eri_set_forms(eri.ERI_FORM_HRR)
+        got = gpu_list(cls, basis, bra, ket, q, dbasis=db)
+        assert eri.eri_last_form()[1] is False
+    finally:
+        eri.eri_set_forms(0)
+    sample = np.random.default_rng(1).choice(len(q), 24, replace=False)
+    assert_close(got[sample], oracle_blocks(cls, basis, bra, ket, q[sample]), what="guarded (ff|dd) K=5")
+    sbasis, pools = synth.class_sweep_pools(seed=0, pool=64, K=3)
+    sbra, sket, sq = synth.class_sweep_batch(pools, (2, 2, 2, 2), seed=3, npairs=40, nq=50)
+    try:
+        eri.eri_set_forms(eri.ERI_FORM_HRR)
+        gpu_list((2, 2, 2, 2), sbasis, sbra, sket, sq)
+        assert eri.eri_last_form()[1] is True
+    finally:
+        eri.eri_set_forms(0)
