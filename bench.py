@@ -300,7 +300,9 @@ def adjoint_variant(args, eri, dev, timed):
     pairs, batches = synth.all_unique_quartets(basis)
     torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees this variant too
     db = eri.DeviceBasis(basis)
+    from paper_2506_12501_gb300 import opcount
     tf = tg = 0.0
+    gflop = 0.0
     nq_tot = 0
     for cls, (bra, ket, q) in batches.items():
         q = q[: args.adjoint_nq]
@@ -315,10 +317,17 @@ def adjoint_variant(args, eri, dev, timed):
         tf += timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o), reps=1)
         tg += timed(lambda: eri.eri_batch_grad(cls, db, b, k, qq, Wd, gc, ge), reps=1)
         nq_tot += len(q)
+        Ks = basis.shell_K
+        kb = (Ks[bra[q[:, 0], 0]] * Ks[bra[q[:, 0], 1]]).astype(np.int64)
+        kk = (Ks[ket[q[:, 1], 0]] * Ks[ket[q[:, 1], 1]]).astype(np.int64)
+        for (x, y), n in zip(*np.unique(np.stack([kb, kk], 1), axis=0, return_counts=True)):
+            gflop += n * opcount.grad_flops(cls, int(x), int(y))
     torch.cuda.profiler.stop()
     return {"workload": f"16-atom molecule basis, {len(batches)} classes, <= {args.adjoint_nq} "
                         "quartets per class", "quartets": nq_tot, "fwd_ms": tf, "grad_ms": tg,
-            "grad_over_fwd": tg / tf, "grad_quartets_per_s": nq_tot / (tg / 1e3)}
+            "grad_over_fwd": tg / tf, "grad_quartets_per_s": nq_tot / (tg / 1e3),
+            "grad_gflops_sparse": gflop / (tg / 1e3) / 1e9,
+            "grad_frac_fp64_peak_sparse": gflop / (tg / 1e3) / 1e9 / FP64_PEAK_GFLOPS}
 
 
 def batched_variant(args, eri, dev, timed):

@@ -161,3 +161,28 @@ def sparse_flops3(cls3, Kx: int, Kket: int, pure: bool, swapped: bool, pure_term
         ket = 2 * nh(lc + ld) * tx
         bra = 2 * nx * tcd + ncd * nx
     return kb * kk * (prim_quartet_flops(L) + ket) + kb * bra
+
+
+def _grad_launch_flops(cls, Kbra: int, Kket: int) -> int:
+    """FP64 flops of one adjoint launch (the channels of the kernel's bra):
+    per primitive quartet the auxiliary integrals to order L+2 and the ket
+    transform over the raised bra Hermite range; per bra primitive the
+    contraction with W and the 8 channel terms (about 40 flops for each
+    (ab, p') whose Hermite indices stay within a_i + b_i + 2)."""
+    la, lb, lc, ld = cls
+    L = la + lb + lc + ld
+    nhb2 = nh(la + lb + 2)
+    nab, ncd = nc(la) * nc(lb), nc(lc) * nc(ld)
+    support = 0
+    for a in carts(la):
+        for b in carts(lb):
+            support += math.prod(a[i] + b[i] + 3 for i in range(3))
+    return Kbra * Kket * (prim_quartet_flops(L + 2) + 2 * nhb2 * terms(lc, ld)) + \
+        Kbra * (2 * nab * nhb2 * ncd + 40 * support)
+
+
+def grad_flops(cls, Kbra: int, Kket: int) -> int:
+    """FP64 flops of the adjoint of one quartet: the bra channels, then the
+    ket channels in a second launch with the sides exchanged."""
+    la, lb, lc, ld = cls
+    return _grad_launch_flops(cls, Kbra, Kket) + _grad_launch_flops((lc, ld, la, lb), Kket, Kbra)
