@@ -77,3 +77,57 @@ def test_two_rank_energy_equals_single_rank():
     assert out[0][0] == out[1][0]
     assert abs(total - single) <= 1e-12 * max(1.0, abs(single))
     assert out[0][1] > 0 and out[1][1] > 0
+
+
+def _partial_coulomb(basis, shells, D):
+    """J' over a share of the unique quartets with the plans' weighting rule
+    (2s, s = 1/2 per coincident pair or pair of pairs); J = J' + J'^T."""
+    n = (basis.shell_l + 1) * (basis.shell_l + 2) // 2
+    off = np.concatenate([[0], np.cumsum(n)[:-1]])
+    nbf = int(n.sum())
+    Jp = np.zeros((nbf, nbf))
+    if len(shells) == 0:
+        return Jp
+    vals = oracle.eri_quartets(basis, shells, prec="d")
+    pos = 0
+    for a, b, c, d in shells:
+        na, nb, nc_, nd = n[a], n[b], n[c], n[d]
+        blk = vals[pos:pos + na * nb * nc_ * nd].reshape(na, nb, nc_, nd)
+        pos += na * nb * nc_ * nd
+        w = 2.0 * (0.5 if a == b else 1.0) * (0.5 if c == d else 1.0) * (0.5 if {a, b} == {c, d} else 1.0)
+        sa, sb, sc, sd = (slice(off[x], off[x] + n[x]) for x in (a, b, c, d))
+        Jp[sa, sb] += w * np.einsum("abcd,cd->ab", blk, D[sc, sd])
+        Jp[sc, sd] += w * np.einsum("abcd,ab->cd", blk, D[sa, sb])
+    return Jp
+
+
+def _j_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        basis, shells, costs = _quartets()
+        nbf = int(((basis.shell_l + 1) * (basis.shell_l + 2) // 2).sum())
+        U = np.random.default_rng(2).uniform(-1, 1, (nbf, nbf))
+        D = np.triu(U) + np.triu(U, 1).T
+        mine = shard.partition(costs, world)[rank]
+        Jp = shard.allreduce_sum(_partial_coulomb(basis, shells[mine], D).ravel(), dist).reshape(nbf, nbf)
+        out[rank] = (Jp + Jp.T, (_partial_coulomb(basis, shells, D), D) if rank == 0 else None)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_coulomb_matrix_equals_single_rank():
+    """Sharded J digestion: per-rank J' over each rank's quartets, one
+    all-reduce, then J = J' + J'^T equals the single-rank J."""
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    out = mp.get_context("spawn").Manager().dict()
+    mp.start_processes(_j_worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    J0, J1 = out[0][0], out[1][0]
+    Jp_single, _ = out[0][1]
+    J_single = Jp_single + Jp_single.T
+    assert np.array_equal(J0, J1)
+    assert np.abs(J0 - J_single).max() <= 1e-12 * np.abs(J_single).max()
