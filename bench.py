@@ -390,6 +390,7 @@ def run_library(args):
     eri.lib()
 
     only = tuple(int(x) for x in args.only_class) if args.only_class else None
+    prec = eri.ERI_PREC_SPLIT if args.precision == "split" else eri.ERI_PREC_FP64
     basis, batches = sweep(seed=rank, only=only, nq=args.nq)
     nq_class = args.nq
     db = eri.DeviceBasis(basis)
@@ -410,7 +411,7 @@ def run_library(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            eri.eri_batch(cls, db, b, k, q, out=outs[cls])
+            eri.eri_batch(cls, db, b, k, q, out=outs[cls], precision=prec)
             forms[cls] = eri.eri_last_form()
             if timing is not None:
                 e1.record(stream)
@@ -501,7 +502,7 @@ def run_library(args):
             off = 0
             for cls in batches:
                 b, k, q = (d.copy_(h, non_blocking=True) for d, h in zip(dev_batches[cls], host_in[cls]))
-                eri.eri_batch(cls, db, b, k, q, out=outs[cls])
+                eri.eri_batch(cls, db, b, k, q, out=outs[cls], precision=prec)
                 n = outs[cls].numel()
                 host_out[off:off + n].copy_(outs[cls], non_blocking=True)
                 off += n
@@ -529,7 +530,8 @@ def run_library(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == eri.ERI_PREC_FP64 else "f64+f32x2",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD if only is None else f"single class {args.only_class}, {nq_class} quartets",
                        "classes": len(batches), "quartets_per_class": nq_class,
                        "K_per_shell": K_PER_SHELL, "pairs_per_side": NPAIRS, "pool_per_l": POOL,
@@ -562,6 +564,8 @@ def main():
     ap.add_argument("--molecule-natom", type=int, default=16)
     ap.add_argument("--three-nt", type=int, default=100_000, help="triples per 3-centre class")
     ap.add_argument("--nq", type=int, default=NQ_PER_CLASS, help="quartets per class")
+    ap.add_argument("--precision", choices=["fp64", "split"], default="fp64",
+                    help="transforms of the timed sweep (profiling aid; the benchmark value is fp64)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
