@@ -352,7 +352,11 @@ def batched_variant(args, eri, dev, timed):
         kb, kk = plan.job_degrees(j)
         flops += nq * opcount.sparse_flops(cls, kb, kk, form=(False, False))
     e = torch.zeros(1, dtype=torch.float64, device=dev)
+    plan.execute(D=Dm, energy=e)  # graph capture outside the profiled region
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed replays
     t_exec = timed(lambda: plan.execute(D=Dm, energy=e), reps=2)
+    torch.cuda.profiler.stop()
     J = torch.empty_like(Dm)
     t_j = timed(lambda: plan.coulomb(Dm, J), reps=2)
     K = torch.empty_like(Dm)

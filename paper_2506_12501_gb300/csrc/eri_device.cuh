@@ -44,6 +44,8 @@ __device__ __forceinline__ void boys_eval(int L, double T, const double* __restr
         f = fma(f, md, r23.x);
         f = fma(f, md, r01.y);
         f = fma(f, md, r01.x);
+        F[L] = f;
+        if (L == 0) return;  // exp(-T) only feeds the downward recursion
         double e = 1.0 / 720.0;
         e = fma(e, md, 1.0 / 120.0);
         e = fma(e, md, 1.0 / 24.0);
@@ -52,7 +54,6 @@ __device__ __forceinline__ void boys_eval(int L, double T, const double* __restr
         e = fma(e, md, 1.0);
         e = fma(e, md, 1.0);
         const double eT = r67.y * e;
-        F[L] = f;
         const double twoT = T + T;
         for (int n = L - 1; n >= 0; --n) {
             f = fma(twoT, f, eT) * c_inv_odd[n];

@@ -393,7 +393,7 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     return tp->bytes <= (size_t)max_smem_optin();
 }
 
-bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best)
+bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best, size_t max_bytes)
 {
     bool found = false;
     double best_score = -1.0;
@@ -403,7 +403,7 @@ bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* bes
             if (TQ > 1 && (int64_t)TQ > 2 * nq) continue;
             for (int IC = KB; IC >= 1; IC = (IC + 1) / 2 - (IC == 1)) {
                 TilePlan tp;
-                if (!tile_layout(ct, KB, KK, TQ, IC, e_smem, &tp)) {
+                if (!tile_layout(ct, KB, KK, TQ, IC, e_smem, &tp) || (max_bytes && tp.bytes > max_bytes)) {
                     if (IC == 1) break;
                     continue;
                 }

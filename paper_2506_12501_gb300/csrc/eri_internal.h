@@ -171,7 +171,8 @@ struct TilePlan {
     int o_dj;         // Coulomb digestion scratch (TQ + nab_f doubles)
     size_t bytes;
 };
-bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best);
+// max_bytes > 0: only shapes whose shared memory stays within it
+bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best, size_t max_bytes = 0);
 bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp);
 
 // Measurement hook: events around launches of kernel `id` (eri_profile_*).

@@ -132,7 +132,7 @@ __global__ void plan_finish_kernel(const PlanParams* p)
 }
 
 template <bool SPLIT>
-__global__ void __launch_bounds__(kNT, 1)
+__global__ void __launch_bounds__(kNT, 2)
     plan_kernel(const FwdArgs* __restrict__ jobs, const WorkItem* __restrict__ items, int64_t nitems,
                 const PlanParams* __restrict__ pp)
 {
@@ -225,12 +225,14 @@ static bool autotune_job(const FwdArgs& base, const std::vector<WorkItem>& sampl
                          cudaStream_t st, TilePlan* best)
 {
     std::vector<TilePlan> cands;
+    const size_t half_sm = (size_t)smem_per_sm() / 2 - 1024;
     for (int TQ = 1; TQ <= 128; TQ *= 2) {
         if (TQ * base.ct.nab * base.ct.ncd > kNT * kNACC) break;
         for (int IC : {base.KB, (base.KB + 1) / 2, 1}) {
             for (int es = 1; es >= 0; --es) {
                 TilePlan tp;
-                if (tile_layout(base.ct, base.KB, base.KK, TQ, IC, es, &tp) && tp.acc_regs) {
+                // shapes within half an SM's shared memory (two CTAs per SM)
+                if (tile_layout(base.ct, base.KB, base.KK, TQ, IC, es, &tp) && tp.acc_regs && tp.bytes <= half_sm) {
                     bool dup = false;
                     for (auto& c : cands) dup |= (c.TQ == TQ && c.IC == IC && c.e_smem == es);
                     if (!dup) cands.push_back(tp);
@@ -322,6 +324,7 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
         return ERI_EINVAL;
     if (flags & ~(ERI_PLAN_STORE | ERI_PLAN_SPLIT | ERI_PLAN_NO_TUNE)) return ERI_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    const size_t half_sm = (size_t)smem_per_sm() / 2 - 1024;
     eri_plan* p = new eri_plan();
     p->flags = flags;
     p->threshold = threshold;
@@ -511,7 +514,11 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
             const int KB = bt == A ? KA : KBt;  // primitive pairs of the bra type
             const int KK = bt == A ? KBt : KA;  // and of the ket type
             TilePlan tp;
-            if (!plan_tiles(*ct, KB, KK, nq, &tp) || !tp.acc_regs) return plan_fail(p, ERI_EINVAL);
+            // the persistent kernel runs every job with the largest job's
+            // shared memory: keep each job within half an SM so two CTAs fit
+            if (!(plan_tiles(*ct, KB, KK, nq, &tp, half_sm) && tp.acc_regs) &&
+                !(plan_tiles(*ct, KB, KK, nq, &tp) && tp.acc_regs))
+                return plan_fail(p, ERI_EINVAL);
             FwdArgs& a = J.args;
             a = FwdArgs{};
             a.ct = *ct;

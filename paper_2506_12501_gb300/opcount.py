@@ -62,9 +62,11 @@ def r_recursion_flops(L: int) -> int:
 
 
 def prim_quartet_flops(L: int) -> int:
-    """setup (rho, T, prefactor: 15 + rsqrt counted as 2), Boys (Taylor 12,
-    exp(-T) 13, 2T 1, downward 3 per order), scaling 2 per order, recursion"""
-    return 17 + 26 + 3 * L + 2 * (L + 1) + r_recursion_flops(L)
+    """setup (rho, T, prefactor: 15 + rsqrt counted as 2), Boys (Taylor 12;
+    for L > 0 also exp(-T) 13, 2T 1 and the downward recursion, 3 per
+    order), scaling 2 per order, recursion"""
+    boys = 12 + (14 + 3 * L if L > 0 else 0)
+    return 17 + boys + 2 * (L + 1) + r_recursion_flops(L)
 
 
 def terms_hrr(l1: int, l2: int) -> int:
