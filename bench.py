@@ -304,6 +304,7 @@ def adjoint_variant(args, eri, dev, timed):
     tf = tg = 0.0
     gflop = 0.0
     nq_tot = 0
+    per = {}
     for cls, (bra, ket, q) in batches.items():
         q = q[: args.adjoint_nq]
         W = synth.density_weights(cls, bra, ket, q, D, bf_off)
@@ -314,8 +315,11 @@ def adjoint_variant(args, eri, dev, timed):
         o = torch.empty(W.size, dtype=torch.float64, device=dev)
         gc = torch.zeros_like(db.centres)
         ge = torch.zeros_like(db.exps)
-        tf += timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o), reps=1)
-        tg += timed(lambda: eri.eri_batch_grad(cls, db, b, k, qq, Wd, gc, ge), reps=1)
+        t_f = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o), reps=1)
+        t_g = timed(lambda: eri.eri_batch_grad(cls, db, b, k, qq, Wd, gc, ge), reps=1)
+        tf += t_f
+        tg += t_g
+        per["".join(map(str, cls))] = {"quartets": len(q), "fwd_ms": t_f, "grad_ms": t_g}
         nq_tot += len(q)
         Ks = basis.shell_K
         kb = (Ks[bra[q[:, 0], 0]] * Ks[bra[q[:, 0], 1]]).astype(np.int64)
@@ -327,7 +331,7 @@ def adjoint_variant(args, eri, dev, timed):
                         "quartets per class", "quartets": nq_tot, "fwd_ms": tf, "grad_ms": tg,
             "grad_over_fwd": tg / tf, "grad_quartets_per_s": nq_tot / (tg / 1e3),
             "grad_gflops_sparse": gflop / (tg / 1e3) / 1e9,
-            "grad_frac_fp64_peak_sparse": gflop / (tg / 1e3) / 1e9 / FP64_PEAK_GFLOPS}
+            "grad_frac_fp64_peak_sparse": gflop / (tg / 1e3) / 1e9 / FP64_PEAK_GFLOPS, "per_class": per}
 
 
 def batched_variant(args, eri, dev, timed):
@@ -495,6 +499,18 @@ def run_library(args):
         h2d = sum(t.numel() * t.element_size() for v in host_in.values() for t in v) + \
             sum(t.numel() * t.element_size() for t in host_basis.values())
         d2h = host_out.numel() * 8
+        # each class's integrals go back to the host on a second stream while
+        # the next class computes.  A class's copy is queued only after the
+        # next eri_batch call has returned: that call reads a few bytes back
+        # (its validation pass), and a read queued behind a large copy on the
+        # device-to-host engine would stall it.  The step ends when every
+        # copy has landed.
+        cstream = torch.cuda.Stream(device=dev)
+
+        def read_back(p):
+            cstream.wait_event(p[3])
+            with torch.cuda.stream(cstream):
+                host_out[p[1]:p[1] + p[2]].copy_(outs[p[0]], non_blocking=True)
         e_ms = []
         for it in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
@@ -504,12 +520,18 @@ def run_library(args):
             for k_, t in host_basis.items():
                 getattr(db, k_).copy_(t.reshape(getattr(db, k_).shape), non_blocking=True)
             off = 0
+            pending = None
             for cls in batches:
                 b, k, q = (d.copy_(h, non_blocking=True) for d, h in zip(dev_batches[cls], host_in[cls]))
                 eri.eri_batch(cls, db, b, k, q, out=outs[cls], precision=prec)
-                n = outs[cls].numel()
-                host_out[off:off + n].copy_(outs[cls], non_blocking=True)
-                off += n
+                done = torch.cuda.Event()
+                done.record(stream)
+                if pending is not None:
+                    read_back(pending)
+                pending = (cls, off, outs[cls].numel(), done)
+                off += outs[cls].numel()
+            read_back(pending)
+            stream.wait_stream(cstream)
             a1.record(stream)
             torch.cuda.synchronize()
             if it > 0:

@@ -102,12 +102,16 @@ __device__ __forceinline__ void herm_of(int idx, int* t, int* u, int* v)
     *v = N - *t - *u;
 }
 
+// Small integers as doubles (the factors a_i of the lowering terms).
+__constant__ double c_int_d[8] = {0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0};
+
 // The 8 channel contributions of one Hermite function p' = (t,u,v) of the
 // component pair (a, b) of one bra primitive pair, times y = T[ab][p'].
-// Ax: the three per-axis tables E[i][j][t] (i <= l1+2, j <= l2+2).
+// Ax: the three per-axis tables E[i][j][t] (i <= l1+2, j <= l2+2);
+// tz1, tz2: twice the two exponents.
 __device__ __forceinline__ void channel_terms(int l1, int l2, const int qa[3], const int qb[3], const int tt[3],
-                                              const double* __restrict__ Ax, int eax, double z1, double z2, double y,
-                                              double ch[8])
+                                              const double* __restrict__ Ax, int eax, double tz1, double tz2,
+                                              double y, double ch[8])
 {
     const int n2 = l2 + 3, nt = l1 + l2 + 5;
     auto Ev = [&](int x, int i, int j, int t) -> double {
@@ -127,8 +131,8 @@ __device__ __forceinline__ void channel_terms(int l1, int l2, const int qa[3], c
     for (int x = 0; x < 3; ++x) {
         const int o1 = (x + 1) % 3, o2 = (x + 2) % 3;
         const double rest = base[o1] * base[o2] * y;
-        const double ga = 2.0 * z1 * up1[x] - (double)(float)qa[x] * dn1[x];
-        const double gb = 2.0 * z2 * upb1[x] - (double)(float)qb[x] * dnb1[x];
+        const double ga = fma(tz1, up1[x], -c_int_d[qa[x]] * dn1[x]);
+        const double gb = fma(tz2, upb1[x], -c_int_d[qb[x]] * dnb1[x]);
         ch[x] = fma(ga, rest, ch[x]);
         ch[3 + x] = fma(gb, rest, ch[3 + x]);
         ch[6] = fma(-up2[x], rest, ch[6]);
@@ -242,7 +246,8 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 double v = 0.0;
                 if (i < s_q[4 * q + 2]) {
                     const size_t slot = (size_t)s_q[4 * q] * KB + i;
-                    v = c < 3 * eax ? a.pb.ax[slot * 3 * eax + c] : a.pb.zz[slot * 2 + (c - 3 * eax)];
+                    // the axis tables, then twice the two exponents
+                    v = c < 3 * eax ? a.pb.ax[slot * 3 * eax + c] : 2.0 * a.pb.zz[slot * 2 + (c - 3 * eax)];
                 }
                 sA[idx] = v;
             }
