@@ -297,3 +297,50 @@ def test_plan_exchange_against_oracle(cuda):
     with pytest.raises(eri.EriError) as ex:
         plan.jk(Dd, want_j=False, want_k=False)
     assert ex.value.code == eri.ERI_EPLAN
+
+
+def test_plan_full_size_sampled(cuda):
+    """The benchmark's batched workload (16 atoms, Schwarz 1e-12, 1.08e7
+    unique quartets) in store mode: a sample of 200 quartets spread over the
+    jobs against the oracle, and the energy digestion against the stored
+    integrals weighted by D_ab D_cd (summed on the GPU)."""
+    basis = synth.molecule_basis(natom=16, radius=7.0 * (16 / 64) ** (1 / 3), seed=0)
+    _, nbf = bf_offsets(basis)
+    db = eri.DeviceBasis(basis)
+    store = eri.Plan(db, threshold=1e-12, flags=eri.ERI_PLAN_STORE)
+    info = store.info()
+    out = torch.empty(info["out_len"], dtype=torch.float64, device=cuda)
+    store.execute(out=out)
+    torch.cuda.synchronize()
+    assert store.status() == eri.ERI_OK
+    rng = np.random.default_rng(8)
+    U = rng.uniform(-1, 1, (nbf, nbf))
+    D = np.triu(U) + np.triu(U, 1).T
+    Dd = torch.as_tensor(D, device=cuda)
+    off_bf, _ = bf_offsets(basis)
+    offd = torch.as_tensor(off_bf, device=cuda)
+    e_store = 0.0
+    sampled, refs = [], []
+    njobs = info["njobs"]
+    for j in range(njobs):
+        cls, nq, off, shells = store.job(j, with_quartets=True)
+        n = [nc(l) for l in cls]
+        blk = out[off:off + nq * int(np.prod(n))].view(int(np.prod(n)), nq)  # [abcd][q]
+        sh = torch.as_tensor(shells, device=cuda, dtype=torch.int64)
+        idx = [offd[sh[:, i]][:, None] + torch.arange(n[i], device=cuda)[None, :] for i in range(4)]
+        Dab = Dd[idx[0][:, :, None], idx[1][:, None, :]].reshape(nq, -1)
+        Dcd = Dd[idx[2][:, :, None], idx[3][:, None, :]].reshape(nq, -1)
+        W = (Dab[:, :, None] * Dcd[:, None, :]).reshape(nq, -1).T
+        e_store += float((blk * W).sum())
+        pick = rng.choice(nq, min(nq, max(1, 200 // njobs + 1)), replace=False)
+        sampled.append(blk[:, torch.as_tensor(pick, device=cuda)].T.cpu().numpy())
+        refs.append(oracle.eri_quartets(basis, shells[pick], prec="d", threads=THREADS).reshape(len(pick), -1))
+    for got, ref in zip(sampled, refs):
+        assert_close(got, ref, what="plan store, 16 atoms")
+    e = torch.zeros(1, dtype=torch.float64, device=cuda)
+    plan = eri.Plan(db, threshold=1e-12)
+    assert plan.info()["nquartets"] == info["nquartets"]
+    plan.execute(D=Dd, energy=e)
+    assert plan.status() == eri.ERI_OK
+    # the two sums take different orders over 1e7 quartets (atomics): relative round-off only
+    assert abs(float(e.item()) - e_store) <= 1e-10 * max(1.0, abs(e_store)), (float(e.item()), e_store)
