@@ -40,6 +40,10 @@
 namespace eri {
 
 constexpr int64_t kChunk = 512;  // quartets per work item (at most)
+// static shared memory of the plan kernel (job arguments and a few words),
+// taken off the dynamic budget that lets two CTAs share an SM
+constexpr size_t kPlanStaticSmem = 1024 + 256;
+static_assert(sizeof(FwdArgs) + 64 <= kPlanStaticSmem, "plan kernel static shared memory budget");
 
 struct WorkItem {
     int32_t job, bra;
@@ -140,6 +144,10 @@ __global__ void __launch_bounds__(kNT, 2)
     __shared__ double s_red;
     __shared__ int64_t s_item;
     __shared__ int s_stop;
+    // the current job's arguments, one copy per CTA (a per-thread copy would
+    // live in local memory under the two-CTA register bound); thread 0
+    // writes it between barriers, every thread reads it
+    __shared__ FwdArgs a;
     const int tid = threadIdx.x;
     const PlanParams P = *pp;
     if (tid == 0) {
@@ -148,7 +156,6 @@ __global__ void __launch_bounds__(kNT, 2)
     }
     const long long t_start = clock64();
     int cur = -1;
-    FwdArgs a;
     for (;;) {
         __syncthreads();
         if (tid == 0) {
@@ -163,22 +170,29 @@ __global__ void __launch_bounds__(kNT, 2)
         if (item >= nitems) break;
         const WorkItem it = items[item];
         if (it.job != cur) {
-            a = jobs[it.job];
-            a.energy = P.energy;
-            a.Jmat = P.J;
-            a.Kmat = P.K;
-            a.D = P.D;
-            a.nbf = P.nbf;
-            if (P.out) a.out = P.out + (int64_t)(size_t)a.out;  // stored as an offset
+            if (tid == 0) {
+                a = jobs[it.job];
+                a.energy = P.energy;
+                a.Jmat = P.J;
+                a.Kmat = P.K;
+                a.D = P.D;
+                a.nbf = P.nbf;
+                if (P.out) a.out = P.out + (int64_t)(size_t)a.out;  // stored as an offset
+            }
             __syncthreads();
             stage_class_tables(a, sm);
             cur = it.job;
         }
-        a.rbra = it.bra;
-        for (int64_t k = it.k0; k < it.k1; k += a.TQ) {
-            a.rk0 = k;
-            a.rq0 = it.q0 + (k - it.k0);
-            tile_body<SPLIT>(a, a.rq0, (int)min((int64_t)a.TQ, it.k1 - k), sm, &s_red);
+        const int TQ = a.TQ;
+        for (int64_t k = it.k0; k < it.k1; k += TQ) {
+            __syncthreads();  // the previous tile no longer reads the range fields
+            if (tid == 0) {
+                a.rbra = it.bra;
+                a.rk0 = k;
+                a.rq0 = it.q0 + (k - it.k0);
+            }
+            // tile_body starts with a barrier, after which every thread sees them
+            tile_body<SPLIT>(a, it.q0 + (k - it.k0), (int)min((int64_t)TQ, it.k1 - k), sm, &s_red);
         }
     }
 }
@@ -225,7 +239,7 @@ static bool autotune_job(const FwdArgs& base, const std::vector<WorkItem>& sampl
                          cudaStream_t st, TilePlan* best)
 {
     std::vector<TilePlan> cands;
-    const size_t half_sm = (size_t)smem_per_sm() / 2 - 1024;
+    const size_t half_sm = (size_t)smem_per_sm() / 2 - 1024 - kPlanStaticSmem;
     for (int TQ = 1; TQ <= 128; TQ *= 2) {
         if (TQ * base.ct.nab * base.ct.ncd > kNT * kNACC) break;
         for (int IC : {base.KB, (base.KB + 1) / 2, 1}) {
@@ -324,7 +338,7 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
         return ERI_EINVAL;
     if (flags & ~(ERI_PLAN_STORE | ERI_PLAN_SPLIT | ERI_PLAN_NO_TUNE)) return ERI_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t half_sm = (size_t)smem_per_sm() / 2 - 1024;
+    const size_t half_sm = (size_t)smem_per_sm() / 2 - 1024 - kPlanStaticSmem;
     eri_plan* p = new eri_plan();
     p->flags = flags;
     p->threshold = threshold;
