@@ -12,14 +12,21 @@
 //                  (the forward ket transform, over the raised bra range),
 //   T_i[ab][p']  = sum_cd W_abcd X'_i[p'][cd],
 //   dE/dch      += sum_ab sum_p' G^ch_{i;ab,p'} T_i[ab][p']
-// for the 8 channels of the bra (3 per centre, 2 exponents).  The ket's
+// for the 8 channels of the bra (3 per centre, 2 exponents).  G^ch is a
+// product of one-dimensional tables, so T is formed only for the (ab, p')
+// where some channel's G is non-zero, and each T value is folded into the
+// channels as soon as it is formed.  The ket's
 // channels come from a second launch with the sides exchanged, since
 // (ab|cd) = (cd|ab).  The auxiliary integrals [r]^(0) (order up to L+2) are
 // recomputed, not stored.  Channel sums are reduced per quartet in shared
 // memory and added atomically to the gradients (only the order of the
 // additions varies).
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "eri_device.cuh"
 #include "eri_internal.h"
@@ -44,8 +51,12 @@ struct GradArgs {
     const double* W;
     double* gc;                // [natom][3] or null
     double* ge;                // [nprim] or null
+    const int2* items;         // channel items of the bra class (see ItemTable)
+    int nit;                   // their number
+    int ND, PST;               // derived-table entries per axis and value; doubles per bra primitive
+    int Ws, Eks;               // shared-memory row strides of W and of the ket E products (odd)
     int TQ, KB, KK, IC;
-    int o_q, o_W, o_Pb, o_Pk, o_Ek, o_A, o_R, o_X, o_T, o_ch, o_che;
+    int o_q, o_W, o_Pb, o_Pk, o_Ek, o_D, o_R, o_X, o_ch, o_che;
     int64_t ntiles;
 };
 
@@ -72,73 +83,92 @@ __device__ __forceinline__ int64_t g_windex(const GradArgs& a, int64_t qq, int a
     return bra + a.nbra * (abo + (int64_t)a.nab_o * (cdo + (int64_t)a.ncd_o * ket));
 }
 
-// Cartesian component k of a shell of angular momentum l (x^l first).
-__device__ __forceinline__ void cart_of(int l, int k, int q[3])
+// ---------------------------------------------------------------------------
+// Channel items.  The bra channels of one (ab, p') with p' = (t, u, v) are
+//   d/dA_i:    (2 zeta_a E^{a+1_i,b} - a_i E^{a-1_i,b})_{t_i} * prod_{j != i} E^{ab}_{t_j}
+//   d/dB_i:    (2 zeta_b E^{a,b+1_i} - b_i E^{a,b-1_i})_{t_i} * prod_{j != i} E^{ab}_{t_j}
+//   d/dzeta_a: -sum_i E^{a+2_i,b}_{t_i} prod_{j != i} E^{ab}_{t_j}   (zeta_b likewise)
+// per axis.  A one-dimensional E^{ij}_t vanishes for t > i + j, so (ab, p')
+// contributes only if t_j <= a_j + b_j on all axes but at most one, which may
+// exceed it by 1 or 2.  The item list holds exactly those pairs of a class
+// (46 % of all (ab, p') for d-d), each as
+//   .x = ab | p' << 16,
+//   .y = the per-axis derived-table offsets (a_i (lb+1) + b_i) nt + t_i,
+//        nt = la + lb + 3, at bits 0, 10 and 20.
+// ---------------------------------------------------------------------------
+struct ItemTable {
+    const int2* list[kLmax + 1][kLmax + 1];
+    int n[kLmax + 1][kLmax + 1];
+};
+
+static std::vector<std::array<int, 3>> cart_list(int l)
 {
-    int idx = 0;
+    std::vector<std::array<int, 3>> r;
     for (int ax = l; ax >= 0; --ax)
-        for (int ay = l - ax; ay >= 0; --ay) {
-            if (idx == k) {
-                q[0] = ax;
-                q[1] = ay;
-                q[2] = l - ax - ay;
-                return;
-            }
-            ++idx;
-        }
+        for (int ay = l - ax; ay >= 0; --ay) r.push_back({ax, ay, l - ax - ay});
+    return r;
 }
 
-// Hermite function (t, u, v) of tetrahedral index idx (order N, then t, u descending).
-__device__ __forceinline__ void herm_of(int idx, int* t, int* u, int* v)
+static const ItemTable* get_items(cudaStream_t s, int* err)
 {
-    int N = 0;
-    while ((N + 1) * (N + 2) * (N + 3) / 6 <= idx) ++N;
-    const int r = idx - N * (N + 1) * (N + 2) / 6;
-    int d = 0;
-    while ((d + 1) * (d + 2) / 2 <= r) ++d;
-    const int e = r - d * (d + 1) / 2;
-    *t = N - d;
-    *u = d - e;
-    *v = N - *t - *u;
+    static std::map<int, ItemTable> tabs;
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = tabs.find(dev);
+    if (it != tabs.end()) return &it->second;
+    std::vector<int2> all;
+    int start[kLmax + 1][kLmax + 1];
+    ItemTable t{};
+    for (int la = 0; la <= kLmax; ++la)
+        for (int lb = 0; lb <= kLmax; ++lb) {
+            start[la][lb] = (int)all.size();
+            const auto ca = cart_list(la), cb = cart_list(lb);
+            const int nt = la + lb + 3, N2 = la + lb + 2;
+            for (int ia = 0; ia < (int)ca.size(); ++ia)
+                for (int ib = 0; ib < (int)cb.size(); ++ib) {
+                    const int ab = ia * (int)cb.size() + ib;
+                    for (int N = 0; N <= N2; ++N)
+                        for (int tt = N; tt >= 0; --tt)
+                            for (int uu = N - tt; uu >= 0; --uu) {
+                                const int h[3] = {tt, uu, N - tt - uu};
+                                int over = 0, ok = 1, off[3];
+                                for (int x = 0; x < 3; ++x) {
+                                    const int e = h[x] - ca[ia][x] - cb[ib][x];
+                                    if (e > 2) ok = 0;
+                                    if (e > 0) ++over;
+                                    off[x] = (ca[ia][x] * (lb + 1) + cb[ib][x]) * nt + h[x];
+                                }
+                                if (!ok || over > 1) continue;
+                                const int p = herm_index(h[0], h[1], h[2]);
+                                all.push_back(make_int2(ab | (p << 16), off[0] | (off[1] << 10) | (off[2] << 20)));
+                            }
+                }
+            t.n[la][lb] = (int)all.size() - start[la][lb];
+        }
+    int2* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int2) * all.size()) != cudaSuccess) {
+        *err = ERI_ENOMEM;
+        return nullptr;
+    }
+    if (cudaMemcpyAsync(d, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(d);
+        *err = ERI_ECUDA;
+        return nullptr;
+    }
+    for (int la = 0; la <= kLmax; ++la)
+        for (int lb = 0; lb <= kLmax; ++lb) t.list[la][lb] = d + start[la][lb];
+    tabs[dev] = t;
+    return &tabs[dev];
 }
 
 // Small integers as doubles (the factors a_i of the lowering terms).
 __constant__ double c_int_d[8] = {0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0};
 
-// The 8 channel contributions of one Hermite function p' = (t,u,v) of the
-// component pair (a, b) of one bra primitive pair, times y = T[ab][p'].
-// Ax: the three per-axis tables E[i][j][t] (i <= l1+2, j <= l2+2);
-// tz1, tz2: twice the two exponents.
-__device__ __forceinline__ void channel_terms(int l1, int l2, const int qa[3], const int qb[3], const int tt[3],
-                                              const double* __restrict__ Ax, int eax, double tz1, double tz2,
-                                              double y, double ch[8])
-{
-    const int n2 = l2 + 3, nt = l1 + l2 + 5;
-    auto Ev = [&](int x, int i, int j, int t) -> double {
-        if (i < 0 || j < 0) return 0.0;
-        return Ax[x * eax + (i * n2 + j) * nt + t];
-    };
-    double base[3], up1[3], dn1[3], up2[3], upb1[3], dnb1[3], upb2[3];
-    for (int x = 0; x < 3; ++x) {
-        base[x] = Ev(x, qa[x], qb[x], tt[x]);
-        up1[x] = Ev(x, qa[x] + 1, qb[x], tt[x]);
-        dn1[x] = Ev(x, qa[x] - 1, qb[x], tt[x]);
-        up2[x] = Ev(x, qa[x] + 2, qb[x], tt[x]);
-        upb1[x] = Ev(x, qa[x], qb[x] + 1, tt[x]);
-        dnb1[x] = Ev(x, qa[x], qb[x] - 1, tt[x]);
-        upb2[x] = Ev(x, qa[x], qb[x] + 2, tt[x]);
-    }
-    for (int x = 0; x < 3; ++x) {
-        const int o1 = (x + 1) % 3, o2 = (x + 2) % 3;
-        const double rest = base[o1] * base[o2] * y;
-        const double ga = fma(tz1, up1[x], -c_int_d[qa[x]] * dn1[x]);
-        const double gb = fma(tz2, upb1[x], -c_int_d[qb[x]] * dnb1[x]);
-        ch[x] = fma(ga, rest, ch[x]);
-        ch[3 + x] = fma(gb, rest, ch[3 + x]);
-        ch[6] = fma(-up2[x], rest, ch[6]);
-        ch[7] = fma(-upb2[x], rest, ch[7]);
-    }
-}
+// Derived-table entries per axis and value: (la+1)(lb+1)(la+lb+3).
+static int derived_entries(int la, int lb) { return (la + 1) * (lb + 1) * (la + lb + 3); }
 
 __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
 {
@@ -148,22 +178,23 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     const int TQ = a.TQ, KB = a.KB, KK = a.KK, IC = a.IC;
     const int nab = ct.nab, ncd = ct.ncd, nhk = ct.nhk, nhb2 = ct.nhb2, nhl2 = ct.nhl2;
     const int L2 = ct.L + 2;
-    const int NI = TQ * IC * KK;  // items of stage A
+    const int NI = TQ * IC * KK;  // items of stage A, ordered (k, ii, q) with q fastest
     const int NIs = NI | 1;       // R row stride (odd: spreads scattered rows over the banks)
+    const int ICT = IC * TQ;
+    const int Ws = a.Ws, Eks = a.Eks, ND = a.ND, PST = a.PST, nit = a.nit;
     const int eax = a.pb.eax;
-    const int AX = 3 * eax + 2;  // axis tables + the two exponents
+    const int n2 = ct.lb + 3, nte = ct.la + ct.lb + 5;  // strides of the raised E tables
+    const int nbd = ct.lb + 1, ntd = ct.la + ct.lb + 3; // strides of the derived tables
     int* s_q = reinterpret_cast<int*>(sm + a.o_q);
     double* sW = sm + a.o_W;
     double* sPb = sm + a.o_Pb;
     double* sPk = sm + a.o_Pk;
     double* sEk = sm + a.o_Ek;
-    double* sA = sm + a.o_A;
+    double* sD = sm + a.o_D;
     double* sR = sm + a.o_R;
     double* sX = sm + a.o_X;
-    double* sT = sm + a.o_T;
     double* sCh = sm + a.o_ch;
     double* sChE = sm + a.o_che;
-    const int ncb = (ct.lb + 1) * (ct.lb + 2) / 2;
 
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         const int64_t q0 = tile * TQ;
@@ -192,11 +223,11 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
         }
         for (int idx = tid; idx < TQ * KK * ct.Tcd; idx += kGT) {
             const int nk = KK * ct.Tcd, q = idx / nk, r = idx - q * nk, k = r % KK;
-            sEk[idx] = k < s_q[4 * q + 3] ? a.pk.E[(size_t)s_q[4 * q + 1] * nk + r] : 0.0;
+            sEk[(size_t)q * Eks + r] = k < s_q[4 * q + 3] ? a.pk.E[(size_t)s_q[4 * q + 1] * nk + r] : 0.0;
         }
         for (int idx = tid; idx < TQ * nab * ncd; idx += kGT) {
             const int q = idx / (nab * ncd), r = idx - q * nab * ncd;
-            sW[idx] = q < nqt ? a.W[g_windex(a, q0 + q, r / ncd, r % ncd)] : 0.0;
+            sW[(size_t)q * Ws + r] = q < nqt ? a.W[g_windex(a, q0 + q, r / ncd, r % ncd)] : 0.0;
         }
         for (int idx = tid; idx < TQ * 8; idx += kGT) sCh[idx] = 0.0;
         for (int idx = tid; idx < TQ * IC * 2; idx += kGT) sChE[idx] = 0.0;
@@ -208,7 +239,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
             const bool coop = NI * 4 < kGT;
             const int lane = tid & 31;
             for (int item = coop ? tid >> 5 : tid; item < NI; item += coop ? kGT / 32 : kGT) {
-                const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
+                const int q = item % TQ, r = item / TQ, ii = r % IC, k = r / IC;
                 const int i = i0 + ii;
                 struct S {
                     double* p;
@@ -239,17 +270,37 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                     for (int e = coop ? lane : 0; e < nhl2; e += coop ? 32 : 1) R[e] = 0.0;
                 }
             }
-            // axis tables and exponents of the chunk's bra primitives
-            for (int idx = tid; idx < TQ * IC * AX; idx += kGT) {
-                const int q = idx / (IC * AX), r = idx - q * IC * AX, ii = r / AX, c = r - ii * AX;
-                const int i = i0 + ii;
-                double v = 0.0;
+            // derived per-axis tables of the chunk's bra primitives,
+            // sD[(ii TQ + q) PST + (x 5 + c) ND + e], e = (a nbd + b) ntd + t:
+            // c = 0: E^{ab}_t; 1: 2 zeta_a E^{a+1,b}_t - a E^{a-1,b}_t;
+            // 2: 2 zeta_b E^{a,b+1}_t - b E^{a,b-1}_t; 3: -E^{a+2,b}_t; 4: -E^{a,b+2}_t
+            for (int idx = tid; idx < ICT * 3 * ND; idx += kGT) {
+                const int e = idx % ND;
+                int r = idx / ND;
+                const int x = r % 3;
+                r /= 3;
+                const int q = r % TQ, ii = r / TQ, i = i0 + ii;
+                double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0;
                 if (i < s_q[4 * q + 2]) {
+                    const int t = e % ntd, ab2 = e / ntd, bb = ab2 % nbd, aa = ab2 / nbd;
                     const size_t slot = (size_t)s_q[4 * q] * KB + i;
-                    // the axis tables, then twice the two exponents
-                    v = c < 3 * eax ? a.pb.ax[slot * 3 * eax + c] : 2.0 * a.pb.zz[slot * 2 + (c - 3 * eax)];
+                    const double* Ax = a.pb.ax + (slot * 3 + x) * eax + t;
+                    const double tz1 = 2.0 * a.pb.zz[2 * slot], tz2 = 2.0 * a.pb.zz[2 * slot + 1];
+                    const int r0 = aa * n2 + bb;
+                    v0 = Ax[r0 * nte];
+                    v1 = tz1 * Ax[(r0 + n2) * nte];
+                    if (aa) v1 = fma(-c_int_d[aa], Ax[(r0 - n2) * nte], v1);
+                    v2 = tz2 * Ax[(r0 + 1) * nte];
+                    if (bb) v2 = fma(-c_int_d[bb], Ax[(r0 - 1) * nte], v2);
+                    v3 = -Ax[(r0 + 2 * n2) * nte];
+                    v4 = -Ax[(r0 + 2) * nte];
                 }
-                sA[idx] = v;
+                double* o = sD + (size_t)(ii * TQ + q) * PST + x * 5 * ND + e;
+                o[0] = v0;
+                o[ND] = v1;
+                o[2 * ND] = v2;
+                o[3 * ND] = v3;
+                o[4 * ND] = v4;
             }
             __syncthreads();
             const int ICe = min(IC, KB - i0);
@@ -260,8 +311,8 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 const int p = r % nhb2;
                 r /= nhb2;
                 const int cd = r % ncd, ii = r / ncd;
-                const double* Ek = sEk + (size_t)q * KK * ct.Tcd;
-                const double* Rc = sR + (q * IC + ii) * KK;
+                const double* Ek = sEk + (size_t)q * Eks;
+                const double* Rc = sR + ii * TQ + q;
                 const int16_t* row = ct.pq2b + (size_t)p * nhk;
                 const int t0 = ct.ket_start[cd], t1 = ct.ket_start[cd + 1];
                 double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
@@ -273,56 +324,38 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                     const double* Eb = Ea + KK;
                     int k = 0;
                     for (; k + 1 < KK; k += 2) {
-                        v0 = fma(Ea[k], Ra[k], v0);
-                        v1 = fma(Ea[k + 1], Ra[k + 1], v1);
-                        v2 = fma(Eb[k], Rb[k], v2);
-                        v3 = fma(Eb[k + 1], Rb[k + 1], v3);
+                        v0 = fma(Ea[k], Ra[k * ICT], v0);
+                        v1 = fma(Ea[k + 1], Ra[(k + 1) * ICT], v1);
+                        v2 = fma(Eb[k], Rb[k * ICT], v2);
+                        v3 = fma(Eb[k + 1], Rb[(k + 1) * ICT], v3);
                     }
                     if (k < KK) {
-                        v0 = fma(Ea[k], Ra[k], v0);
-                        v2 = fma(Eb[k], Rb[k], v2);
+                        v0 = fma(Ea[k], Ra[k * ICT], v0);
+                        v2 = fma(Eb[k], Rb[k * ICT], v2);
                     }
                 }
                 if (t < t1) {
                     const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NIs;
                     const double* Ea = Ek + t * KK;
-                    for (int k = 0; k < KK; ++k) v0 = fma(Ea[k], Ra[k], v0);
+                    for (int k = 0; k < KK; ++k) v0 = fma(Ea[k], Ra[k * ICT], v0);
                 }
                 sX[(((size_t)ii * nhb2 + p) * ncd + cd) * TQ + q] = (v0 + v1) + (v2 + v3);
             }
             __syncthreads();
-            // ---- C'': T[ii][ab][p'][q] = sum_cd W[q][ab][cd] X'[ii][p'][cd][q]
-            for (int item = tid; item < TQ * ICe * nab * nhb2; item += kGT) {
-                const int q = item % TQ;
-                int r = item / TQ;
-                const int p = r % nhb2;
-                r /= nhb2;
-                const int ab = r % nab, ii = r / nab;
-                const double* w = sW + (size_t)q * nab * ncd + (size_t)ab * ncd;
-                const double* x = sX + ((size_t)ii * nhb2 + p) * ncd * TQ + q;
-                double va = 0.0, vb = 0.0;
-                int cd = 0;
-                for (; cd + 1 < ncd; cd += 2) {
-                    va = fma(w[cd], x[(size_t)cd * TQ], va);
-                    vb = fma(w[cd + 1], x[(size_t)(cd + 1) * TQ], vb);
-                }
-                if (cd < ncd) va = fma(w[cd], x[(size_t)cd * TQ], va);
-                sT[item] = va + vb;
-            }
-            __syncthreads();
-            // ---- D: channel contributions.  A thread's items share q = tid % TQ
+            // ---- C+D, per channel item (ab, p') of each bra primitive:
+            //   y = T[ab][p'] = sum_cd W[q][ab][cd] X'[ii][p'][cd][q],
+            // then the 8 channel terms of y.  A thread's items share q = tid % TQ
             // (TQ divides kGT) and run through the bra primitives in order: the
-            // centre channels stay in registers for the whole tile, the two
+            // centre channels stay in registers for the whole chunk, the two
             // exponent channels go to shared memory whenever ii changes.
             {
                 double ch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                 const int q = tid % TQ;
                 int cur = -1;
-                for (int item = tid; item < TQ * ICe * nab * nhb2; item += kGT) {
-                    int r = item / TQ;
-                    const int p = r % nhb2;
-                    r /= nhb2;
-                    const int ab = r % nab, ii = r / nab;
+                const double* wq = sW + (size_t)q * Ws;
+                for (int item = tid; item < TQ * ICe * nit; item += kGT) {
+                    const int r = item / TQ;
+                    const int j = r % nit, ii = r / nit;
                     if (ii != cur) {
                         if (cur >= 0) {
                             atomicAdd(&sChE[(q * IC + cur) * 2], ch[6]);
@@ -332,13 +365,36 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                         ch[6] = ch[7] = 0.0;
                     }
                     if (i0 + ii >= s_q[4 * q + 2]) continue;  // padding bra primitive
-                    int qa[3], qb[3], tt[3];
-                    cart_of(ct.la, ab / ncb, qa);
-                    cart_of(ct.lb, ab % ncb, qb);
-                    herm_of(p, &tt[0], &tt[1], &tt[2]);
-                    if (tt[0] > qa[0] + qb[0] + 2 || tt[1] > qa[1] + qb[1] + 2 || tt[2] > qa[2] + qb[2] + 2) continue;
-                    const double* A = sA + ((size_t)q * IC + ii) * AX;
-                    channel_terms(ct.la, ct.lb, qa, qb, tt, A, eax, A[3 * eax], A[3 * eax + 1], sT[item], ch);
+                    const int2 g = __ldg(a.items + j);
+                    const double* w = wq + (g.x & 0xffff) * ncd;
+                    const double* xv = sX + (size_t)(ii * nhb2 + (g.x >> 16)) * ncd * TQ + q;
+                    double ya = 0.0, yb = 0.0;
+                    int cd = 0;
+                    for (; cd + 1 < ncd; cd += 2) {
+                        ya = fma(w[cd], xv[(size_t)cd * TQ], ya);
+                        yb = fma(w[cd + 1], xv[(size_t)(cd + 1) * TQ], yb);
+                    }
+                    if (cd < ncd) ya = fma(w[cd], xv[(size_t)cd * TQ], ya);
+                    const double y = ya + yb;
+                    const double* Dq = sD + (size_t)(ii * TQ + q) * PST;
+                    const double* Dx = Dq + (g.y & 1023);
+                    const double* Dy = Dq + 5 * ND + ((g.y >> 10) & 1023);
+                    const double* Dz = Dq + 10 * ND + (g.y >> 20);
+                    const double ex = Dx[0], ey = Dy[0], ez = Dz[0];
+                    const double yx = y * ex;
+                    const double pyz = y * ey * ez, pxz = yx * ez, pxy = yx * ey;
+                    ch[0] = fma(Dx[ND], pyz, ch[0]);
+                    ch[3] = fma(Dx[2 * ND], pyz, ch[3]);
+                    ch[6] = fma(Dx[3 * ND], pyz, ch[6]);
+                    ch[7] = fma(Dx[4 * ND], pyz, ch[7]);
+                    ch[1] = fma(Dy[ND], pxz, ch[1]);
+                    ch[4] = fma(Dy[2 * ND], pxz, ch[4]);
+                    ch[6] = fma(Dy[3 * ND], pxz, ch[6]);
+                    ch[7] = fma(Dy[4 * ND], pxz, ch[7]);
+                    ch[2] = fma(Dz[ND], pxy, ch[2]);
+                    ch[5] = fma(Dz[2 * ND], pxy, ch[5]);
+                    ch[6] = fma(Dz[3 * ND], pxy, ch[6]);
+                    ch[7] = fma(Dz[4 * ND], pxy, ch[7]);
                 }
                 if (cur >= 0) {
                     atomicAdd(&sChE[(q * IC + cur) * 2], ch[6]);
@@ -376,7 +432,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     }
 }
 
-static bool grad_layout(const ClassTables& ct, int KB, int KK, int eax, int TQ, int IC, GradArgs* a, size_t* bytes)
+static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, GradArgs* a, size_t* bytes)
 {
     size_t off = 0;
     auto take = [&](size_t nd) {
@@ -384,15 +440,18 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int eax, int TQ, 
         off += (nd + 1) & ~size_t(1);
         return (int)o;
     };
+    a->ND = derived_entries(ct.la, ct.lb);
+    a->PST = (15 * a->ND) | 1;
+    a->Ws = (ct.nab * ct.ncd) | 1;
+    a->Eks = (KK * ct.Tcd) | 1;
     a->o_q = take((size_t)TQ * 2);
-    a->o_W = take((size_t)TQ * ct.nab * ct.ncd);
+    a->o_W = take((size_t)TQ * a->Ws);
     a->o_Pb = take((size_t)TQ * KB * PS_N);
     a->o_Pk = take((size_t)TQ * KK * PS_N);
-    a->o_Ek = take((size_t)TQ * KK * ct.Tcd);
-    a->o_A = take((size_t)TQ * IC * (3 * eax + 2));
+    a->o_Ek = take((size_t)TQ * a->Eks);
+    a->o_D = take((size_t)TQ * IC * a->PST);
     a->o_R = take((size_t)ct.nhl2 * ((TQ * IC * KK) | 1));
     a->o_X = take((size_t)ct.nhb2 * ct.ncd * TQ * IC);
-    a->o_T = take((size_t)ct.nab * ct.nhb2 * TQ * IC);
     a->o_ch = take((size_t)TQ * 8);
     a->o_che = take((size_t)TQ * IC * 2);
     *bytes = off * 8;
@@ -404,40 +463,41 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int eax, int TQ, 
 // Tile shape (TQ quartets, IC bra primitives per stage pass): the feasible
 // shape with the lowest modelled time per quartet.  Each stage pass costs its
 // rounds of kGT items times the FP64 work of one item, plus a barrier; a
-// tile makes ceil(KB / IC) passes of five stages.  Shapes that leave room for
+// tile makes ceil(KB / IC) passes of four stages.  Shapes that leave room for
 // two CTAs per SM (so one CTA's barriers overlap the other's work) are
 // preferred whenever one exists.
-static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int eax, int64_t nq, size_t limit, GradArgs* a,
+static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int64_t nq, size_t limit, GradArgs* a,
                              size_t* bytes);
 
-static bool grad_plan(const ClassTables& ct, int KB, int KK, int eax, int64_t nq, GradArgs* a, size_t* bytes)
+static bool grad_plan(const ClassTables& ct, int KB, int KK, int nit, int64_t nq, GradArgs* a, size_t* bytes)
 {
     const size_t two_per_sm = (size_t)smem_per_sm() / 2 - 1024;
     for (int pass = 0; pass < 2; ++pass) {
-        if (grad_plan_within(ct, KB, KK, eax, nq, pass == 0 ? two_per_sm : (size_t)max_smem_optin(), a, bytes))
+        if (grad_plan_within(ct, KB, KK, nit, nq, pass == 0 ? two_per_sm : (size_t)max_smem_optin(), a, bytes))
             return true;
     }
     return false;
 }
 
-static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int eax, int64_t nq, size_t limit, GradArgs* a,
+static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int64_t nq, size_t limit, GradArgs* a,
                              size_t* bytes)
 {
     double best = -1.0;
     GradArgs pick{};
     size_t pick_bytes = 0;
+    const int ND = derived_entries(ct.la, ct.lb);
     for (int TQ = 32; TQ >= 1; TQ /= 2) {
         if (TQ > 1 && TQ > nq) continue;
         for (int IC = KB; IC >= 1; IC = IC == 1 ? 0 : (IC + 1) / 2) {
             GradArgs t = *a;
             size_t b = 0;
-            if (!grad_layout(ct, KB, KK, eax, TQ, IC, &t, &b) || b > limit) continue;
+            if (!grad_layout(ct, KB, KK, TQ, IC, &t, &b) || b > limit) continue;
             auto rounds = [](double n) { return std::ceil(n / kGT); };
             const double kBarrier = 60.0;
             const double pass = rounds((double)TQ * IC * KK) * (3.0 * ct.nhl2 + 60.0) +
+                                rounds((double)TQ * IC * 3 * ND) * 14.0 +
                                 rounds((double)TQ * IC * ct.nhb2 * ct.ncd) * (2.0 * KK * ct.Tcd / ct.ncd + 8.0) +
-                                rounds((double)TQ * IC * ct.nab * ct.nhb2) * (2.0 * ct.ncd + 8.0) +
-                                rounds((double)TQ * IC * ct.nab * ct.nhb2) * 50.0 + 5.0 * kBarrier;
+                                rounds((double)TQ * IC * nit) * (2.0 * ct.ncd + 40.0) + 4.0 * kBarrier;
             const double cost = std::ceil((double)KB / IC) * pass / TQ;
             if (best < 0 || cost < best) {
                 best = cost;
@@ -489,8 +549,12 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     a.ge = ge;
     a.KB = KB;
     a.KK = KK;
+    const ItemTable* items = get_items(st, &err);
+    if (!items) return err;
+    a.items = items->list[ct->la][ct->lb];
+    a.nit = items->n[ct->la][ct->lb];
     size_t bytes = 0;
-    if (!grad_plan(*ct, KB, KK, pb.eax, a.nq, &a, &bytes)) return ERI_EINVAL;
+    if (!grad_plan(*ct, KB, KK, a.nit, a.nq, &a, &bytes)) return ERI_EINVAL;
     a.ntiles = (a.nq + a.TQ - 1) / a.TQ;
     if (cudaFuncSetAttribute(grad_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return ERI_ECUDA;

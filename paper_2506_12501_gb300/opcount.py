@@ -165,22 +165,38 @@ def sparse_flops3(cls3, Kx: int, Kket: int, pure: bool, swapped: bool, pure_term
     return kb * kk * (prim_quartet_flops(L) + ket) + kb * bra
 
 
+def grad_items(la: int, lb: int) -> int:
+    """Channel items of a bra class: the (ab, p') pairs, p' = (t, u, v) of
+    order <= la + lb + 2, with t_i <= a_i + b_i on all axes but at most one,
+    which may exceed it by 1 or 2 (every other pair has zero weight in all
+    8 channels, the one-dimensional E^{ij}_t vanishing for t > i + j)."""
+    n = 0
+    for a in carts(la):
+        for b in carts(lb):
+            for N in range(la + lb + 3):
+                for t in range(N, -1, -1):
+                    for u in range(N - t, -1, -1):
+                        over = [h - a[i] - b[i] for i, h in enumerate((t, u, N - t - u))]
+                        if max(over) <= 2 and sum(1 for e in over if e > 0) <= 1:
+                            n += 1
+    return n
+
+
 def _grad_launch_flops(cls, Kbra: int, Kket: int) -> int:
     """FP64 flops of one adjoint launch (the channels of the kernel's bra):
     per primitive quartet the auxiliary integrals to order L+2 and the ket
     transform over the raised bra Hermite range; per bra primitive the
-    contraction with W and the 8 channel terms (about 40 flops for each
-    (ab, p') whose Hermite indices stay within a_i + b_i + 2)."""
+    derived per-axis tables (3 (la+1)(lb+1)(la+lb+3) entries, 6 flops each)
+    and, per channel item, the contraction with W (2 ncd) and the 8 channel
+    terms (5 multiplies and 12 FMAs, 29 flops)."""
     la, lb, lc, ld = cls
     L = la + lb + lc + ld
     nhb2 = nh(la + lb + 2)
-    nab, ncd = nc(la) * nc(lb), nc(lc) * nc(ld)
-    support = 0
-    for a in carts(la):
-        for b in carts(lb):
-            support += math.prod(a[i] + b[i] + 3 for i in range(3))
+    ncd = nc(lc) * nc(ld)
+    nit = grad_items(la, lb)
+    nd = (la + 1) * (lb + 1) * (la + lb + 3)
     return Kbra * Kket * (prim_quartet_flops(L + 2) + 2 * nhb2 * terms(lc, ld)) + \
-        Kbra * (2 * nab * nhb2 * ncd + 40 * support)
+        Kbra * (18 * nd + nit * (2 * ncd + 29))
 
 
 def grad_flops(cls, Kbra: int, Kket: int) -> int:
