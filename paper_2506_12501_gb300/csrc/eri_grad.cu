@@ -45,6 +45,8 @@ struct GradArgs {
     const int32_t* shell_off;
     const int32_t* shell_K;
     const int64_t* quartets;   // the caller's list (NULL: product form)
+    const int64_t* order;      // processing order of the caller's quartet indices
+    unsigned long long* next;  // tile queue (zero at launch)
     int64_t nq, nbra, nket;    // the caller's counts
     int swap;                  // 1: the kernel's bra is the caller's ket
     int nab_o, ncd_o;          // the caller's component-pair counts
@@ -56,7 +58,8 @@ struct GradArgs {
     int ND, PST;               // derived-table entries per axis and value; doubles per bra primitive
     int Ws, Eks;               // shared-memory row strides of W and of the ket E products (odd)
     int TQ, KB, KK, IC;
-    int o_q, o_W, o_Pb, o_Pk, o_Ek, o_D, o_R, o_X, o_ch, o_che;
+    int Xs, XQ;                // X' strides: per Hermite function p' and per (ii, q) (odd)
+    int o_q, o_W, o_Pb, o_Pk, o_Ek, o_D, o_R, o_X, o_ch;
     int64_t ntiles;
 };
 
@@ -181,11 +184,14 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     const int NI = TQ * IC * KK;  // items of stage A, ordered (k, ii, q) with q fastest
     const int NIs = NI | 1;       // R row stride (odd: spreads scattered rows over the banks)
     const int ICT = IC * TQ;
-    const int Ws = a.Ws, Eks = a.Eks, ND = a.ND, PST = a.PST, nit = a.nit;
+    const int Ws = a.Ws, Eks = a.Eks, ND = a.ND, PST = a.PST, nit = a.nit, Xs = a.Xs, XQ = a.XQ;
     const int eax = a.pb.eax;
     const int n2 = ct.lb + 3, nte = ct.la + ct.lb + 5;  // strides of the raised E tables
     const int nbd = ct.lb + 1, ntd = ct.la + ct.lb + 3; // strides of the derived tables
     int* s_q = reinterpret_cast<int*>(sm + a.o_q);
+    int64_t* s_qq = reinterpret_cast<int64_t*>(sm + a.o_q + 2 * TQ);
+    __shared__ int s_kmax[2];
+    __shared__ int64_t s_tile;
     double* sW = sm + a.o_W;
     double* sPb = sm + a.o_Pb;
     double* sPk = sm + a.o_Pk;
@@ -193,26 +199,41 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     double* sD = sm + a.o_D;
     double* sR = sm + a.o_R;
     double* sX = sm + a.o_X;
-    double* sCh = sm + a.o_ch;
-    double* sChE = sm + a.o_che;
+    double* sC8 = sm + a.o_ch;
 
-    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    // tiles from a queue: the sorted order puts the heaviest first, so the
+    // CTAs that finish early take the lighter tiles of the tail
+    for (;;) {
+        __syncthreads();  // the previous tile is done with shared memory
+        if (tid == 0) {
+            s_tile = (int64_t)atomicAdd(a.next, 1ULL);
+            s_kmax[0] = s_kmax[1] = 0;
+        }
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= a.ntiles) break;
         const int64_t q0 = tile * TQ;
         const int nqt = (int)min((int64_t)TQ, a.nq - q0);
-        __syncthreads();
         for (int q = tid; q < TQ; q += kGT) {
             int b = 0, k = 0, kb = 0, kk = 0;
+            int64_t qq = 0;
             if (q < nqt) {
-                g_pairs(a, q0 + q, &b, &k);
+                qq = a.order[q0 + q];
+                g_pairs(a, qq, &b, &k);
                 kb = a.pb.kp[b];
                 kk = a.pk.kp[k];
+                atomicMax(&s_kmax[0], kb);
+                atomicMax(&s_kmax[1], kk);
             }
             s_q[4 * q] = b;
             s_q[4 * q + 1] = k;
             s_q[4 * q + 2] = kb;
             s_q[4 * q + 3] = kk;
+            s_qq[q] = qq;
         }
         __syncthreads();
+        // the tile's own contraction degrees (its quartets share them when sorted)
+        const int KBt = s_kmax[0], KKt = s_kmax[1];
         for (int idx = tid; idx < TQ * KB * PS_N; idx += kGT) {
             const int q = idx / (KB * PS_N), r = idx - q * KB * PS_N, i = r / PS_N;
             sPb[idx] = i < s_q[4 * q + 2] ? a.pb.ps[(size_t)s_q[4 * q] * KB * PS_N + r] : 1.0;
@@ -227,18 +248,18 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
         }
         for (int idx = tid; idx < TQ * nab * ncd; idx += kGT) {
             const int q = idx / (nab * ncd), r = idx - q * nab * ncd;
-            sW[(size_t)q * Ws + r] = q < nqt ? a.W[g_windex(a, q0 + q, r / ncd, r % ncd)] : 0.0;
+            sW[(size_t)q * Ws + r] = q < nqt ? a.W[g_windex(a, s_qq[q], r / ncd, r % ncd)] : 0.0;
         }
-        for (int idx = tid; idx < TQ * 8; idx += kGT) sCh[idx] = 0.0;
-        for (int idx = tid; idx < TQ * IC * 2; idx += kGT) sChE[idx] = 0.0;
+        for (int idx = tid; idx < TQ * IC * 8; idx += kGT) sC8[idx] = 0.0;
 
-        for (int i0 = 0; i0 < KB; i0 += IC) {
+        const int NIt = TQ * IC * KKt;  // stage-A items of this tile (k < KKt)
+        for (int i0 = 0; i0 < KBt; i0 += IC) {
             __syncthreads();
             // ---- A: auxiliary integrals up to order L+2 for (q, i0+ii, k);
             // with few items a warp shares each item's recursion
-            const bool coop = NI * 4 < kGT;
+            const bool coop = NIt * 4 < kGT;
             const int lane = tid & 31;
-            for (int item = coop ? tid >> 5 : tid; item < NI; item += coop ? kGT / 32 : kGT) {
+            for (int item = coop ? tid >> 5 : tid; item < NIt; item += coop ? kGT / 32 : kGT) {
                 const int q = item % TQ, r = item / TQ, ii = r % IC, k = r / IC;
                 const int i = i0 + ii;
                 struct S {
@@ -303,8 +324,8 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 o[4 * ND] = v4;
             }
             __syncthreads();
-            const int ICe = min(IC, KB - i0);
-            // ---- B': X'[ii][p'][cd][q] over the raised bra range (four chains)
+            const int ICe = min(IC, KBt - i0);
+            // ---- B': X'[ii][q][p'][cd] over the raised bra range (four chains)
             for (int item = tid; item < TQ * ICe * nhb2 * ncd; item += kGT) {
                 const int q = item % TQ;
                 int r = item / TQ;
@@ -323,13 +344,13 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                     const double* Ea = Ek + t * KK;
                     const double* Eb = Ea + KK;
                     int k = 0;
-                    for (; k + 1 < KK; k += 2) {
+                    for (; k + 1 < KKt; k += 2) {
                         v0 = fma(Ea[k], Ra[k * ICT], v0);
                         v1 = fma(Ea[k + 1], Ra[(k + 1) * ICT], v1);
                         v2 = fma(Eb[k], Rb[k * ICT], v2);
                         v3 = fma(Eb[k + 1], Rb[(k + 1) * ICT], v3);
                     }
-                    if (k < KK) {
+                    if (k < KKt) {
                         v0 = fma(Ea[k], Ra[k * ICT], v0);
                         v2 = fma(Eb[k], Rb[k * ICT], v2);
                     }
@@ -337,96 +358,112 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 if (t < t1) {
                     const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NIs;
                     const double* Ea = Ek + t * KK;
-                    for (int k = 0; k < KK; ++k) v0 = fma(Ea[k], Ra[k * ICT], v0);
+                    for (int k = 0; k < KKt; ++k) v0 = fma(Ea[k], Ra[k * ICT], v0);
                 }
-                sX[(((size_t)ii * nhb2 + p) * ncd + cd) * TQ + q] = (v0 + v1) + (v2 + v3);
+                sX[(size_t)(ii * TQ + q) * XQ + p * Xs + cd] = (v0 + v1) + (v2 + v3);
             }
             __syncthreads();
-            // ---- C+D, per channel item (ab, p') of each bra primitive:
-            //   y = T[ab][p'] = sum_cd W[q][ab][cd] X'[ii][p'][cd][q],
-            // then the 8 channel terms of y.  A thread's items share q = tid % TQ
-            // (TQ divides kGT) and run through the bra primitives in order: the
-            // centre channels stay in registers for the whole chunk, the two
-            // exponent channels go to shared memory whenever ii changes.
+            // ---- C+D.  Each (q, ii) of the chunk is taken by a group of G
+            // consecutive lanes.  The group's lanes split its channel items
+            // (ab, p'), form y = T[ab][p'] = sum_cd W[q][ab][cd] X'[ii][q][p'][cd]
+            // and fold y into the 8 channel sums, which are then reduced over
+            // the group by shuffles.  G: the fewest rounds of items, with
+            // log2(G) shuffle steps counted.
             {
-                double ch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                const int q = tid % TQ;
-                int cur = -1;
-                const double* wq = sW + (size_t)q * Ws;
-                for (int item = tid; item < TQ * ICe * nit; item += kGT) {
-                    const int r = item / TQ;
-                    const int j = r % nit, ii = r / nit;
-                    if (ii != cur) {
-                        if (cur >= 0) {
-                            atomicAdd(&sChE[(q * IC + cur) * 2], ch[6]);
-                            atomicAdd(&sChE[(q * IC + cur) * 2 + 1], ch[7]);
+                int G = 1;
+                {
+                    int best = -1;
+                    for (int g = 1; g <= 32; g *= 2) {
+                        const int c = ((TQ * ICe * g + kGT - 1) / kGT) * ((nit + g - 1) / g) * (ncd + 20) +
+                                      24 * (__ffs(g) - 1);
+                        if (best < 0 || c < best) {
+                            best = c;
+                            G = g;
                         }
-                        cur = ii;
-                        ch[6] = ch[7] = 0.0;
                     }
-                    if (i0 + ii >= s_q[4 * q + 2]) continue;  // padding bra primitive
-                    const int2 g = __ldg(a.items + j);
-                    const double* w = wq + (g.x & 0xffff) * ncd;
-                    const double* xv = sX + (size_t)(ii * nhb2 + (g.x >> 16)) * ncd * TQ + q;
-                    double ya = 0.0, yb = 0.0;
-                    int cd = 0;
-                    for (; cd + 1 < ncd; cd += 2) {
-                        ya = fma(w[cd], xv[(size_t)cd * TQ], ya);
-                        yb = fma(w[cd + 1], xv[(size_t)(cd + 1) * TQ], yb);
+                }
+                const int s = tid & (G - 1), NG = kGT / G;
+                const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((tid & 31) & ~(G - 1));
+                for (int combo = tid / G; combo < TQ * ICe; combo += NG) {
+                    const int q = combo % TQ, ii = combo / TQ;
+                    const bool live = i0 + ii < s_q[4 * q + 2];  // the same for the whole group
+                    double ch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    if (live) {
+                        const double* wq = sW + (size_t)q * Ws;
+                        const double* xq = sX + (size_t)(ii * TQ + q) * XQ;
+                        const double* Dq = sD + (size_t)(ii * TQ + q) * PST;
+                        for (int j = s; j < nit; j += G) {
+                            const int2 g = __ldg(a.items + j);
+                            const double* w = wq + (g.x & 0xffff) * ncd;
+                            const double* xv = xq + (g.x >> 16) * Xs;
+                            double ya = 0.0, yb = 0.0;
+                            int cd = 0;
+                            for (; cd + 1 < ncd; cd += 2) {
+                                ya = fma(w[cd], xv[cd], ya);
+                                yb = fma(w[cd + 1], xv[cd + 1], yb);
+                            }
+                            if (cd < ncd) ya = fma(w[cd], xv[cd], ya);
+                            const double y = ya + yb;
+                            const double* Dx = Dq + (g.y & 1023);
+                            const double* Dy = Dq + 5 * ND + ((g.y >> 10) & 1023);
+                            const double* Dz = Dq + 10 * ND + (g.y >> 20);
+                            const double ex = Dx[0], ey = Dy[0], ez = Dz[0];
+                            const double yx = y * ex;
+                            const double pyz = y * ey * ez, pxz = yx * ez, pxy = yx * ey;
+                            ch[0] = fma(Dx[ND], pyz, ch[0]);
+                            ch[3] = fma(Dx[2 * ND], pyz, ch[3]);
+                            ch[6] = fma(Dx[3 * ND], pyz, ch[6]);
+                            ch[7] = fma(Dx[4 * ND], pyz, ch[7]);
+                            ch[1] = fma(Dy[ND], pxz, ch[1]);
+                            ch[4] = fma(Dy[2 * ND], pxz, ch[4]);
+                            ch[6] = fma(Dy[3 * ND], pxz, ch[6]);
+                            ch[7] = fma(Dy[4 * ND], pxz, ch[7]);
+                            ch[2] = fma(Dz[ND], pxy, ch[2]);
+                            ch[5] = fma(Dz[2 * ND], pxy, ch[5]);
+                            ch[6] = fma(Dz[3 * ND], pxy, ch[6]);
+                            ch[7] = fma(Dz[4 * ND], pxy, ch[7]);
+                        }
                     }
-                    if (cd < ncd) ya = fma(w[cd], xv[(size_t)cd * TQ], ya);
-                    const double y = ya + yb;
-                    const double* Dq = sD + (size_t)(ii * TQ + q) * PST;
-                    const double* Dx = Dq + (g.y & 1023);
-                    const double* Dy = Dq + 5 * ND + ((g.y >> 10) & 1023);
-                    const double* Dz = Dq + 10 * ND + (g.y >> 20);
-                    const double ex = Dx[0], ey = Dy[0], ez = Dz[0];
-                    const double yx = y * ex;
-                    const double pyz = y * ey * ez, pxz = yx * ez, pxy = yx * ey;
-                    ch[0] = fma(Dx[ND], pyz, ch[0]);
-                    ch[3] = fma(Dx[2 * ND], pyz, ch[3]);
-                    ch[6] = fma(Dx[3 * ND], pyz, ch[6]);
-                    ch[7] = fma(Dx[4 * ND], pyz, ch[7]);
-                    ch[1] = fma(Dy[ND], pxz, ch[1]);
-                    ch[4] = fma(Dy[2 * ND], pxz, ch[4]);
-                    ch[6] = fma(Dy[3 * ND], pxz, ch[6]);
-                    ch[7] = fma(Dy[4 * ND], pxz, ch[7]);
-                    ch[2] = fma(Dz[ND], pxy, ch[2]);
-                    ch[5] = fma(Dz[2 * ND], pxy, ch[5]);
-                    ch[6] = fma(Dz[3 * ND], pxy, ch[6]);
-                    ch[7] = fma(Dz[4 * ND], pxy, ch[7]);
-                }
-                if (cur >= 0) {
-                    atomicAdd(&sChE[(q * IC + cur) * 2], ch[6]);
-                    atomicAdd(&sChE[(q * IC + cur) * 2 + 1], ch[7]);
-                }
+                    for (int o = G >> 1; o > 0; o >>= 1)
 #pragma unroll
-                for (int c = 0; c < 6; ++c)
-                    if (ch[c] != 0.0) atomicAdd(&sCh[q * 8 + c], ch[c]);
+                        for (int c = 0; c < 8; ++c) ch[c] += __shfl_xor_sync(gmask, ch[c], o);
+                    if (live && s == 0) {
+                        // centre channels accumulate over the chunks; the exponent
+                        // channels belong to this chunk's primitive i0 + ii
+                        double* o8 = sC8 + (size_t)(q * IC + ii) * 8;
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) o8[c] += ch[c];
+                        o8[6] = ch[6];
+                        o8[7] = ch[7];
+                    }
+                }
             }
             __syncthreads();
             // exponent channels of the chunk's bra primitives
-            for (int idx = tid; idx < TQ * ICe; idx += kGT) {
-                const int q = idx % TQ, ii = idx / TQ, i = i0 + ii;
-                double* e = sChE + (q * IC + ii) * 2;
-                if (q < nqt && i < s_q[4 * q + 2] && a.ge) {
-                    const int sa = a.bra_sh[2 * s_q[4 * q]], sb = a.bra_sh[2 * s_q[4 * q] + 1];
-                    const int K2 = a.shell_K[sb], i1 = i / K2, i2 = i - i1 * K2;
-                    atomicAdd(&a.ge[a.shell_off[sa] + i1], e[0]);
-                    atomicAdd(&a.ge[a.shell_off[sb] + i2], e[1]);
+            if (a.ge)
+                for (int idx = tid; idx < TQ * ICe; idx += kGT) {
+                    const int q = idx % TQ, ii = idx / TQ, i = i0 + ii;
+                    if (q < nqt && i < s_q[4 * q + 2]) {
+                        const double* e = sC8 + (size_t)(q * IC + ii) * 8 + 6;
+                        const int sa = a.bra_sh[2 * s_q[4 * q]], sb = a.bra_sh[2 * s_q[4 * q] + 1];
+                        const int K2 = a.shell_K[sb], i1 = i / K2, i2 = i - i1 * K2;
+                        atomicAdd(&a.ge[a.shell_off[sa] + i1], e[0]);
+                        atomicAdd(&a.ge[a.shell_off[sb] + i2], e[1]);
+                    }
                 }
-                e[0] = 0.0;
-                e[1] = 0.0;
-            }
         }
         __syncthreads();
-        // centre channels of the tile's quartets
+        // centre channels of the tile's quartets (summed over the IC slots)
         if (a.gc)
             for (int q = tid; q < nqt; q += kGT) {
                 const int sa = a.bra_sh[2 * s_q[4 * q]], sb = a.bra_sh[2 * s_q[4 * q] + 1];
+                double c6[6] = {0, 0, 0, 0, 0, 0};
+                for (int ii = 0; ii < IC; ++ii)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) c6[c] += sC8[(size_t)(q * IC + ii) * 8 + c];
                 for (int x = 0; x < 3; ++x) {
-                    atomicAdd(&a.gc[3 * a.shell_atom[sa] + x], sCh[q * 8 + x]);
-                    atomicAdd(&a.gc[3 * a.shell_atom[sb] + x], sCh[q * 8 + 3 + x]);
+                    atomicAdd(&a.gc[3 * a.shell_atom[sa] + x], c6[x]);
+                    atomicAdd(&a.gc[3 * a.shell_atom[sb] + x], c6[3 + x]);
                 }
             }
     }
@@ -444,22 +481,29 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, G
     a->PST = (15 * a->ND) | 1;
     a->Ws = (ct.nab * ct.ncd) | 1;
     a->Eks = (KK * ct.Tcd) | 1;
-    a->o_q = take((size_t)TQ * 2);
+    a->o_q = take((size_t)TQ * 3);  // (b, k, kb, kk) as int32, then the quartet index
     a->o_W = take((size_t)TQ * a->Ws);
     a->o_Pb = take((size_t)TQ * KB * PS_N);
     a->o_Pk = take((size_t)TQ * KK * PS_N);
     a->o_Ek = take((size_t)TQ * a->Eks);
     a->o_D = take((size_t)TQ * IC * a->PST);
     a->o_R = take((size_t)ct.nhl2 * ((TQ * IC * KK) | 1));
-    a->o_X = take((size_t)ct.nhb2 * ct.ncd * TQ * IC);
-    a->o_ch = take((size_t)TQ * 8);
-    a->o_che = take((size_t)TQ * IC * 2);
+    a->Xs = ct.ncd | 1;
+    a->XQ = (ct.nhb2 * a->Xs) | 1;
+    a->o_X = take((size_t)a->XQ * TQ * IC);
+    a->o_ch = take((size_t)TQ * IC * 8);
     *bytes = off * 8;
     a->TQ = TQ;
     a->IC = IC;
     return *bytes <= (size_t)max_smem_optin();
 }
 
+// Tile shape (TQ quartets, IC bra primitives per stage pass): the feasible
+// shape with the lowest modelled time per quartet.  Each stage pass costs its
+// rounds of kGT items times the FP64 work of one item, plus a barrier; a
+// tile makes ceil(KB / IC) passes of four stages.  Shapes that leave room for
+// two CTAs per SM (so one CTA's barriers overlap the other's work) are
+// preferred whenever one exists.
 // Tile shape (TQ quartets, IC bra primitives per stage pass): the feasible
 // shape with the lowest modelled time per quartet.  Each stage pass costs its
 // rounds of kGT items times the FP64 work of one item, plus a barrier; a
@@ -512,11 +556,50 @@ static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Processing order.  A batch may mix contraction degrees (a molecule's s
+// shells of K = 6, 3 and 1); the tile loops run to the tile's largest
+// primitive-pair counts, so the quartets are processed sorted by
+// (kb, kk), descending: a counting sort over the keys kb (KK + 1) + kk.
+// Equal keys keep no particular order (only the order of the gradient
+// additions depends on it).
+// ---------------------------------------------------------------------------
+__global__ void order_hist_kernel(GradArgs a, unsigned long long* cnt)
+{
+    for (int64_t qq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qq < a.nq;
+         qq += (int64_t)gridDim.x * blockDim.x) {
+        int b, k;
+        g_pairs(a, qq, &b, &k);
+        atomicAdd(&cnt[a.pb.kp[b] * (a.KK + 1) + a.pk.kp[k]], 1ULL);
+    }
+}
+
+__global__ void order_scan_kernel(int nbins, unsigned long long* cnt)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long run = 0;
+    for (int key = nbins - 1; key >= 0; --key) {
+        const unsigned long long c = cnt[key];
+        cnt[key] = run;
+        run += c;
+    }
+}
+
+__global__ void order_scatter_kernel(GradArgs a, unsigned long long* off, int64_t* order)
+{
+    for (int64_t qq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qq < a.nq;
+         qq += (int64_t)gridDim.x * blockDim.x) {
+        int b, k;
+        g_pairs(a, qq, &b, &k);
+        order[atomicAdd(&off[a.pb.kp[b] * (a.KK + 1) + a.pk.kp[k]], 1ULL)] = qq;
+    }
+}
+
 // One launch: the channels of the kernel's bra.  bra/ket are the kernel's
 // lists (the caller's ket/bra when swap = 1); nbra_o/nket_o are the caller's.
 static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                        int64_t nket, const int64_t* quartets, int64_t nq, const double* W, double* gc, double* ge,
-                       int swap, int64_t nbra_o, int64_t nket_o, cudaStream_t st)
+                       int swap, int64_t nbra_o, int64_t nket_o, int64_t** order, cudaStream_t st)
 {
     const ClassTables* ct = nullptr;
     PairTables pb{}, pk{};
@@ -556,6 +639,26 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     size_t bytes = 0;
     if (!grad_plan(*ct, KB, KK, a.nit, a.nq, &a, &bytes)) return ERI_EINVAL;
     a.ntiles = (a.nq + a.TQ - 1) / a.TQ;
+    if (!*order) {  // first launch: sort; the second (sides exchanged) reuses the order
+        // [nq] order, the two launches' tile queues, [nbins] key counts
+        const int nbins = (KB + 1) * (KK + 1);
+        int64_t* ord = (int64_t*)aux_workspace(sizeof(int64_t) * ((size_t)a.nq + 2 + nbins), &err);
+        if (!ord) return err;
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ord + a.nq + 2);
+        const int g = (int)std::min<int64_t>((a.nq + 255) / 256, (int64_t)sm_count() * 8);
+        if (cudaMemsetAsync(ord + a.nq, 0, sizeof(unsigned long long) * (2 + nbins), st) != cudaSuccess)
+            return ERI_ECUDA;
+        count_launch();
+        order_hist_kernel<<<g, 256, 0, st>>>(a, cnt);
+        count_launch();
+        order_scan_kernel<<<1, 1, 0, st>>>(nbins, cnt);
+        count_launch();
+        order_scatter_kernel<<<g, 256, 0, st>>>(a, cnt, ord);
+        if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+        *order = ord;
+    }
+    a.order = *order;
+    a.next = reinterpret_cast<unsigned long long*>(*order + a.nq) + swap;
     if (cudaFuncSetAttribute(grad_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return ERI_ECUDA;
     int per_sm = 0;
@@ -584,9 +687,10 @@ extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const i
     if (!grad_centres && !grad_exps) return ERI_OK;
     cudaStream_t st = (cudaStream_t)stream;
     // channels of the bra (a, b), then of the ket (c, d) with the sides exchanged
+    int64_t* order = nullptr;
     err = launch_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, grad_centres, grad_exps, 0, nbra,
-                      nket, st);
+                      nket, &order, st);
     if (err != ERI_OK) return err;
     return launch_grad(eri_class_t{cls.lc, cls.ld, cls.la, cls.lb}, basis, ket_pairs, nket, bra_pairs, nbra, quartets,
-                       nq, W, grad_centres, grad_exps, 1, nbra, nket, st);
+                       nq, W, grad_centres, grad_exps, 1, nbra, nket, &order, st);
 }
