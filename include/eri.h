@@ -151,7 +151,7 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
  *             m = -lx..lx, Racah normalisation: S_l0(0,0,1) = 1, and
  *             S_lm over the unit sphere has norm 4 pi / (2l + 1)), whose
  *             transform uses only the terminal Hermite functions of order lx
- *             (Section 3.2.3); 0 => Cartesian x (nc(lx) components).
+ *             (Section 2.2.3); 0 => Cartesian x (nc(lx) components).
  *   out:      list form out[t + nt*(x*ncd + cd)]; product form
  *             out[i + nx*(x + nxc*(cd + ncd*k))], nxc the x component count.
  * The batch runs as the 4-centre kernel on (x 1|cd), 1 being the unit

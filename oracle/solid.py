@@ -16,7 +16,7 @@ with t = 0..floor((l-|m|)/2), u = 0..t, and 2v running over the even
 (m >= 0, v_m = 0) or odd (m < 0, v_m = 1/2) integers up to |m|.  The paper
 uses such Cartesian-to-solid coefficients for its H matrices (Section 2.1,
 Eqs. solid2herm-1 and -2) and for its solid-harmonic 3-centre bra
-(Section 3.2.3).  Every property above is checked independently in
+(Section 2.2.3).  Every property above is checked independently in
 tests/test_oracle_solid.py.
 
 3-centre integrals.  (x|cd) = int int phi_x(r1) r12^-1 phi_c(r2) phi_d(r2) is

@@ -75,7 +75,7 @@ struct ClassTables {
     // bra (la, lb = 0) a real solid harmonic, pure = 2 the kernel ket
     // (lc, ld = 0).  Its rows are m = -l..l (2l+1 of them) and its terms
     // only the terminal Hermite functions |t| = l, each E product scaled by
-    // the Cartesian coefficient of the harmonic (Section 3.2.3).
+    // the Cartesian coefficient of the harmonic (Section 2.2.3).
     int pure;
     // Solid-harmonic output (4-centre): the epilogue maps the contracted
     // Cartesian block to real solid harmonics on every centre, one index at
