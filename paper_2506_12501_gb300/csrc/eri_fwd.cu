@@ -58,6 +58,7 @@ struct PrepassArgs {
     const int32_t* shell_atom;
     const int32_t* shell_off;
     const double* exps;
+    int* kmin;   // optional [2]: the smallest primitive-pair count K1 K2 over bra (ket) pairs
 };
 
 // (2|A-B|)^l2 max over primitive pairs of exp(-z1 z2 / (z1 + z2) |A-B|^2)
@@ -105,6 +106,12 @@ __global__ void prepass_kernel(PrepassArgs a)
                     continue;
                 }
                 atomicMax(&a.info[2 * side + c], K);
+            }
+            if (a.kmin) {
+                const int s1 = pr[2 * i], s2 = pr[2 * i + 1];
+                const bool unit = a.unit_b && side == 0;
+                if (s1 >= 0 && s1 < a.nshell && (unit || (s2 >= 0 && s2 < a.nshell)))
+                    atomicMin(&a.kmin[side], a.shell_K[s1] * (unit ? 1 : a.shell_K[s2]));
             }
             if (a.risk) {
                 const int s1 = pr[2 * i], s2 = pr[2 * i + 1];
@@ -386,7 +393,7 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     tp->o_tab = take((tab_bytes + 7) / 8);
     tp->o_q = take((size_t)TQ * 2);
     tp->o_geo = take(ct.hrr ? (size_t)TQ * 6 : 0);
-    tp->o_dj = take((size_t)TQ + ct.nab_f);
+    tp->o_dj = take((size_t)TQ + ct.nab_f);  // also the quartet indices of a sorted batch
     tp->bytes = off * 8;
     tp->acc_regs = (TQ * ct.nab * ct.ncd <= kNT * kNACC) ? 1 : 0;
     if (ct.hrr && !tp->acc_regs) return false;
@@ -485,7 +492,7 @@ void remember_form(eri_class_t cls, int KB, int KK, int split, int kind, int for
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
-                  int allow_swap, FormChoice* fc, int split, int kind)
+                  int allow_swap, FormChoice* fc, int split, int kind, int* mixed)
 {
     int err = ERI_OK;
     // kind 2: the caller's bra side (x, unit) is a solid harmonic
@@ -506,15 +513,19 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
     }
     int* status = device_status();
     if (!status) return ERI_ECUDA;
-    int32_t* hinfo = host_pinned_i32(8);
+    int32_t* hinfo = host_pinned_i32(16);
     if (!hinfo) return ERI_ENOMEM;
-    // info lives in the status block (slots 8..12), separate from the error word
+    // info lives in the status block (slots 8..16), separate from the error word:
+    // [0..6] as PrepassArgs::info, [7..8] the smallest pair counts per side
     int* dinfo = status + 8;
-    if (cudaMemsetAsync(dinfo, 0, 7 * sizeof(int), st) != cudaSuccess) return ERI_ECUDA;
+    if (cudaMemsetAsync(dinfo, 0, 7 * sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(dinfo + 7, 0x7f, 2 * sizeof(int), st) != cudaSuccess)
+        return ERI_ECUDA;
     PrepassArgs pa{basis->shell_l, basis->shell_K, basis->nshell, bra, nbra, ket, nket, quartets,
                    quartets ? nq : (int64_t)0,
                    {cls.la, cls.lb, cls.lc, cls.ld}, (kind == 1 || kind == 2) ? 1 : 0, dinfo,
-                   allow_swap > 1 ? 1 : 0, basis->centres, basis->shell_atom, basis->shell_off, basis->exps};
+                   allow_swap > 1 ? 1 : 0, basis->centres, basis->shell_atom, basis->shell_off, basis->exps,
+                   dinfo + 7};
     const int64_t n = std::max(std::max(nbra, nket), quartets ? nq : (int64_t)0);
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
     {
@@ -522,12 +533,13 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         prepass_kernel<<<std::max(grid, 1), 256, 0, st>>>(pa);
     }
     if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
-    if (cudaMemcpyAsync(hinfo, dinfo, 7 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ERI_ECUDA;
+    if (cudaMemcpyAsync(hinfo, dinfo, 9 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ERI_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return ERI_ECUDA;
     if (hinfo[4] != 0) return dev_err_to_code(hinfo[4]);
     for (int c = 0; c < 4; ++c) kmax[c] = hinfo[c];
     *KB = kmax[0] * kmax[1];
     *KK = kmax[2] * kmax[3];
+    if (mixed) *mixed = (hinfo[7] < *KB || hinfo[8] < *KK) ? 1 : 0;
     if (allow_swap) {
         // Four forms: which side is transformed first (Section 3.2.2
         // transforms the ket first, assuming it has the lower l) and whether
@@ -788,6 +800,88 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
     return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Processing order (build_order).  A batch may mix contraction degrees (a
+// molecule's s shells of K = 6, 3 and 1); the tile loops run to the tile's
+// largest primitive-pair counts, so the quartets are counting-sorted by the
+// key kb (KK + 1) + kk, descending: histogram, offsets, scatter.  Equal keys
+// keep no particular order (only the positions the tiles read and write from
+// depend on it, not the values).
+// ---------------------------------------------------------------------------
+struct OrderArgs {
+    const int64_t* quartets;  // NULL: product form
+    int64_t nq, nbra;
+    const int32_t* kpb;
+    const int32_t* kpk;
+    int KK, swap;
+};
+
+__device__ __forceinline__ int order_key(const OrderArgs& o, int64_t qq)
+{
+    int64_t ob, ok;
+    if (o.quartets) {
+        ob = o.quartets[2 * qq];
+        ok = o.quartets[2 * qq + 1];
+    } else {
+        ob = qq % o.nbra;
+        ok = qq / o.nbra;
+    }
+    const int64_t b = o.swap ? ok : ob, k = o.swap ? ob : ok;
+    return o.kpb[b] * (o.KK + 1) + o.kpk[k];
+}
+
+__global__ void order_hist_kernel(OrderArgs o, unsigned long long* cnt)
+{
+    for (int64_t qq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qq < o.nq; qq += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[order_key(o, qq)], 1ULL);
+}
+
+__global__ void order_scan_kernel(int nbins, unsigned long long* cnt)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long run = 0;
+    for (int key = nbins - 1; key >= 0; --key) {
+        const unsigned long long c = cnt[key];
+        cnt[key] = run;
+        run += c;
+    }
+}
+
+__global__ void order_scatter_kernel(OrderArgs o, unsigned long long* off, int64_t* order)
+{
+    for (int64_t qq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qq < o.nq; qq += (int64_t)gridDim.x * blockDim.x)
+        order[atomicAdd(&off[order_key(o, qq)], 1ULL)] = qq;
+}
+
+int build_order(const int64_t* quartets, int64_t nq, int64_t nbra, const int32_t* kpb, const int32_t* kpk, int KB,
+                int KK, int swap, int sort, cudaStream_t st, int64_t** order, unsigned long long** queue)
+{
+    int err = ERI_OK;
+    const int nbins = (KB + 1) * (KK + 1);
+    // [2] tile-queue counters, then (sort) [nbins] key counts and [nq] order
+    const size_t n64 = 2 + (sort ? (size_t)nbins + (size_t)nq : 0);
+    unsigned long long* buf = (unsigned long long*)order_workspace(sizeof(unsigned long long) * n64, &err);
+    if (!buf) return err;
+    *queue = buf;
+    *order = nullptr;
+    if (cudaMemsetAsync(buf, 0, sizeof(unsigned long long) * (sort ? 2 + (size_t)nbins : 2), st) != cudaSuccess)
+        return ERI_ECUDA;
+    if (!sort) return ERI_OK;
+    unsigned long long* cnt = buf + 2;
+    int64_t* ord = reinterpret_cast<int64_t*>(cnt + nbins);
+    const OrderArgs o{quartets, nq, nbra, kpb, kpk, KK, swap};
+    const int g = (int)std::min<int64_t>((nq + 255) / 256, (int64_t)sm_count() * 8);
+    count_launch();
+    order_hist_kernel<<<std::max(g, 1), 256, 0, st>>>(o, cnt);
+    count_launch();
+    order_scan_kernel<<<1, 1, 0, st>>>(nbins, cnt);
+    count_launch();
+    order_scatter_kernel<<<std::max(g, 1), 256, 0, st>>>(o, cnt, ord);
+    if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+    *order = ord;
+    return ERI_OK;
+}
+
 }  // namespace eri
 
 using namespace eri;
@@ -870,12 +964,26 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     // transforms' rounding (about 1e-14 of those larger values) past the
     // 1e-10 bar when the centres are far apart.  3-centre batches have none.
     const int allow = (kind == 1 || kind == 2 || split) ? 1 : 2;
-    auto prepare = [&](FormChoice* f, FwdArgs* a, TilePlan* tp) {
+    // a batch that mixes contraction degrees runs its quartets sorted by
+    // (kb, kk), each tile looping to its own largest counts; the order is
+    // built once, in the first form's orientation (the grouping is the same
+    // in the other)
+    int mixed = 0;
+    int64_t* order = nullptr;
+    auto prepare = [&](FormChoice* f, FwdArgs* a, TilePlan* tp) -> int {
         int e = prepare_batch(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, 0, st, &ct, &pb, &pk, &KB,
-                              &KK, kmax, allow, f, split, kind);
+                              &KK, kmax, allow, f, split, kind, &mixed);
         if (e != ERI_OK) return e;
-        return forward_args(basis, bra_pairs, nbra, ket_pairs, nket, quartets, nqq, out, ct, pb, pk, KB, KK,
-                            f->form & 1, st, a, tp);
+        e = forward_args(basis, bra_pairs, nbra, ket_pairs, nket, quartets, nqq, out, ct, pb, pk, KB, KK,
+                         f->form & 1, st, a, tp);
+        if (e != ERI_OK) return e;
+        if (mixed && !order && nqq > 1) {
+            unsigned long long* queue = nullptr;
+            e = build_order(quartets, nqq, nbra, pb.kp, pk.kp, KB, KK, f->form & 1, 1, st, &order, &queue);
+            if (e != ERI_OK) return e;
+        }
+        a->order = order;
+        return ERI_OK;
     };
     FwdArgs a;
     TilePlan tp;

@@ -45,7 +45,7 @@ struct GradArgs {
     const int32_t* shell_off;
     const int32_t* shell_K;
     const int64_t* quartets;   // the caller's list (NULL: product form)
-    const int64_t* order;      // processing order of the caller's quartet indices
+    const int64_t* order;      // processing order of the caller's quartet indices (NULL: identity)
     unsigned long long* next;  // tile queue (zero at launch)
     int64_t nq, nbra, nket;    // the caller's counts
     int swap;                  // 1: the kernel's bra is the caller's ket
@@ -214,22 +214,31 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
         if (tile >= a.ntiles) break;
         const int64_t q0 = tile * TQ;
         const int nqt = (int)min((int64_t)TQ, a.nq - q0);
-        for (int q = tid; q < TQ; q += kGT) {
-            int b = 0, k = 0, kb = 0, kk = 0;
-            int64_t qq = 0;
-            if (q < nqt) {
-                qq = a.order[q0 + q];
-                g_pairs(a, qq, &b, &k);
-                kb = a.pb.kp[b];
-                kk = a.pk.kp[k];
-                atomicMax(&s_kmax[0], kb);
-                atomicMax(&s_kmax[1], kk);
+        {
+            int mkb = 0, mkk = 0;
+            for (int q = tid; q < TQ; q += kGT) {
+                int b = 0, k = 0, kb = 0, kk = 0;
+                int64_t qq = 0;
+                if (q < nqt) {
+                    qq = a.order ? a.order[q0 + q] : q0 + q;
+                    g_pairs(a, qq, &b, &k);
+                    kb = a.pb.kp[b];
+                    kk = a.pk.kp[k];
+                }
+                s_q[4 * q] = b;
+                s_q[4 * q + 1] = k;
+                s_q[4 * q + 2] = kb;
+                s_q[4 * q + 3] = kk;
+                s_qq[q] = qq;
+                mkb = max(mkb, kb);
+                mkk = max(mkk, kk);
             }
-            s_q[4 * q] = b;
-            s_q[4 * q + 1] = k;
-            s_q[4 * q + 2] = kb;
-            s_q[4 * q + 3] = kk;
-            s_qq[q] = qq;
+            mkb = __reduce_max_sync(0xffffffffu, mkb);
+            mkk = __reduce_max_sync(0xffffffffu, mkk);
+            if ((tid & 31) == 0 && mkb > 0) {
+                atomicMax(&s_kmax[0], mkb);
+                atomicMax(&s_kmax[1], mkk);
+            }
         }
         __syncthreads();
         // the tile's own contraction degrees (its quartets share them when sorted)
@@ -556,57 +565,25 @@ static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int
     return true;
 }
 
-// ---------------------------------------------------------------------------
-// Processing order.  A batch may mix contraction degrees (a molecule's s
-// shells of K = 6, 3 and 1); the tile loops run to the tile's largest
-// primitive-pair counts, so the quartets are processed sorted by
-// (kb, kk), descending: a counting sort over the keys kb (KK + 1) + kk.
-// Equal keys keep no particular order (only the order of the gradient
-// additions depends on it).
-// ---------------------------------------------------------------------------
-__global__ void order_hist_kernel(GradArgs a, unsigned long long* cnt)
-{
-    for (int64_t qq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qq < a.nq;
-         qq += (int64_t)gridDim.x * blockDim.x) {
-        int b, k;
-        g_pairs(a, qq, &b, &k);
-        atomicAdd(&cnt[a.pb.kp[b] * (a.KK + 1) + a.pk.kp[k]], 1ULL);
-    }
-}
-
-__global__ void order_scan_kernel(int nbins, unsigned long long* cnt)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long run = 0;
-    for (int key = nbins - 1; key >= 0; --key) {
-        const unsigned long long c = cnt[key];
-        cnt[key] = run;
-        run += c;
-    }
-}
-
-__global__ void order_scatter_kernel(GradArgs a, unsigned long long* off, int64_t* order)
-{
-    for (int64_t qq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qq < a.nq;
-         qq += (int64_t)gridDim.x * blockDim.x) {
-        int b, k;
-        g_pairs(a, qq, &b, &k);
-        order[atomicAdd(&off[a.pb.kp[b] * (a.KK + 1) + a.pk.kp[k]], 1ULL)] = qq;
-    }
-}
+// The quartet order and the two tile queues, shared by the two launches.
+struct GradOrder {
+    int64_t* order = nullptr;            // NULL: the identity
+    unsigned long long* queue = nullptr;
+};
 
 // One launch: the channels of the kernel's bra.  bra/ket are the kernel's
 // lists (the caller's ket/bra when swap = 1); nbra_o/nket_o are the caller's.
 static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                        int64_t nket, const int64_t* quartets, int64_t nq, const double* W, double* gc, double* ge,
-                       int swap, int64_t nbra_o, int64_t nket_o, int64_t** order, cudaStream_t st)
+                       int swap, int64_t nbra_o, int64_t nket_o, GradOrder* ord, cudaStream_t st)
 {
     const ClassTables* ct = nullptr;
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
     // the quartet indices refer to the caller's lists: validated on the first launch only
+    int mixed = 0;
     int err = prepare_batch(cls, basis, bra, nbra, ket, nket, swap ? nullptr : quartets, swap ? 0 : nq, 2, st, &ct,
-                            &pb, &pk, &KB, &KK, kmax, 0, nullptr);
+                            &pb, &pk, &KB, &KK, kmax, 0, nullptr, 0, 0, &mixed);
     if (err != ERI_OK) return err;
     if (ct->L + 2 > kLtotMax) return ERI_EINVAL;
     GradArgs a{};
@@ -639,26 +616,12 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     size_t bytes = 0;
     if (!grad_plan(*ct, KB, KK, a.nit, a.nq, &a, &bytes)) return ERI_EINVAL;
     a.ntiles = (a.nq + a.TQ - 1) / a.TQ;
-    if (!*order) {  // first launch: sort; the second (sides exchanged) reuses the order
-        // [nq] order, the two launches' tile queues, [nbins] key counts
-        const int nbins = (KB + 1) * (KK + 1);
-        int64_t* ord = (int64_t*)aux_workspace(sizeof(int64_t) * ((size_t)a.nq + 2 + nbins), &err);
-        if (!ord) return err;
-        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ord + a.nq + 2);
-        const int g = (int)std::min<int64_t>((a.nq + 255) / 256, (int64_t)sm_count() * 8);
-        if (cudaMemsetAsync(ord + a.nq, 0, sizeof(unsigned long long) * (2 + nbins), st) != cudaSuccess)
-            return ERI_ECUDA;
-        count_launch();
-        order_hist_kernel<<<g, 256, 0, st>>>(a, cnt);
-        count_launch();
-        order_scan_kernel<<<1, 1, 0, st>>>(nbins, cnt);
-        count_launch();
-        order_scatter_kernel<<<g, 256, 0, st>>>(a, cnt, ord);
-        if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
-        *order = ord;
+    if (!ord->queue) {  // first launch: order (sorted if the batch mixes degrees); the second reuses it
+        err = build_order(quartets, a.nq, nbra_o, pb.kp, pk.kp, KB, KK, swap, mixed, st, &ord->order, &ord->queue);
+        if (err != ERI_OK) return err;
     }
-    a.order = *order;
-    a.next = reinterpret_cast<unsigned long long*>(*order + a.nq) + swap;
+    a.order = ord->order;
+    a.next = ord->queue + swap;
     if (cudaFuncSetAttribute(grad_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return ERI_ECUDA;
     int per_sm = 0;
@@ -687,7 +650,7 @@ extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const i
     if (!grad_centres && !grad_exps) return ERI_OK;
     cudaStream_t st = (cudaStream_t)stream;
     // channels of the bra (a, b), then of the ket (c, d) with the sides exchanged
-    int64_t* order = nullptr;
+    GradOrder order;
     err = launch_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, grad_centres, grad_exps, 0, nbra,
                       nket, &order, st);
     if (err != ERI_OK) return err;

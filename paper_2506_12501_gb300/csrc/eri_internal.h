@@ -148,10 +148,20 @@ void remember_form(eri_class_t cls, int KB, int KK, int split, int kind, int for
 // the unit function, an s Gaussian of exponent 0 and coefficient 1);
 // 2: 3-centre with x a real solid harmonic; 3: 4-centre with solid-harmonic
 // output on every centre.
+// mixed (optional out): 1 when the listed pairs of a side differ in their
+// primitive-pair counts (the batch mixes contraction degrees).
 int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                   int64_t nket, const int64_t* quartets, int64_t nq, int ldelta, cudaStream_t st,
                   const ClassTables** ct_out, PairTables* pb, PairTables* pk, int* KB, int* KK, int kmax[4],
-                  int allow_swap, FormChoice* fc, int split = 0, int kind = 0);
+                  int allow_swap, FormChoice* fc, int split = 0, int kind = 0, int* mixed = nullptr);
+// Processing order of a batch's quartets (list or product form, caller's
+// indices): sorted by the kernel-orientation primitive-pair counts (kb, kk),
+// descending, so that a tile's quartets share them (sort = 1; else *order =
+// nullptr, the identity).  kpb/kpk: the kernel's per-pair counts (<= KB, KK);
+// swap: the kernel's bra is the caller's ket.  *queue: two zeroed tile-queue
+// counters.  Lives in order_workspace until the next call.
+int build_order(const int64_t* quartets, int64_t nq, int64_t nbra, const int32_t* kpb, const int32_t* kpk, int KB,
+                int KK, int swap, int sort, cudaStream_t st, int64_t** order, unsigned long long** queue);
 int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                  int64_t nket, const int64_t* quartets, int64_t nq, double* out, const ClassTables& ct,
                  const double* boys, const RStep* rs, int* dinfo, double* scratch, size_t scratch_doubles,
@@ -189,6 +199,7 @@ void count_launch();
 // Device workspace (grows, cached per process; calls on one device serialise)
 void* workspace(size_t bytes, int* err);
 void* aux_workspace(size_t bytes, int* err);  // a second cached buffer (3-centre pair lists)
+void* order_workspace(size_t bytes, int* err);  // a third (quartet processing orders, tile queues)
 int* device_status();   // device error word
 int32_t* host_pinned_i32(int n);
 

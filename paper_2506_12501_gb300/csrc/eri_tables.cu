@@ -539,6 +539,8 @@ struct DevState {
     size_t ws_bytes = 0;
     void* aux = nullptr;
     size_t aux_bytes = 0;
+    void* ord = nullptr;
+    size_t ord_bytes = 0;
     int* status = nullptr;
 };
 static std::map<int, DevState> g_dev;
@@ -590,6 +592,29 @@ void* aux_workspace(size_t bytes, int* err)
     return d.aux;
 }
 
+void* order_workspace(size_t bytes, int* err)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevState& d = g_dev[dev];
+    if (bytes <= d.ord_bytes) return d.ord;
+    if (d.ord) {
+        cudaDeviceSynchronize();
+        cudaFree(d.ord);
+        d.ord = nullptr;
+        d.ord_bytes = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&d.ord, want) != cudaSuccess) {
+        cudaGetLastError();
+        *err = ERI_ENOMEM;
+        return nullptr;
+    }
+    d.ord_bytes = want;
+    return d.ord;
+}
+
 int* device_status()
 {
     int dev = 0;
@@ -597,8 +622,8 @@ int* device_status()
     std::lock_guard<std::mutex> lk(g_dev_mu);
     DevState& d = g_dev[dev];
     if (!d.status) {
-        if (cudaMalloc(&d.status, 64) != cudaSuccess) return nullptr;
-        cudaMemset(d.status, 0, 64);
+        if (cudaMalloc(&d.status, 128) != cudaSuccess) return nullptr;
+        cudaMemset(d.status, 0, 128);
         cudaDeviceSynchronize();
     }
     return d.status;
@@ -632,6 +657,7 @@ void release_all()
         if (it != g_dev.end()) {
             if (it->second.ws) cudaFree(it->second.ws);
             if (it->second.aux) cudaFree(it->second.aux);
+            if (it->second.ord) cudaFree(it->second.ord);
             if (it->second.status) cudaFree(it->second.status);
             g_dev.erase(it);
         }

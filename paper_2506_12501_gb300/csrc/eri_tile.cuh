@@ -53,6 +53,7 @@ struct FwdArgs {
     const double* ket_E;
     const int32_t* ket_kp;
     const int64_t* quartets;  // NULL: product form
+    const int64_t* order;     // processing order of the quartet indices (NULL: identity)
     int64_t nq, nbra, nket;   // nbra/nket: the caller's lists (before any swap)
     int swap;                 // 1: the kernel's bra is the caller's ket
     int nab_o, ncd_o;         // component-pair counts of the caller's class
@@ -386,26 +387,47 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     const int16_t* s_kq = s_bp + ct.Tab;
     const int16_t* s_pq = s_kq + ct.Tcd;
     int* s_q = reinterpret_cast<int*>(sm + a.o_q);  // [TQ][4]: bra, ket, Kbra, Kket
+    // [TQ] quartet indices of a sorted batch (order != NULL, eri_batch only),
+    // kept in the Coulomb-digestion scratch, which only plans (never sorted) use
+    int64_t* s_qq = reinterpret_cast<int64_t*>(sm + a.o_dj);
+    __shared__ int s_kmax[2];
     double* sEb = sm + a.o_Eb;
     double* sEk = sm + a.o_Ek;
     double* sPb = sm + a.o_Pb;
     double* sPk = sm + a.o_Pk;
     double* sR = sm + a.o_R;
     double* sX = sm + a.o_X;
+    if (tid == 0) s_kmax[0] = s_kmax[1] = 0;
     __syncthreads();
-    for (int q = tid; q < TQ; q += kNT) {
-        int b = 0, k = 0, kb = 0, kk = 0;
-        if (q < nqt) {
-            quartet_pairs(a, q0 + q, &b, &k);
-            kb = a.bra_kp[b];
-            kk = a.ket_kp[k];
+    {
+        int mkb = 0, mkk = 0;
+        for (int q = tid; q < TQ; q += kNT) {
+            int b = 0, k = 0, kb = 0, kk = 0;
+            const int64_t qq = q < nqt && a.order ? a.order[q0 + q] : q0 + q;
+            if (q < nqt) {
+                quartet_pairs(a, qq, &b, &k);
+                kb = a.bra_kp[b];
+                kk = a.ket_kp[k];
+            }
+            s_q[4 * q] = b;
+            s_q[4 * q + 1] = k;
+            s_q[4 * q + 2] = kb;
+            s_q[4 * q + 3] = kk;
+            if (a.order) s_qq[q] = qq;
+            mkb = max(mkb, kb);
+            mkk = max(mkk, kk);
         }
-        s_q[4 * q] = b;
-        s_q[4 * q + 1] = k;
-        s_q[4 * q + 2] = kb;
-        s_q[4 * q + 3] = kk;
+        mkb = __reduce_max_sync(0xffffffffu, mkb);
+        mkk = __reduce_max_sync(0xffffffffu, mkk);
+        if ((tid & 31) == 0 && mkb > 0) {
+            atomicMax(&s_kmax[0], mkb);
+            atomicMax(&s_kmax[1], mkk);
+        }
     }
     __syncthreads();
+    // the tile's own largest primitive-pair counts (a sorted batch's tiles share them)
+    const int KBt = s_kmax[0], KKt = s_kmax[1];
+    const int NIt = TQ * IC * KKt;  // stage-A items of this tile
     // stage primitive-pair scalars (and E products) of the tile
     for (int idx = tid; idx < TQ * KB * PS_N; idx += kNT) {
         const int q = idx / (KB * PS_N), r = idx - q * KB * PS_N, i = r / PS_N;
@@ -431,17 +453,16 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
 #pragma unroll
     for (int s = 0; s < kNACC; ++s) acc[s] = 0.0;
 
-    for (int i0 = 0; i0 < KB; i0 += IC) {
+    for (int i0 = 0; i0 < KBt; i0 += IC) {
         __syncthreads();
-        // ---- A: auxiliary integrals of the primitive quartets (q, i0+ii, k)
-        // few items (small tiles of high-l classes with K = 1): a warp shares
-        // each item's recursion instead of leaving most threads idle
-        const bool coop = NI * 4 < kNT;
+        // ---- A: auxiliary integrals of the primitive quartets (q, i0+ii, k),
+        // k < KKt; few items (small tiles of high-l classes with K = 1): a warp
+        // shares each item's recursion instead of leaving most threads idle
+        const bool coop = NIt * 4 < kNT;
         const int lane = tid & 31;
-        for (int item = coop ? tid >> 5 : tid; item < NI; item += coop ? kNT / 32 : kNT) {
-            const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
+        auto stage_a_item = [&](int q, int ii, int k) {
             const int i = i0 + ii;
-            Strided R{sR + item, NIs};
+            Strided R{sR + (q * IC + ii) * KK + k, NIs};
             const int e0 = coop ? lane : 0, de = coop ? 32 : 1;
             if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
                 const double* pb = sPb + (q * KB + i) * PS_N;
@@ -473,9 +494,23 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             } else {
                 for (int e = e0; e < nhl; e += de) R[e] = 0.0;
             }
+        };
+        // the decode divides by the tile's ket count; a tile at the batch's
+        // own counts (every tile of a uniform batch) divides by the kernel
+        // argument instead, which the compiler keeps in uniform registers
+        if (KKt == KK) {
+            for (int item = coop ? tid >> 5 : tid; item < NIt; item += coop ? kNT / 32 : kNT) {
+                const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
+                stage_a_item(q, ii, k);
+            }
+        } else {
+            for (int item = coop ? tid >> 5 : tid; item < NIt; item += coop ? kNT / 32 : kNT) {
+                const int q = item / (IC * KKt), r = item - q * IC * KKt, ii = r / KKt, k = r - ii * KKt;
+                stage_a_item(q, ii, k);
+            }
         }
         __syncthreads();
-        for (int ii = 0; ii < IC && i0 + ii < KB; ++ii) {
+        for (int ii = 0; ii < IC && i0 + ii < KBt; ++ii) {
             const int i = i0 + ii;
             // ---- B: ket transform + ket contraction
             // only the bra Hermite functions the bra transform reads (all of
@@ -502,13 +537,13 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                         const double* Ea = Ek + t * KK;
                         const double* Eb2 = Ea + KK;
                         int k = 0;
-                        for (; k + 1 < KK; k += 2) {
+                        for (; k + 1 < KKt; k += 2) {
                             v0 = fma(Ea[k], Ra[k], v0);
                             v1 = fma(Ea[k + 1], Ra[k + 1], v1);
                             v2 = fma(Eb2[k], Rb[k], v2);
                             v3 = fma(Eb2[k + 1], Rb[k + 1], v3);
                         }
-                        if (k < KK) {
+                        if (k < KKt) {
                             v0 = fma(Ea[k], Ra[k], v0);
                             v2 = fma(Eb2[k], Rb[k], v2);
                         }
@@ -517,11 +552,11 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                         const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NIs;
                         const double* Ea = Ek + t * KK;
                         int k = 0;
-                        for (; k + 1 < KK; k += 2) {
+                        for (; k + 1 < KKt; k += 2) {
                             v0 = fma(Ea[k], Ra[k], v0);
                             v1 = fma(Ea[k + 1], Ra[k + 1], v1);
                         }
-                        if (k < KK) v0 = fma(Ea[k], Ra[k], v0);
+                        if (k < KKt) v0 = fma(Ea[k], Ra[k], v0);
                     }
                     sX[(p * ncd + cd) * TQ + q] = (v0 + v1) + (v2 + v3);
                 } else {
@@ -533,13 +568,13 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                         const float2* Ea = reinterpret_cast<const float2*>(Ek + t * KK);
                         const float2* Eb2 = Ea + KK;
                         int k = 0;
-                        for (; k + 1 < KK; k += 2) {
+                        for (; k + 1 < KKt; k += 2) {
                             ff_mac(Ea[k], Ra[k], S[0], c[0]);
                             ff_mac(Ea[k + 1], Ra[k + 1], S[1], c[1]);
                             ff_mac(Eb2[k], Rb[k], S[2], c[2]);
                             ff_mac(Eb2[k + 1], Rb[k + 1], S[3], c[3]);
                         }
-                        if (k < KK) {
+                        if (k < KKt) {
                             ff_mac(Ea[k], Ra[k], S[0], c[0]);
                             ff_mac(Eb2[k], Rb[k], S[2], c[2]);
                         }
@@ -548,11 +583,11 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                         const float2* Ra = reinterpret_cast<const float2*>(Rc + (size_t)pqrow[s_kq[t]] * NIs);
                         const float2* Ea = reinterpret_cast<const float2*>(Ek + t * KK);
                         int k = 0;
-                        for (; k + 1 < KK; k += 2) {
+                        for (; k + 1 < KKt; k += 2) {
                             ff_mac(Ea[k], Ra[k], S[0], c[0]);
                             ff_mac(Ea[k + 1], Ra[k + 1], S[1], c[1]);
                         }
-                        if (k < KK) ff_mac(Ea[k], Ra[k], S[0], c[0]);
+                        if (k < KKt) ff_mac(Ea[k], Ra[k], S[0], c[0]);
                     }
                     // fold the four chains into one split pair (error-free sums of the highs)
                     float Sh = S[0], ch = c[0];
@@ -587,7 +622,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     const double* Eb = a.e_smem ? sEb + q * a.sEbS : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab;
                     const double v =
                         bra_sum<SPLIT>(Eb + i, KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
-                    const int64_t o = out_index(a, q0 + q, ab, cd);
+                    const int64_t o = out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd);
                     a.out[o] = (i == 0) ? v : a.out[o] + v;
                 }
             }
@@ -608,7 +643,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             const double* fin = to_solid_harmonics(a, buf, 0);
             for (int item = tid; item < TQ * ct.nab_s * ct.ncd_s; item += kNT) {
                 const int q = item % TQ, r = item / TQ, cd = r % ct.ncd_s, ab = r / ct.ncd_s;
-                if (q < nqt) a.out[out_index(a, q0 + q, ab, cd)] = fin[item];
+                if (q < nqt) a.out[out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd)] = fin[item];
             }
         } else if (!ct.hrr && (a.Jmat || a.Kmat)) {
             // the values go to shared memory (the staging regions are dead)
@@ -630,7 +665,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                         if (a.energy)
                             esum = fma(acc[s], digest_weight(a, s_q[4 * q], s_q[4 * q + 1], ab, cd), esum);
                         else
-                            a.out[out_index(a, q0 + q, ab, cd)] = acc[s];
+                            a.out[out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd)] = acc[s];
                     }
                 }
             }
@@ -690,7 +725,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 const double* fs = to_solid_harmonics(a, hbuf, g & 1);
                 for (int item = tid; item < TQ * ct.nab_s * ct.ncd_s; item += kNT) {
                     const int q = item % TQ, r = item / TQ, cd = r % ct.ncd_s, ab = r / ct.ncd_s;
-                    if (q < nqt) a.out[out_index(a, q0 + q, ab, cd)] = fs[item];
+                    if (q < nqt) a.out[out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd)] = fs[item];
                 }
             } else if (a.Jmat || a.Kmat) {
                 if (a.Jmat) digest_coulomb(a, fin, nqt, s_q, sm + a.o_dj);
@@ -702,7 +737,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     if (a.energy)
                         esum = fma(fin[item], digest_weight(a, s_q[4 * q], s_q[4 * q + 1], ab, cd), esum);
                     else
-                        a.out[out_index(a, q0 + q, ab, cd)] = fin[item];
+                        a.out[out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd)] = fin[item];
                 }
             }
         }

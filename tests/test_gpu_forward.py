@@ -120,6 +120,43 @@ def test_mixed_contraction_degrees(cuda):
         assert_close(got, ref, what=f"mixed K {cls}")
 
 
+@pytest.mark.parametrize("cls", [(0, 0, 0, 0), (1, 0, 1, 0), (1, 1, 1, 0), (2, 0, 1, 1), (2, 1, 0, 0)])
+def test_mixed_degrees_sorted_batches(cuda, cls):
+    """Batches mixing K = 6, 3 and 1 run their quartets sorted by the
+    primitive-pair counts, each tile looping to its own largest: the list form
+    (every form forced in turn, and the split precision), the product form,
+    and a batch large enough for the tile tuner, checked on a sample."""
+    basis = synth.molecule_basis(natom=6, radius=3.0, seed=2)
+    by_l = {l: np.where(basis.shell_l == l)[0].astype(np.int32) for l in range(3)}
+    rng = np.random.default_rng([11, *cls])
+    bra = np.stack([rng.choice(by_l[cls[0]], 30), rng.choice(by_l[cls[1]], 30)], 1).astype(np.int32)
+    ket = np.stack([rng.choice(by_l[cls[2]], 25), rng.choice(by_l[cls[3]], 25)], 1).astype(np.int32)
+    q = np.stack([rng.integers(0, 30, 300), rng.integers(0, 25, 300)], 1).astype(np.int64)
+    ref = oracle_blocks(cls, basis, bra, ket, q)
+    db = eri.DeviceBasis(basis)
+    try:
+        for form in range(4):
+            eri.eri_set_forms(1 << form)
+            assert_close(gpu_list(cls, basis, bra, ket, q, dbasis=db), ref, what=f"mixed K {cls} form {form}")
+    finally:
+        eri.eri_set_forms(0)
+    assert_close(gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT, dbasis=db), ref,
+                 what=f"mixed K split {cls}")
+    # product form: [kl][cd][ab][ij]
+    nb, nk = 12, 9
+    b, k, _ = to_device(bra[:nb], ket[:nk])
+    out = eri.eri_batch(cls, db, b, k, None).cpu().numpy()
+    nab, ncd = nc(cls[0]) * nc(cls[1]), nc(cls[2]) * nc(cls[3])
+    qp = np.array([(i, j) for j in range(nk) for i in range(nb)], dtype=np.int64)
+    refp = oracle_blocks(cls, basis, bra[:nb], ket[:nk], qp).reshape(nk, nb, nab, ncd)
+    assert_close(out.reshape(nk, ncd, nab, nb), refp.transpose(0, 3, 2, 1), what=f"mixed K product {cls}")
+    # a tuned batch: 2e4 quartets, a sample of 200 against the oracle
+    qb = np.stack([rng.integers(0, 30, 20000), rng.integers(0, 25, 20000)], 1).astype(np.int64)
+    big = gpu_list(cls, basis, bra, ket, qb, dbasis=db)
+    pick = rng.choice(20000, 200, replace=False)
+    assert_close(big[pick], oracle_blocks(cls, basis, bra, ket, qb[pick]), what=f"mixed K tuned {cls}")
+
+
 def test_bra_ket_swap_symmetry(cuda):
     """(ab|cd) = (cd|ab): the GPU result of class (2,1|1,0) equals the
     transposed result of class (1,0|2,1) on swapped lists."""
