@@ -83,6 +83,7 @@ __device__ __forceinline__ void set_err(int* p, int code) { atomicCAS(p, 0, code
 __global__ void prepass_kernel(PrepassArgs a)
 {
     const int64_t n = max(max(a.nbra, a.nket), a.nq);
+    int kmin[2] = {0x7fffffff, 0x7fffffff};  // this thread's smallest pair counts, reduced per warp at the end
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         for (int side = 0; side < 2; ++side) {
             const int32_t* pr = side == 0 ? a.bra : a.ket;
@@ -111,7 +112,7 @@ __global__ void prepass_kernel(PrepassArgs a)
                 const int s1 = pr[2 * i], s2 = pr[2 * i + 1];
                 const bool unit = a.unit_b && side == 0;
                 if (s1 >= 0 && s1 < a.nshell && (unit || (s2 >= 0 && s2 < a.nshell)))
-                    atomicMin(&a.kmin[side], a.shell_K[s1] * (unit ? 1 : a.shell_K[s2]));
+                    kmin[side] = min(kmin[side], a.shell_K[s1] * (unit ? 1 : a.shell_K[s2]));
             }
             if (a.risk) {
                 const int s1 = pr[2 * i], s2 = pr[2 * i + 1];
@@ -127,6 +128,13 @@ __global__ void prepass_kernel(PrepassArgs a)
         if (a.quartets && i < a.nq) {
             const int64_t b = a.quartets[2 * i], k = a.quartets[2 * i + 1];
             if (b < 0 || b >= a.nbra || k < 0 || k >= a.nket) set_err(&a.info[4], DEV_EINDEX);
+        }
+    }
+    if (a.kmin) {  // every thread of the block reaches this point
+        const int m0 = __reduce_min_sync(0xffffffffu, kmin[0]), m1 = __reduce_min_sync(0xffffffffu, kmin[1]);
+        if ((threadIdx.x & 31) == 0) {
+            if (m0 != 0x7fffffff) atomicMin(&a.kmin[0], m0);
+            if (m1 != 0x7fffffff) atomicMin(&a.kmin[1], m1);
         }
     }
 }
@@ -772,14 +780,22 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
         const int64_t nq = std::min(base.nq, std::max(kTuneQuartets, 4 * slots * tp.TQ));
         a.ntiles = (nq + tp.TQ - 1) / tp.TQ;
         const int64_t grid = std::min<int64_t>(a.ntiles, slots);
-        float ms = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {
+        // one warm-up launch, then the fastest of three timed ones: candidates
+        // often lie within a few per cent of each other
+        float ms = 3e38f;
+        bool timed = true;
+        count_launch();
+        kern<<<(int)grid, kNT, tp.bytes, st>>>(a);
+        for (int rep = 0; rep < 3 && timed; ++rep) {
+            float t = 0.f;
             cudaEventRecord(e0, st);
             count_launch();
             kern<<<(int)grid, kNT, tp.bytes, st>>>(a);
             cudaEventRecord(e1, st);
+            timed = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+            ms = std::min(ms, t);
         }
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (!timed) {
             cudaGetLastError();
             continue;
         }
