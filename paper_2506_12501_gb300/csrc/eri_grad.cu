@@ -94,10 +94,15 @@ __device__ __forceinline__ int64_t g_windex(const GradArgs& a, int64_t qq, int a
 // per axis.  A one-dimensional E^{ij}_t vanishes for t > i + j, so (ab, p')
 // contributes only if t_j <= a_j + b_j on all axes but at most one, which may
 // exceed it by 1 or 2.  The item list holds exactly those pairs of a class
-// (46 % of all (ab, p') for d-d), each as
-//   .x = ab | p' << 16,
+// (46 % of all (ab, p') for d-d).  A pair that exceeds on axis i has zero
+// weight in every channel but those of axis i and the exponents (E^{ab} of
+// axis i vanishes there), and by 2 also in the A_i and B_i channels: such
+// items get their own, shorter channel code.  Each item is
+//   .x = ab | p' << 10 | kind << 20, kind 0: within a_j + b_j on every axis,
+//        1 + i: above by 1 on axis i, 4 + i: above by 2 on axis i;
 //   .y = the per-axis derived-table offsets (a_i (lb+1) + b_i) nt + t_i,
-//        nt = la + lb + 3, at bits 0, 10 and 20.
+//        nt = la + lb + 3, at bits 0, 10 and 20,
+// ordered by kind, so that neighbouring lanes mostly take the same code.
 // ---------------------------------------------------------------------------
 struct ItemTable {
     const int2* list[kLmax + 1][kLmax + 1];
@@ -127,6 +132,7 @@ static const ItemTable* get_items(cudaStream_t s, int* err)
     for (int la = 0; la <= kLmax; ++la)
         for (int lb = 0; lb <= kLmax; ++lb) {
             start[la][lb] = (int)all.size();
+            std::vector<int2> by_kind[7];
             const auto ca = cart_list(la), cb = cart_list(lb);
             const int nt = la + lb + 3, N2 = la + lb + 2;
             for (int ia = 0; ia < (int)ca.size(); ++ia)
@@ -136,18 +142,23 @@ static const ItemTable* get_items(cudaStream_t s, int* err)
                         for (int tt = N; tt >= 0; --tt)
                             for (int uu = N - tt; uu >= 0; --uu) {
                                 const int h[3] = {tt, uu, N - tt - uu};
-                                int over = 0, ok = 1, off[3];
+                                int over = 0, ok = 1, kind = 0, off[3];
                                 for (int x = 0; x < 3; ++x) {
                                     const int e = h[x] - ca[ia][x] - cb[ib][x];
                                     if (e > 2) ok = 0;
-                                    if (e > 0) ++over;
+                                    if (e > 0) {
+                                        ++over;
+                                        kind = (e == 1 ? 1 : 4) + x;
+                                    }
                                     off[x] = (ca[ia][x] * (lb + 1) + cb[ib][x]) * nt + h[x];
                                 }
                                 if (!ok || over > 1) continue;
                                 const int p = herm_index(h[0], h[1], h[2]);
-                                all.push_back(make_int2(ab | (p << 16), off[0] | (off[1] << 10) | (off[2] << 20)));
+                                by_kind[kind].push_back(
+                                    make_int2(ab | (p << 10) | (kind << 20), off[0] | (off[1] << 10) | (off[2] << 20)));
                             }
                 }
+            for (const auto& v : by_kind) all.insert(all.end(), v.begin(), v.end());
             t.n[la][lb] = (int)all.size() - start[la][lb];
         }
     int2* d = nullptr;
@@ -403,8 +414,8 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                         const double* Dq = sD + (size_t)(ii * TQ + q) * PST;
                         for (int j = s; j < nit; j += G) {
                             const int2 g = __ldg(a.items + j);
-                            const double* w = wq + (g.x & 0xffff) * ncd;
-                            const double* xv = xq + (g.x >> 16) * Xs;
+                            const double* w = wq + (g.x & 1023) * ncd;
+                            const double* xv = xq + ((g.x >> 10) & 1023) * Xs;
                             double ya = 0.0, yb = 0.0;
                             int cd = 0;
                             for (; cd + 1 < ncd; cd += 2) {
@@ -416,21 +427,68 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                             const double* Dx = Dq + (g.y & 1023);
                             const double* Dy = Dq + 5 * ND + ((g.y >> 10) & 1023);
                             const double* Dz = Dq + 10 * ND + (g.y >> 20);
-                            const double ex = Dx[0], ey = Dy[0], ez = Dz[0];
-                            const double yx = y * ex;
-                            const double pyz = y * ey * ez, pxz = yx * ez, pxy = yx * ey;
-                            ch[0] = fma(Dx[ND], pyz, ch[0]);
-                            ch[3] = fma(Dx[2 * ND], pyz, ch[3]);
-                            ch[6] = fma(Dx[3 * ND], pyz, ch[6]);
-                            ch[7] = fma(Dx[4 * ND], pyz, ch[7]);
-                            ch[1] = fma(Dy[ND], pxz, ch[1]);
-                            ch[4] = fma(Dy[2 * ND], pxz, ch[4]);
-                            ch[6] = fma(Dy[3 * ND], pxz, ch[6]);
-                            ch[7] = fma(Dy[4 * ND], pxz, ch[7]);
-                            ch[2] = fma(Dz[ND], pxy, ch[2]);
-                            ch[5] = fma(Dz[2 * ND], pxy, ch[5]);
-                            ch[6] = fma(Dz[3 * ND], pxy, ch[6]);
-                            ch[7] = fma(Dz[4 * ND], pxy, ch[7]);
+                            switch (g.x >> 20) {
+                                case 0: {  // every channel
+                                    const double ex = Dx[0], ey = Dy[0], ez = Dz[0];
+                                    const double yx = y * ex;
+                                    const double pyz = y * ey * ez, pxz = yx * ez, pxy = yx * ey;
+                                    ch[0] = fma(Dx[ND], pyz, ch[0]);
+                                    ch[3] = fma(Dx[2 * ND], pyz, ch[3]);
+                                    ch[6] = fma(Dx[3 * ND], pyz, ch[6]);
+                                    ch[7] = fma(Dx[4 * ND], pyz, ch[7]);
+                                    ch[1] = fma(Dy[ND], pxz, ch[1]);
+                                    ch[4] = fma(Dy[2 * ND], pxz, ch[4]);
+                                    ch[6] = fma(Dy[3 * ND], pxz, ch[6]);
+                                    ch[7] = fma(Dy[4 * ND], pxz, ch[7]);
+                                    ch[2] = fma(Dz[ND], pxy, ch[2]);
+                                    ch[5] = fma(Dz[2 * ND], pxy, ch[5]);
+                                    ch[6] = fma(Dz[3 * ND], pxy, ch[6]);
+                                    ch[7] = fma(Dz[4 * ND], pxy, ch[7]);
+                                    break;
+                                }
+                                case 1: {  // above by 1 on x: A_x, B_x and the exponents
+                                    const double r = y * Dy[0] * Dz[0];
+                                    ch[0] = fma(Dx[ND], r, ch[0]);
+                                    ch[3] = fma(Dx[2 * ND], r, ch[3]);
+                                    ch[6] = fma(Dx[3 * ND], r, ch[6]);
+                                    ch[7] = fma(Dx[4 * ND], r, ch[7]);
+                                    break;
+                                }
+                                case 2: {
+                                    const double r = y * Dx[0] * Dz[0];
+                                    ch[1] = fma(Dy[ND], r, ch[1]);
+                                    ch[4] = fma(Dy[2 * ND], r, ch[4]);
+                                    ch[6] = fma(Dy[3 * ND], r, ch[6]);
+                                    ch[7] = fma(Dy[4 * ND], r, ch[7]);
+                                    break;
+                                }
+                                case 3: {
+                                    const double r = y * Dx[0] * Dy[0];
+                                    ch[2] = fma(Dz[ND], r, ch[2]);
+                                    ch[5] = fma(Dz[2 * ND], r, ch[5]);
+                                    ch[6] = fma(Dz[3 * ND], r, ch[6]);
+                                    ch[7] = fma(Dz[4 * ND], r, ch[7]);
+                                    break;
+                                }
+                                case 4: {  // above by 2 on x: the exponents only
+                                    const double r = y * Dy[0] * Dz[0];
+                                    ch[6] = fma(Dx[3 * ND], r, ch[6]);
+                                    ch[7] = fma(Dx[4 * ND], r, ch[7]);
+                                    break;
+                                }
+                                case 5: {
+                                    const double r = y * Dx[0] * Dz[0];
+                                    ch[6] = fma(Dy[3 * ND], r, ch[6]);
+                                    ch[7] = fma(Dy[4 * ND], r, ch[7]);
+                                    break;
+                                }
+                                default: {
+                                    const double r = y * Dx[0] * Dy[0];
+                                    ch[6] = fma(Dz[3 * ND], r, ch[6]);
+                                    ch[7] = fma(Dz[4 * ND], r, ch[7]);
+                                    break;
+                                }
+                            }
                         }
                     }
                     for (int o = G >> 1; o > 0; o >>= 1)

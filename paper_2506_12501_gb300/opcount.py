@@ -165,12 +165,13 @@ def sparse_flops3(cls3, Kx: int, Kket: int, pure: bool, swapped: bool, pure_term
     return kb * kk * (prim_quartet_flops(L) + ket) + kb * bra
 
 
-def grad_items(la: int, lb: int) -> int:
-    """Channel items of a bra class: the (ab, p') pairs, p' = (t, u, v) of
-    order <= la + lb + 2, with t_i <= a_i + b_i on all axes but at most one,
+def grad_item_kinds(la: int, lb: int):
+    """Channel items of a bra class by kind: the (ab, p') pairs, p' = (t, u, v)
+    of order <= la + lb + 2, with t_i <= a_i + b_i on all axes but at most one,
     which may exceed it by 1 or 2 (every other pair has zero weight in all
-    8 channels, the one-dimensional E^{ij}_t vanishing for t > i + j)."""
-    n = 0
+    8 channels, the one-dimensional E^{ij}_t vanishing for t > i + j).
+    Returns (within on every axis, above by 1 on one axis, above by 2)."""
+    n = [0, 0, 0]
     for a in carts(la):
         for b in carts(lb):
             for N in range(la + lb + 3):
@@ -178,8 +179,13 @@ def grad_items(la: int, lb: int) -> int:
                     for u in range(N - t, -1, -1):
                         over = [h - a[i] - b[i] for i, h in enumerate((t, u, N - t - u))]
                         if max(over) <= 2 and sum(1 for e in over if e > 0) <= 1:
-                            n += 1
-    return n
+                            n[max(0, max(over))] += 1
+    return tuple(n)
+
+
+def grad_items(la: int, lb: int) -> int:
+    """All channel items of a bra class (see grad_item_kinds)."""
+    return sum(grad_item_kinds(la, lb))
 
 
 def _grad_launch_flops(cls, Kbra: int, Kket: int) -> int:
@@ -187,16 +193,18 @@ def _grad_launch_flops(cls, Kbra: int, Kket: int) -> int:
     per primitive quartet the auxiliary integrals to order L+2 and the ket
     transform over the raised bra Hermite range; per bra primitive the
     derived per-axis tables (3 (la+1)(lb+1)(la+lb+3) entries, 6 flops each)
-    and, per channel item, the contraction with W (2 ncd) and the 8 channel
-    terms (5 multiplies and 12 FMAs, 29 flops)."""
+    and, per channel item, the contraction with W (2 ncd) and the channel
+    terms: all 8 (5 multiplies and 12 FMAs, 29 flops), or, for an item above
+    a_i + b_i on one axis, the 4 (2 multiplies and 4 FMAs, 10 flops) or 2
+    (6 flops) with non-zero weight."""
     la, lb, lc, ld = cls
     L = la + lb + lc + ld
     nhb2 = nh(la + lb + 2)
     ncd = nc(lc) * nc(ld)
-    nit = grad_items(la, lb)
+    n0, n1, n2 = grad_item_kinds(la, lb)
     nd = (la + 1) * (lb + 1) * (la + lb + 3)
     return Kbra * Kket * (prim_quartet_flops(L + 2) + 2 * nhb2 * terms(lc, ld)) + \
-        Kbra * (18 * nd + nit * (2 * ncd + 29))
+        Kbra * (18 * nd + (n0 + n1 + n2) * 2 * ncd + 29 * n0 + 10 * n1 + 6 * n2)
 
 
 def grad_flops(cls, Kbra: int, Kket: int) -> int:
