@@ -317,15 +317,17 @@ def adjoint_variant(args, eri, dev, timed):
         ge = torch.zeros_like(db.exps)
         t_f = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o), reps=1)
         t_g = timed(lambda: eri.eri_batch_grad(cls, db, b, k, qq, Wd, gc, ge), reps=1)
+        gforms = eri.eri_last_grad_forms()
         tf += t_f
         tg += t_g
-        per["".join(map(str, cls))] = {"quartets": len(q), "fwd_ms": t_f, "grad_ms": t_g}
+        per["".join(map(str, cls))] = {"quartets": len(q), "fwd_ms": t_f, "grad_ms": t_g,
+                                       "grad_forms": "".join("XV"[f] for f in gforms)}
         nq_tot += len(q)
         Ks = basis.shell_K
         kb = (Ks[bra[q[:, 0], 0]] * Ks[bra[q[:, 0], 1]]).astype(np.int64)
         kk = (Ks[ket[q[:, 1], 0]] * Ks[ket[q[:, 1], 1]]).astype(np.int64)
         for (x, y), n in zip(*np.unique(np.stack([kb, kk], 1), axis=0, return_counts=True)):
-            gflop += n * opcount.grad_flops(cls, int(x), int(y))
+            gflop += n * opcount.grad_flops(cls, int(x), int(y), gforms)
     torch.cuda.profiler.stop()
     return {"workload": f"16-atom molecule basis, {len(batches)} classes, <= {args.adjoint_nq} "
                         "quartets per class", "quartets": nq_tot, "fwd_ms": tf, "grad_ms": tg,

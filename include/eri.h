@@ -140,6 +140,23 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
                    double* grad_centres, double* grad_exps, void* stream);
 
 /*
+ * eri_last_grad_forms -- the forms the last eri_batch_grad call ran, for its
+ * bra-channel launch and its ket-channel launch: ERI_GRAD_X (the forward ket
+ * transform over the raised bra range, X'[p'][cd], contracted with W per
+ * channel item) or ERI_GRAD_V (W contracted with the ket E products once per
+ * quartet, V_k[ab][q], then each channel item's T from V and the auxiliary
+ * integrals).  Both give the same derivatives to round-off; a cost model
+ * picks the cheaper per launch.  ERI_EINVAL before any call.
+ * eri_set_grad_forms -- restrict the planner to the forms in mask (bit
+ * ERI_GRAD_X / ERI_GRAD_V set = allowed; 0 = both).  Returns the previous
+ * mask, or ERI_EINVAL for a mask outside 0..3.  Process-wide; for testing.
+ */
+#define ERI_GRAD_X 0
+#define ERI_GRAD_V 1
+int eri_last_grad_forms(int32_t* bra_form, int32_t* ket_form);
+int eri_set_grad_forms(int32_t mask);
+
+/*
  * eri_batch3 -- 3-centre integrals
  *   (x|cd) = int int phi_x(r1) |r1 - r2|^-1 phi_c(r2) phi_d(r2) dr1 dr2
  * of one class (lx | lc ld) for a batch: x from a list of single shells

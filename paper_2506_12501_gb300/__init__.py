@@ -23,6 +23,9 @@ from .binding import (  # noqa: F401
     eri_last_form,
     eri_set_forms,
     ERI_FORM_PLAIN, ERI_FORM_HRR,
+    eri_last_grad_forms,
+    eri_set_grad_forms,
+    ERI_GRAD_X, ERI_GRAD_V,
     eri_finalize,
     eri_profile_enable,
     eri_profile_read,

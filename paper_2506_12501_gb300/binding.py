@@ -43,10 +43,12 @@ class eri_basis_t(ctypes.Structure):
 EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_error_string", "eri_finalize",
            "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc", "eri_plan_create",
            "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
-           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees", "eri_batch3", "eri_solid_harmonics", "eri_batch_sph"]
+           "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees", "eri_batch3", "eri_solid_harmonics", "eri_batch_sph",
+           "eri_last_grad_forms", "eri_set_grad_forms"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
+ERI_GRAD_X, ERI_GRAD_V = 0, 1
 PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS = 0, 1, 2, 3
 
 
@@ -69,6 +71,8 @@ def lib() -> ctypes.CDLL:
             L.eri_last_status.argtypes = [P]
             L.eri_last_form.argtypes = [P, P]
             L.eri_set_forms.argtypes = [ctypes.c_int32]
+            L.eri_last_grad_forms.argtypes = [P, P]
+            L.eri_set_grad_forms.argtypes = [ctypes.c_int32]
             L.eri_error_string.argtypes = [I]
             L.eri_error_string.restype = ctypes.c_char_p
             L.eri_finalize.argtypes = []
@@ -267,6 +271,22 @@ def eri_last_form() -> tuple:
     hrr = ctypes.c_int32()
     _check(lib().eri_last_form(ctypes.byref(sw), ctypes.byref(hrr)), "eri_last_form")
     return bool(sw.value), bool(hrr.value)
+
+
+def eri_set_grad_forms(mask: int) -> int:
+    """Restrict eri_batch_grad's forms (bit ERI_GRAD_X / ERI_GRAD_V, 0 = both); returns the previous mask."""
+    code = lib().eri_set_grad_forms(int(mask))
+    if code < 0:
+        _check(code, "eri_set_grad_forms")
+    return code
+
+
+def eri_last_grad_forms() -> tuple:
+    """(bra-channel form, ket-channel form) of the last eri_batch_grad call: ERI_GRAD_X or ERI_GRAD_V."""
+    b = ctypes.c_int32()
+    k = ctypes.c_int32()
+    _check(lib().eri_last_grad_forms(ctypes.byref(b), ctypes.byref(k)), "eri_last_grad_forms")
+    return b.value, k.value
 
 
 def eri_finalize() -> int:

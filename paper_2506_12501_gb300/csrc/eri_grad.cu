@@ -23,6 +23,7 @@
 // additions varies).
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -59,6 +60,13 @@ struct GradArgs {
     int Ws, Eks;               // shared-memory row strides of W and of the ket E products (odd)
     int TQ, KB, KK, IC;
     int Xs, XQ;                // X' strides: per Hermite function p' and per (ii, q) (odd)
+    // V form (vform = 1): V_k[ab][q] = sum_cd W_abcd E^cd_{k,q} per quartet,
+    // then T[ab][p'] = sum_k sum_q V_k[ab][q] [p'+q]_{ik} per channel item
+    int vform;
+    const int* vstart;         // [nhk+1] terms of each ket Hermite function q
+    const int* vlist;          // [Tcd] term t | cd << 16, grouped by q
+    int Vs;                    // per-quartet stride of V (odd)
+    int o_V, o_pq;
     int o_q, o_W, o_Pb, o_Pk, o_Ek, o_D, o_R, o_X, o_ch;
     int64_t ntiles;
 };
@@ -181,6 +189,11 @@ static const ItemTable* get_items(cudaStream_t s, int* err)
 // Small integers as doubles (the factors a_i of the lowering terms).
 __constant__ double c_int_d[8] = {0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0};
 
+// Forms of the last eri_batch_grad call's two launches (eri_last_grad_forms),
+// and the forms the planner may pick (eri_set_grad_forms): bit f allows form f.
+static int g_last_grad_form[2] = {-1, -1};
+static std::atomic<int> g_grad_form_mask{3};
+
 // Derived-table entries per axis and value: (la+1)(lb+1)(la+lb+3).
 static int derived_entries(int la, int lb) { return (la + 1) * (lb + 1) * (la + lb + 3); }
 
@@ -211,6 +224,12 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     double* sR = sm + a.o_R;
     double* sX = sm + a.o_X;
     double* sC8 = sm + a.o_ch;
+    double* sV = sm + a.o_V;
+    int16_t* s_pq = reinterpret_cast<int16_t*>(sm + a.o_pq);
+    const int Vs = a.Vs;
+    if (a.vform) {  // the p'+q table, read for every V-form term
+        for (int i = tid; i < nhb2 * nhk; i += kGT) s_pq[i] = ct.pq2b[i];
+    }
 
     // tiles from a queue: the sorted order puts the heaviest first, so the
     // CTAs that finish early take the lighter tiles of the tail
@@ -271,6 +290,34 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
             sW[(size_t)q * Ws + r] = q < nqt ? a.W[g_windex(a, s_qq[q], r / ncd, r % ncd)] : 0.0;
         }
         for (int idx = tid; idx < TQ * IC * 8; idx += kGT) sC8[idx] = 0.0;
+        if (a.vform) {
+            // ---- V: V[q][k][ab][qh] = sum over the terms t = (cd, qh) of
+            // W[q][ab][cd] E[q][t][k] (the caller's W met with the ket transform)
+            __syncthreads();
+            const int nV = TQ * KKt * nab * nhk;
+            for (int item = tid; item < nV; item += kGT) {
+                const int q = item % TQ;
+                int r = item / TQ;
+                const int qh = r % nhk;
+                r /= nhk;
+                const int ab = r % nab, k = r / nab;
+                const double* w = sW + (size_t)q * Ws + ab * ncd;
+                const double* Ek = sEk + (size_t)q * Eks + k;
+                double va = 0.0, vb = 0.0;
+                int e = __ldg(a.vstart + qh);
+                const int e1 = __ldg(a.vstart + qh + 1);
+                for (; e + 1 < e1; e += 2) {
+                    const int g0 = __ldg(a.vlist + e), g1 = __ldg(a.vlist + e + 1);
+                    va = fma(w[g0 >> 16], Ek[(g0 & 0xffff) * KK], va);
+                    vb = fma(w[g1 >> 16], Ek[(g1 & 0xffff) * KK], vb);
+                }
+                if (e < e1) {
+                    const int g0 = __ldg(a.vlist + e);
+                    va = fma(w[g0 >> 16], Ek[(g0 & 0xffff) * KK], va);
+                }
+                sV[(size_t)q * Vs + (k * nab + ab) * nhk + qh] = va + vb;
+            }
+        }
 
         const int NIt = TQ * IC * KKt;  // stage-A items of this tile (k < KKt)
         for (int i0 = 0; i0 < KBt; i0 += IC) {
@@ -346,7 +393,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
             __syncthreads();
             const int ICe = min(IC, KBt - i0);
             // ---- B': X'[ii][q][p'][cd] over the raised bra range (four chains)
-            for (int item = tid; item < TQ * ICe * nhb2 * ncd; item += kGT) {
+            for (int item = tid; item < (a.vform ? 0 : TQ * ICe * nhb2 * ncd); item += kGT) {
                 const int q = item % TQ;
                 int r = item / TQ;
                 const int p = r % nhb2;
@@ -382,7 +429,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 }
                 sX[(size_t)(ii * TQ + q) * XQ + p * Xs + cd] = (v0 + v1) + (v2 + v3);
             }
-            __syncthreads();
+            if (!a.vform) __syncthreads();
             // ---- C+D.  Each (q, ii) of the chunk is taken by a group of G
             // consecutive lanes.  The group's lanes split its channel items
             // (ab, p'), form y = T[ab][p'] = sum_cd W[q][ab][cd] X'[ii][q][p'][cd]
@@ -414,15 +461,36 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                         const double* Dq = sD + (size_t)(ii * TQ + q) * PST;
                         for (int j = s; j < nit; j += G) {
                             const int2 g = __ldg(a.items + j);
-                            const double* w = wq + (g.x & 1023) * ncd;
-                            const double* xv = xq + ((g.x >> 10) & 1023) * Xs;
                             double ya = 0.0, yb = 0.0;
-                            int cd = 0;
-                            for (; cd + 1 < ncd; cd += 2) {
-                                ya = fma(w[cd], xv[cd], ya);
-                                yb = fma(w[cd + 1], xv[cd + 1], yb);
+                            if (!a.vform) {
+                                const double* w = wq + (g.x & 1023) * ncd;
+                                const double* xv = xq + ((g.x >> 10) & 1023) * Xs;
+                                int cd = 0;
+                                for (; cd + 1 < ncd; cd += 2) {
+                                    ya = fma(w[cd], xv[cd], ya);
+                                    yb = fma(w[cd + 1], xv[cd + 1], yb);
+                                }
+                                if (cd < ncd) ya = fma(w[cd], xv[cd], ya);
+                            } else {
+                                // T = sum_qh sum_k V[q][k][ab][qh] R_{ii,k}[p'+qh]
+                                const double* vq = sV + (size_t)q * Vs + (g.x & 1023) * nhk;
+                                const int16_t* pqr = s_pq + ((g.x >> 10) & 1023) * nhk;
+                                const double* Rq = sR + ii * TQ + q;
+                                const int VK = nab * nhk;
+                                int qh = 0;
+                                for (; qh + 1 < nhk; qh += 2) {
+                                    const double* Ra = Rq + (size_t)pqr[qh] * NIs;
+                                    const double* Rb = Rq + (size_t)pqr[qh + 1] * NIs;
+                                    for (int k = 0; k < KKt; ++k) {
+                                        ya = fma(vq[k * VK + qh], Ra[k * ICT], ya);
+                                        yb = fma(vq[k * VK + qh + 1], Rb[k * ICT], yb);
+                                    }
+                                }
+                                if (qh < nhk) {
+                                    const double* Ra = Rq + (size_t)pqr[qh] * NIs;
+                                    for (int k = 0; k < KKt; ++k) ya = fma(vq[k * VK + qh], Ra[k * ICT], ya);
+                                }
                             }
-                            if (cd < ncd) ya = fma(w[cd], xv[cd], ya);
                             const double y = ya + yb;
                             const double* Dx = Dq + (g.y & 1023);
                             const double* Dy = Dq + 5 * ND + ((g.y >> 10) & 1023);
@@ -536,7 +604,8 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     }
 }
 
-static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, GradArgs* a, size_t* bytes)
+static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int vform, GradArgs* a,
+                        size_t* bytes)
 {
     size_t off = 0;
     auto take = [&](size_t nd) {
@@ -557,24 +626,25 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, G
     a->o_R = take((size_t)ct.nhl2 * ((TQ * IC * KK) | 1));
     a->Xs = ct.ncd | 1;
     a->XQ = (ct.nhb2 * a->Xs) | 1;
-    a->o_X = take((size_t)a->XQ * TQ * IC);
+    a->o_X = take(vform ? 0 : (size_t)a->XQ * TQ * IC);
     a->o_ch = take((size_t)TQ * IC * 8);
+    a->Vs = (KK * ct.nab * ct.nhk) | 1;
+    a->o_V = take(vform ? (size_t)TQ * a->Vs : 0);
+    a->o_pq = take(vform ? ((size_t)ct.nhb2 * ct.nhk * 2 + 7) / 8 : 0);
     *bytes = off * 8;
     a->TQ = TQ;
     a->IC = IC;
+    a->vform = vform;
     return *bytes <= (size_t)max_smem_optin();
 }
 
-// Tile shape (TQ quartets, IC bra primitives per stage pass): the feasible
-// shape with the lowest modelled time per quartet.  Each stage pass costs its
-// rounds of kGT items times the FP64 work of one item, plus a barrier; a
-// tile makes ceil(KB / IC) passes of four stages.  Shapes that leave room for
-// two CTAs per SM (so one CTA's barriers overlap the other's work) are
-// preferred whenever one exists.
-// Tile shape (TQ quartets, IC bra primitives per stage pass): the feasible
-// shape with the lowest modelled time per quartet.  Each stage pass costs its
-// rounds of kGT items times the FP64 work of one item, plus a barrier; a
-// tile makes ceil(KB / IC) passes of four stages.  Shapes that leave room for
+// Form and tile shape (TQ quartets, IC bra primitives per stage pass): the
+// feasible pair with the lowest modelled time per quartet.  Each stage pass
+// costs its rounds of kGT items times the FP64 work of one item, plus a
+// barrier; a tile makes ceil(KB / IC) passes.  The X form's pass forms X'
+// over every (p', cd) and contracts it with W per channel item; the V form
+// contracts W with the ket E products once per tile and forms each channel
+// item's T from V and the auxiliary integrals.  Shapes that leave room for
 // two CTAs per SM (so one CTA's barriers overlap the other's work) are
 // preferred whenever one exists.
 static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int64_t nq, size_t limit, GradArgs* a,
@@ -597,19 +667,34 @@ static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int
     GradArgs pick{};
     size_t pick_bytes = 0;
     const int ND = derived_entries(ct.la, ct.lb);
+    for (int vform = 0; vform < 2; ++vform)
     for (int TQ = 32; TQ >= 1; TQ /= 2) {
+        if (!(g_grad_form_mask.load() >> vform & 1)) break;
         if (TQ > 1 && TQ > nq) continue;
         for (int IC = KB; IC >= 1; IC = IC == 1 ? 0 : (IC + 1) / 2) {
             GradArgs t = *a;
             size_t b = 0;
-            if (!grad_layout(ct, KB, KK, TQ, IC, &t, &b) || b > limit) continue;
+            if (!grad_layout(ct, KB, KK, TQ, IC, vform, &t, &b) || b > limit) continue;
             auto rounds = [](double n) { return std::ceil(n / kGT); };
             const double kBarrier = 60.0;
-            const double pass = rounds((double)TQ * IC * KK) * (3.0 * ct.nhl2 + 60.0) +
-                                rounds((double)TQ * IC * 3 * ND) * 14.0 +
-                                rounds((double)TQ * IC * ct.nhb2 * ct.ncd) * (2.0 * KK * ct.Tcd / ct.ncd + 8.0) +
-                                rounds((double)TQ * IC * nit) * (2.0 * ct.ncd + 40.0) + 4.0 * kBarrier;
-            const double cost = std::ceil((double)KB / IC) * pass / TQ;
+            const double common = rounds((double)TQ * IC * KK) * (3.0 * ct.nhl2 + 60.0) +
+                                  rounds((double)TQ * IC * 3 * ND) * 14.0;
+            double cost;
+            // a term's index lookup and scattered load cost about as much as
+            // its FMAs over the ket primitives: weight 2 KK + 1.5 (X's ket
+            // transform) and 2 KK + 2.5 (V's T, one p'+q lookup per term)
+            if (!vform) {
+                const double pass =
+                    common + rounds((double)TQ * IC * ct.nhb2 * ct.ncd) * ((2.0 * KK + 1.5) * ct.Tcd / ct.ncd + 8.0) +
+                    rounds((double)TQ * IC * nit) * (2.0 * ct.ncd + 40.0) + 4.0 * kBarrier;
+                cost = std::ceil((double)KB / IC) * pass / TQ;
+            } else {
+                const double pass =
+                    common + rounds((double)TQ * IC * nit) * ((2.0 * KK + 2.5) * ct.nhk + 40.0) + 3.0 * kBarrier;
+                const double vstage =
+                    rounds((double)TQ * KK * ct.nab * ct.nhk) * (3.5 * ct.Tcd / ct.nhk + 8.0) + kBarrier;
+                cost = (vstage + std::ceil((double)KB / IC) * pass) / TQ;
+            }
             if (best < 0 || cost < best) {
                 best = cost;
                 pick = t;
@@ -621,6 +706,55 @@ static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int
     *a = pick;
     *bytes = pick_bytes;
     return true;
+}
+
+// The ket terms of a class grouped by their Hermite function q (for the V
+// form): vstart[q]..vstart[q+1] index vlist, whose entries are t | cd << 16.
+// Built from the class tables' own term list, once per class table.
+struct VList {
+    int* vstart = nullptr;
+    int* vlist = nullptr;
+};
+
+static const VList* get_vlist(const ClassTables& ct, cudaStream_t st, int* err)
+{
+    static std::map<std::pair<int, const void*>, VList> tabs;
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(dev, (const void*)ct.ket_q);
+    auto it = tabs.find(key);
+    if (it != tabs.end()) return &it->second;
+    std::vector<int> start(ct.ncd + 1);
+    std::vector<int16_t> q(ct.Tcd);
+    if (cudaMemcpyAsync(start.data(), ct.ket_start, sizeof(int) * (ct.ncd + 1), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(q.data(), ct.ket_q, sizeof(int16_t) * ct.Tcd, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        *err = ERI_ECUDA;
+        return nullptr;
+    }
+    std::vector<int> vstart(ct.nhk + 1, 0), vlist(ct.Tcd);
+    for (int t = 0; t < ct.Tcd; ++t) ++vstart[q[t] + 1];
+    for (int h = 0; h < ct.nhk; ++h) vstart[h + 1] += vstart[h];
+    std::vector<int> fill(vstart.begin(), vstart.end() - 1);
+    for (int cd = 0; cd < ct.ncd; ++cd)
+        for (int t = start[cd]; t < start[cd + 1]; ++t) vlist[fill[q[t]]++] = t | (cd << 16);
+    VList v;
+    if (cudaMalloc(&v.vstart, sizeof(int) * (ct.nhk + 1)) != cudaSuccess ||
+        cudaMalloc(&v.vlist, sizeof(int) * std::max(ct.Tcd, 1)) != cudaSuccess) {
+        *err = ERI_ENOMEM;
+        return nullptr;
+    }
+    if (cudaMemcpyAsync(v.vstart, vstart.data(), sizeof(int) * (ct.nhk + 1), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(v.vlist, vlist.data(), sizeof(int) * ct.Tcd, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        *err = ERI_ECUDA;
+        return nullptr;
+    }
+    return &(tabs[key] = v);
 }
 
 // The quartet order and the two tile queues, shared by the two launches.
@@ -671,8 +805,13 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     if (!items) return err;
     a.items = items->list[ct->la][ct->lb];
     a.nit = items->n[ct->la][ct->lb];
+    const VList* vl = get_vlist(*ct, st, &err);
+    if (!vl) return err;
+    a.vstart = vl->vstart;
+    a.vlist = vl->vlist;
     size_t bytes = 0;
     if (!grad_plan(*ct, KB, KK, a.nit, a.nq, &a, &bytes)) return ERI_EINVAL;
+    g_last_grad_form[swap] = a.vform;
     a.ntiles = (a.nq + a.TQ - 1) / a.TQ;
     if (!ord->queue) {  // first launch: order (sorted if the batch mixes degrees); the second reuses it
         err = build_order(quartets, a.nq, nbra_o, pb.kp, pk.kp, KB, KK, swap, mixed, st, &ord->order, &ord->queue);
@@ -709,9 +848,25 @@ extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const i
     cudaStream_t st = (cudaStream_t)stream;
     // channels of the bra (a, b), then of the ket (c, d) with the sides exchanged
     GradOrder order;
+    g_last_grad_form[0] = g_last_grad_form[1] = -1;
     err = launch_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, grad_centres, grad_exps, 0, nbra,
                       nket, &order, st);
     if (err != ERI_OK) return err;
     return launch_grad(eri_class_t{cls.lc, cls.ld, cls.la, cls.lb}, basis, ket_pairs, nket, bra_pairs, nbra, quartets,
                        nq, W, grad_centres, grad_exps, 1, nbra, nket, &order, st);
+}
+
+extern "C" int eri_last_grad_forms(int32_t* bra_form, int32_t* ket_form)
+{
+    if (!bra_form || !ket_form) return ERI_EINVAL;
+    if (g_last_grad_form[0] < 0 || g_last_grad_form[1] < 0) return ERI_EINVAL;
+    *bra_form = g_last_grad_form[0];
+    *ket_form = g_last_grad_form[1];
+    return ERI_OK;
+}
+
+extern "C" int eri_set_grad_forms(int32_t mask)
+{
+    if (mask < 0 || mask > 3) return ERI_EINVAL;
+    return g_grad_form_mask.exchange(mask ? mask : 3);
 }

@@ -188,27 +188,37 @@ def grad_items(la: int, lb: int) -> int:
     return sum(grad_item_kinds(la, lb))
 
 
-def _grad_launch_flops(cls, Kbra: int, Kket: int) -> int:
+def _grad_launch_flops(cls, Kbra: int, Kket: int, vform: int = 0) -> int:
     """FP64 flops of one adjoint launch (the channels of the kernel's bra):
-    per primitive quartet the auxiliary integrals to order L+2 and the ket
-    transform over the raised bra Hermite range; per bra primitive the
-    derived per-axis tables (3 (la+1)(lb+1)(la+lb+3) entries, 6 flops each)
-    and, per channel item, the contraction with W (2 ncd) and the channel
-    terms: all 8 (5 multiplies and 12 FMAs, 29 flops), or, for an item above
-    a_i + b_i on one axis, the 4 (2 multiplies and 4 FMAs, 10 flops) or 2
-    (6 flops) with non-zero weight."""
+    per primitive quartet the auxiliary integrals to order L+2; per bra
+    primitive the derived per-axis tables (3 (la+1)(lb+1)(la+lb+3) entries,
+    6 flops each) and, per channel item, T[ab][p'] and the channel terms: all
+    8 (5 multiplies and 12 FMAs, 29 flops), or, for an item above a_i + b_i on
+    one axis, the 4 (2 multiplies and 4 FMAs, 10 flops) or 2 (6 flops) with
+    non-zero weight.  T comes from
+      the X form (vform 0): per primitive quartet the ket transform over the
+        raised bra Hermite range, then 2 ncd per channel item;
+      the V form (vform 1): per quartet and ket primitive V[ab][q] (2 nab Tcd),
+        then 2 Nh(lc+ld) per channel item and ket primitive."""
     la, lb, lc, ld = cls
     L = la + lb + lc + ld
     nhb2 = nh(la + lb + 2)
     ncd = nc(lc) * nc(ld)
+    nab = nc(la) * nc(lb)
     n0, n1, n2 = grad_item_kinds(la, lb)
+    nit = n0 + n1 + n2
     nd = (la + 1) * (lb + 1) * (la + lb + 3)
+    channels = 18 * nd + 29 * n0 + 10 * n1 + 6 * n2
+    if vform:
+        return Kbra * Kket * prim_quartet_flops(L + 2) + Kket * 2 * nab * terms(lc, ld) + \
+            Kbra * (channels + nit * 2 * nh(lc + ld) * Kket)
     return Kbra * Kket * (prim_quartet_flops(L + 2) + 2 * nhb2 * terms(lc, ld)) + \
-        Kbra * (18 * nd + (n0 + n1 + n2) * 2 * ncd + 29 * n0 + 10 * n1 + 6 * n2)
+        Kbra * (channels + nit * 2 * ncd)
 
 
-def grad_flops(cls, Kbra: int, Kket: int) -> int:
+def grad_flops(cls, Kbra: int, Kket: int, forms=(0, 0)) -> int:
     """FP64 flops of the adjoint of one quartet: the bra channels, then the
-    ket channels in a second launch with the sides exchanged."""
+    ket channels in a second launch with the sides exchanged, each in its
+    form (eri_last_grad_forms)."""
     la, lb, lc, ld = cls
-    return _grad_launch_flops(cls, Kbra, Kket) + _grad_launch_flops((lc, ld, la, lb), Kket, Kbra)
+    return _grad_launch_flops(cls, Kbra, Kket, forms[0]) + _grad_launch_flops((lc, ld, la, lb), Kket, Kbra, forms[1])

@@ -38,7 +38,9 @@ def gpu_grad(cls, basis, bra, ket, q, W):
 def test_grad_against_oracle(cuda, cls, K):
     """Centre and exponent derivatives of sum W (ab|cd) for random W, K = 2 or
     3 per shell (an odd K leaves a partial chunk of bra primitives), against
-    the oracle's shifted-monomial derivative."""
+    the oracle's shifted-monomial derivative, in each of the two forms
+    (X: ket transform over the raised bra range, then W; V: W met with the
+    ket E products first) forced in turn."""
     if K == 3 and sum(cls) > 6:
         pytest.skip("oracle time")
     basis, pools = synth.class_sweep_pools(seed=3, lmax=max(2, max(cls)), pool=24, K=K, cube=5.0)
@@ -46,16 +48,23 @@ def test_grad_against_oracle(cuda, cls, K):
     bra, ket, q = synth.class_sweep_batch(pools, cls, seed=4, npairs=20, nq=nq)
     n = eri.out_len(cls, bra.shape[0], ket.shape[0], nq)
     W = np.random.default_rng(8).uniform(-1, 1, n)
-    gc, ge = gpu_grad(cls, basis, bra, ket, q, W)
     # oracle W layout: per quartet [ab][cd] blocks
     Wq = W.reshape(-1, nq).T.reshape(-1)
     rc, re = oracle.eri_grad_quartets(basis, synth.quartet_shells(bra, ket, q), Wq, prec="d", threads=THREADS)
-    grad_close(gc, rc, f"centres {cls}")
-    grad_close(ge, re, f"exponents {cls}")
-    assert abs(gc.sum(axis=0)).max() < 1e-10 * max(1.0, abs(gc).max())  # translation invariance
+    try:
+        for form in (eri.ERI_GRAD_X, eri.ERI_GRAD_V):
+            eri.eri_set_grad_forms(1 << form)
+            gc, ge = gpu_grad(cls, basis, bra, ket, q, W)
+            assert eri.eri_last_grad_forms() == (form, form)
+            grad_close(gc, rc, f"centres {cls} form {form}")
+            grad_close(ge, re, f"exponents {cls} form {form}")
+            assert abs(gc.sum(axis=0)).max() < 1e-10 * max(1.0, abs(gc).max())  # translation invariance
+    finally:
+        eri.eri_set_grad_forms(0)
 
 
-def test_grad_mixed_K_and_product_form(cuda):
+@pytest.mark.parametrize("form", [0, 1])
+def test_grad_mixed_K_and_product_form(cuda, form):
     basis = synth.molecule_basis(natom=5, radius=3.0, seed=2)
     pairs = synth.unique_pairs(basis)
     sel = pairs[(basis.shell_l[pairs[:, 0]] == 1) & (basis.shell_l[pairs[:, 1]] == 0)][:9]
@@ -67,7 +76,12 @@ def test_grad_mixed_K_and_product_form(cuda):
     b, k, _ = to_device(sel, ket)
     gc = torch.zeros_like(db.centres)
     ge = torch.zeros_like(db.exps)
-    eri.eri_batch_grad(cls, db, b, k, None, torch.as_tensor(W, device="cuda"), gc, ge)
+    try:
+        eri.eri_set_grad_forms(1 << form)
+        eri.eri_batch_grad(cls, db, b, k, None, torch.as_tensor(W, device="cuda"), gc, ge)
+        assert eri.eri_last_grad_forms() == (form, form)
+    finally:
+        eri.eri_set_grad_forms(0)
     q = np.array([(i, j) for j in range(ket.shape[0]) for i in range(sel.shape[0])], dtype=np.int64)
     # product layout [kl][cd][ab][ij] -> per quartet [ab][cd]
     Wq = W.reshape(ket.shape[0], 1, 3, sel.shape[0]).transpose(0, 3, 2, 1).reshape(-1)
