@@ -170,28 +170,40 @@ struct PairArgs {
 };
 
 constexpr int kEax = (kLmax + 3) * (kLmax + 3) * (2 * kLmax + 5);  // per-axis E table bound (adjoint shifts)
+constexpr int kEfw = (kLmax + 1) * (kLmax + 1) * (2 * kLmax + 1);  // without the shifts (also the HRR form's)
 
-__global__ void pair_kernel(PairArgs a)
+// RAISED: the adjoint's tables (a.ax != NULL): the per-axis E tables with
+// both indices raised by 2, one thread per (slot, axis).  The adjoint reads
+// no E products of that side, so none are formed.  Otherwise one thread per
+// slot forms the three tables and the E products of the class's terms.
+template <bool RAISED>
+__global__ void pair_kernel_t(PairArgs a)
 {
-    const int64_t total = a.npairs * a.KS;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    constexpr int NX = RAISED ? 1 : 3;  // axes per thread
+    const int64_t total = a.npairs * a.KS * (RAISED ? 3 : 1);
+    for (int64_t gg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gg < total;
+         gg += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = RAISED ? gg / 3 : gg;       // the slot
+        const int x0 = RAISED ? (int)(gg - g * 3) : 0;  // its first axis
         const int64_t j = g / a.KS;
         const int s = (int)(g - j * a.KS);
         // s2 = -1: the unit function (exponent 0, coefficient 1) of a 3-centre
         // bra; its centre is immaterial and taken as the first shell's
         const int s1 = a.pairs[2 * j], s2 = a.pairs[2 * j + 1];
         const int K1 = a.shell_K[s1], K2 = s2 < 0 ? 1 : a.shell_K[s2];
-        if (s == 0) a.kprim[j] = K1 * K2;
+        if (s == 0 && x0 == 0) a.kprim[j] = K1 * K2;
         if (s >= K1 * K2) {  // padding slot: finite zeros, never contributes
-            for (int t = 0; t < a.T; ++t) a.E[((size_t)j * a.T + t) * a.KS + s] = 0.0;
+            if (RAISED) {
+                for (int q = 0; q < a.eax; ++q) a.ax[((size_t)g * 3 + x0) * a.eax + q] = 0.0;
+                if (x0 != 0) continue;
+                a.zz[2 * g] = a.zz[2 * g + 1] = 1.0;
+            } else {
+                for (int t = 0; t < a.T; ++t) a.E[((size_t)j * a.T + t) * a.KS + s] = 0.0;
+            }
             double* o = a.ps + (size_t)g * PS_N;
             o[PS_P] = 1.0;
             o[PS_PX] = o[PS_PY] = o[PS_PZ] = 0.0;
             o[PS_INVP] = 1.0;
-            if (a.ax) {
-                for (int q = 0; q < 3 * a.eax; ++q) a.ax[(size_t)g * 3 * a.eax + q] = 0.0;
-                a.zz[2 * g] = a.zz[2 * g + 1] = 1.0;
-            }
             continue;
         }
         const int i1 = s / K2, i2 = s - i1 * K2;
@@ -214,14 +226,15 @@ __global__ void pair_kernel(PairArgs a)
         // K_AB c_1 c_2 carried by the x-axis bootstrap E_00^0 (Eq. E2-000),
         // 1 on y and z: the products E^x E^y E^z are unchanged.
         const double e00x = a.coefs[p1] * c2 * exp(-z1 * z2 * invp * AB2);
-        const int ext = a.ax ? 2 : 0;
+        const int ext = RAISED ? 2 : 0;
         // largest raised indices: the adjoint raises both by 2; the
         // horizontal-recursion form needs E_{i,0} for i <= l1 + l2
         const int m1 = a.hrr ? a.l1 + a.l2 : a.l1 + ext, m2 = a.hrr ? 0 : a.l2 + ext;
         const int L12 = a.l1 + a.l2, n2 = m2 + 1, nt = m1 + m2 + 1;
-        double E[3][kEax];
-        for (int x = 0; x < 3; ++x) {
-            double* Ex = E[x];
+        double E[NX][RAISED ? kEax : kEfw];
+        for (int xi = 0; xi < NX; ++xi) {
+            const int x = x0 + xi;
+            double* Ex = E[xi];
             for (int q = 0; q < (m1 + 1) * n2 * nt; ++q) Ex[q] = 0.0;
             Ex[0] = x == 0 ? e00x : 1.0;
             // raise the first index at j = 0 (Eq. E2rr1)
@@ -245,31 +258,31 @@ __global__ void pair_kernel(PairArgs a)
                         Ex[(i * n2 + jj + 1) * nt + t] = v;
                     }
         }
-        double* Eout = a.E + (size_t)j * a.T * a.KS + s;  // term t at Eout[t * KS]
-        const int ntc = L12 + 1, n2c = a.hrr ? 1 : a.l2 + 1;  // dims the class-table indices use
-        for (int t = 0; t < a.T; ++t) {
-            int idx[3], lq = 0;
-            for (int x = 0; x < 3; ++x) {
-                const int f = a.fac[3 * t + x];
-                const int tt = f % ntc, bb = (f / ntc) % n2c, aa = f / (ntc * n2c);
-                idx[x] = (aa * n2 + bb) * nt + tt;
-                lq += tt;
-            }
-            double v = E[0][idx[0]] * E[1][idx[1]] * E[2][idx[2]];
-            if (a.scale) v *= a.scale[t];
-            if (a.ket && (lq & 1)) v = -v;
-            if (a.split)
-                reinterpret_cast<float2*>(Eout)[(size_t)t * a.KS] = split_f64(v);
-            else
-                Eout[(size_t)t * a.KS] = v;
-        }
-        if (a.ax) {
-            for (int x = 0; x < 3; ++x) {
-                double* o = a.ax + ((size_t)g * 3 + x) * a.eax;
-                for (int q = 0; q < (m1 + 1) * n2 * nt; ++q) o[q] = E[x][q];
-            }
+        if (RAISED) {
+            double* o = a.ax + ((size_t)g * 3 + x0) * a.eax;
+            for (int q = 0; q < (m1 + 1) * n2 * nt; ++q) o[q] = E[0][q];
+            if (x0 != 0) continue;
             a.zz[2 * g] = z1;
             a.zz[2 * g + 1] = z2;
+        } else {
+            double* Eout = a.E + (size_t)j * a.T * a.KS + s;  // term t at Eout[t * KS]
+            const int ntc = L12 + 1, n2c = a.hrr ? 1 : a.l2 + 1;  // dims the class-table indices use
+            for (int t = 0; t < a.T; ++t) {
+                int idx[3], lq = 0;
+                for (int x = 0; x < 3; ++x) {
+                    const int f = a.fac[3 * t + x];
+                    const int tt = f % ntc, bb = (f / ntc) % n2c, aa = f / (ntc * n2c);
+                    idx[x] = (aa * n2 + bb) * nt + tt;
+                    lq += tt;
+                }
+                double v = E[0][idx[0]] * E[NX > 1 ? 1 : 0][idx[1]] * E[NX > 2 ? 2 : 0][idx[2]];
+                if (a.scale) v *= a.scale[t];
+                if (a.ket && (lq & 1)) v = -v;
+                if (a.split)
+                    reinterpret_cast<float2*>(Eout)[(size_t)t * a.KS] = split_f64(v);
+                else
+                    Eout[(size_t)t * a.KS] = v;
+            }
         }
         double* o = a.ps + (size_t)g * PS_N;
         o[PS_P] = p;
@@ -278,6 +291,16 @@ __global__ void pair_kernel(PairArgs a)
         o[PS_PZ] = P[2];
         o[PS_INVP] = a.ket ? invp : kTwoPi52 * invp;
     }
+}
+
+// grid: blocks of 128 threads for one thread per slot; the raised kernel
+// takes three per slot
+static void launch_pair(const PairArgs& p, int grid, cudaStream_t st)
+{
+    if (p.ax)
+        pair_kernel_t<true><<<(int)std::min<int64_t>(3LL * grid, 24LL * sm_count()), 128, 0, st>>>(p);
+    else
+        pair_kernel_t<false><<<grid, 128, 0, st>>>(p);
 }
 
 static const auto fwd_kernel = fwd_kernel_t<false>;
@@ -635,17 +658,17 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
     const int eaxb = (cls.la + 3) * (cls.lb + 3) * (cls.la + cls.lb + 5);
     const int eaxk = (cls.lc + 3) * (cls.ld + 3) * (cls.lc + cls.ld + 5);
     const size_t nb_ax = grad ? align_up(sizeof(double) * nbra * *KB * 3 * eaxb) : 0;
-    const size_t nk_ax = grad ? align_up(sizeof(double) * nket * *KK * 3 * eaxk) : 0;
+    const size_t nk_ax = 0;  // the adjoint reads the raised tables of its (kernel) bra side only
     const size_t nb_z = grad ? align_up(sizeof(double) * nbra * *KB * 2) : 0;
-    const size_t nk_z = grad ? align_up(sizeof(double) * nket * *KK * 2) : 0;
+    const size_t nk_z = 0;
     uint8_t* ws = (uint8_t*)workspace(nb_ps + nb_E + nk_ps + nk_E + nb_k + nk_k + nb_ax + nk_ax + nb_z + nk_z, &err);
     if (!ws) return err;
     {
         uint8_t* g0 = ws + nb_ps + nb_E + nk_ps + nk_E + nb_k + nk_k;
         pb->ax = grad ? (double*)g0 : nullptr;
-        pk->ax = grad ? (double*)(g0 + nb_ax) : nullptr;
+        pk->ax = nullptr;
         pb->zz = grad ? (double*)(g0 + nb_ax + nk_ax) : nullptr;
-        pk->zz = grad ? (double*)(g0 + nb_ax + nk_ax + nb_z) : nullptr;
+        pk->zz = nullptr;
         pb->eax = eaxb;
         pk->eax = eaxk;
     }
@@ -684,7 +707,7 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         const int64_t tot = p.npairs * p.KS;
         const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
         ProfScope ps(PROF_PAIR, st);
-        pair_kernel<<<std::max(g, 1), 128, 0, st>>>(p);
+        launch_pair(p, std::max(g, 1), st);
         if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
     }
     return ERI_OK;
@@ -1208,7 +1231,7 @@ int fwd_batch_on(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, 
         const int64_t tot = p.npairs * p.KS;
         const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
         count_launch();
-        pair_kernel<<<std::max(g, 1), 128, 0, st>>>(p);
+        launch_pair(p, std::max(g, 1), st);
         if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
     }
     const int64_t nqq = quartets ? nq : nbra * nket;
@@ -1278,7 +1301,7 @@ int build_pair_tables_on(const eri_basis_t* basis, const int32_t* d_pairs, int64
     const int64_t tot = npairs * KS;
     const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
     count_launch();
-    pair_kernel<<<std::max(g, 1), 128, 0, st>>>(p);
+    launch_pair(p, std::max(g, 1), st);
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_ECUDA;
 }
 
