@@ -555,7 +555,8 @@ def run_library(args):
             if it > 0:
                 e_ms.append(a0.elapsed_time(a1))
         e2e = {"value": world * nq_step / (statistics.median(e_ms) / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": len(e_ms)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": len(e_ms),
+               "step_ms": [round(x, 2) for x in e_ms]}
 
     variants = None
     if rank == 0 and not args.no_variants and (only is None or args.variants):

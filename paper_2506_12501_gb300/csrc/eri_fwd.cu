@@ -61,6 +61,12 @@ struct PrepassArgs {
     int* kmin;   // optional [2]: the smallest primitive-pair count K1 K2 over bra (ket) pairs
 };
 
+// Copies the prepass results to mapped host memory.
+__global__ void info_to_host_kernel(const int* __restrict__ src, int n, int* dst)
+{
+    if ((int)threadIdx.x < n) dst[threadIdx.x] = src[threadIdx.x];
+}
+
 // (2|A-B|)^l2 max over primitive pairs of exp(-z1 z2 / (z1 + z2) |A-B|^2)
 __device__ float pair_recursion_risk(const PrepassArgs& a, int s1, int s2, int l2)
 {
@@ -564,7 +570,19 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         prepass_kernel<<<std::max(grid, 1), 256, 0, st>>>(pa);
     }
     if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
-    if (cudaMemcpyAsync(hinfo, dinfo, 9 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return ERI_ECUDA;
+    // the info goes to the pinned host buffer through its mapped device
+    // address, written by a kernel: a device-to-host copy would queue behind
+    // any large read-back the caller has put on that copy engine
+    int32_t* hmapped = nullptr;
+    if (cudaHostGetDevicePointer((void**)&hmapped, hinfo, 0) == cudaSuccess && hmapped) {
+        count_launch();
+        info_to_host_kernel<<<1, 32, 0, st>>>(dinfo, 9, hmapped);
+        if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
+    } else {
+        cudaGetLastError();
+        if (cudaMemcpyAsync(hinfo, dinfo, 9 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return ERI_ECUDA;
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) return ERI_ECUDA;
     if (hinfo[4] != 0) return dev_err_to_code(hinfo[4]);
     for (int c = 0; c < 4; ++c) kmax[c] = hinfo[c];
