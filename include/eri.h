@@ -112,6 +112,11 @@ int eri_boys(int mmax, const double* T, int64_t n, double* F, void* stream);
  * against `cls` (ERI_ECLASS); its verdict and the largest contraction degree
  * per centre are read back, so each call synchronises `stream` once.  On an
  * error `out` is left untouched.
+ * Shared memory bounds the primitive-pair counts: a tile holds the
+ * auxiliary integrals of every ket primitive pair of one quartet.  With the
+ * same K on all four shells, K = 8 fits for L = la+lb+lc+ld <= 10, K = 7 for
+ * L = 11 and K = 6 for L = 12 (the cheaper side order is taken); beyond,
+ * no tile fits and the call returns ERI_EINVAL.
  * nbra == 0, nket == 0 or nq == 0 is a no-op.
  */
 int eri_batch(eri_class_t cls, const eri_basis_t* basis,
@@ -131,6 +136,12 @@ int eri_batch(eri_class_t cls, const eri_basis_t* basis,
  *   grad_centres: [natom][3], ACCUMULATED (+=);
  *   grad_exps:    [nprim],    ACCUMULATED (+=).
  * Either gradient pointer may be NULL to skip that part.
+ * Its tiles hold the auxiliary integrals to order L+2 of every ket primitive
+ * pair of a quartet, which bounds the contraction degrees more tightly than
+ * the forward's: with the same K on all four shells, K = 8 fits for L <= 4,
+ * K = 5 for L = 5, K = 3 for L = 6..9, K = 2 for L = 10 and K = 1 for
+ * L = 11, 12.  Uncontracted d and f shells with s and p shells of any K
+ * <= ERI_KMAX always fit.  Beyond, the call returns ERI_EINVAL.
  */
 int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
                    const int32_t* bra_pairs, int64_t nbra,
@@ -150,6 +161,9 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
  * eri_set_grad_forms -- restrict the planner to the forms in mask (bit
  * ERI_GRAD_X / ERI_GRAD_V set = allowed; 0 = both).  Returns the previous
  * mask, or ERI_EINVAL for a mask outside 0..3.  Process-wide; for testing.
+ * A launch for which no tile of an allowed form fits in shared memory makes
+ * eri_batch_grad return ERI_EINVAL (with both forms allowed, the X form's
+ * smallest tile always fits for l <= ERI_LMAX and K <= ERI_KMAX).
  */
 #define ERI_GRAD_X 0
 #define ERI_GRAD_V 1
