@@ -6,21 +6,25 @@
 //   d/dzeta_a phi_a = -(phi_{a+2x} + phi_{a+2y} + phi_{a+2z}),
 // so every derivative of the bra product phi_a phi_b expands in Hermite
 // functions (Eq. cart2herm-2) with coefficients G^ch_{ab,p'} built from the
-// E tables with raised indices (Hermite order up to l_bra + 2).  The kernel
-// computes, per tile of quartets and per bra primitive i,
-//   X'_i[p'][cd] = sum_k sum_q E^cd_{k,q} (-1)^{l_q} [p'+q]^(0)_{ik}
-//                  (the forward ket transform, over the raised bra range),
-//   T_i[ab][p']  = sum_cd W_abcd X'_i[p'][cd],
+// E tables with raised indices (Hermite order up to l_bra + 2).  Per tile of
+// quartets and per bra primitive i the kernel forms
+//   T_i[ab][p']  = sum_cd W_abcd sum_k sum_q E^cd_{k,q} (-1)^{l_q} [p'+q]^(0)_{ik}
 //   dE/dch      += sum_ab sum_p' G^ch_{i;ab,p'} T_i[ab][p']
-// for the 8 channels of the bra (3 per centre, 2 exponents).  G^ch is a
-// product of one-dimensional tables, so T is formed only for the (ab, p')
-// where some channel's G is non-zero, and each T value is folded into the
-// channels as soon as it is formed.  The ket's
+// for the 8 channels of the bra (3 per centre, 2 exponents), in one of two
+// orders chosen per launch by a cost model:
+//   X form: X'_i[p'][cd] = sum_k sum_q E^cd_{k,q} [p'+q]_ik (the forward ket
+//           transform over the raised bra range), then T = sum_cd W X';
+//   V form: V_k[ab][q] = sum_cd W_abcd E^cd_{k,q} once per quartet, then
+//           T = sum_k sum_q V_k[ab][q] [p'+q]_ik.
+// G^ch is a product of one-dimensional tables, so T is formed only for the
+// channel items, the (ab, p') where some channel's G is non-zero, and each T
+// value is folded at once into the channels its item can reach.  The ket's
 // channels come from a second launch with the sides exchanged, since
 // (ab|cd) = (cd|ab).  The auxiliary integrals [r]^(0) (order up to L+2) are
-// recomputed, not stored.  Channel sums are reduced per quartet in shared
-// memory and added atomically to the gradients (only the order of the
-// additions varies).
+// recomputed, not stored.  A batch that mixes contraction degrees runs its
+// quartets sorted by primitive-pair counts; CTAs take tiles from a queue.
+// Channel sums are reduced per (quartet, bra primitive) by lane groups and
+// added atomically to the gradients (only the order of the additions varies).
 #include <algorithm>
 #include <array>
 #include <atomic>
