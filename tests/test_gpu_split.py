@@ -66,15 +66,38 @@ def test_split_against_fp64_path(cuda, cls, K, nq):
 
 
 @pytest.mark.parametrize("cls,K,nq", [((2, 2, 2, 2), 1, 16), ((3, 3, 2, 2), 1, 16), ((3, 3, 3, 3), 1, 8),
-                                      ((3, 3, 2, 2), 5, 2)])
+                                      ((2, 2, 2, 2), 5, 32), ((3, 3, 3, 3), 5, 16), ((3, 3, 2, 2), 5, 24)])
 def test_fp64_and_split_against_oracle(cuda, cls, K, nq):
-    """Both forms against the oracle on the high-l workload, K = 5 included."""
+    """Both forms against the oracle, element by element, on the high-l
+    workload (exponents log-uniform in [0.05, 50], centres in a 12-bohr cube),
+    the (dd|dd), (ff|ff) and (ff|dd) classes primitive and with K = 5 on every
+    shell (25 primitive pairs per side).  FP64 takes the parity bar
+    1e-11 + 1e-10 |ref|; split takes the 1e-10 absolute bar (plus the same
+    relative term, which only matters for elements above 1)."""
     basis, bra, ket, q = synth.split_batch(cls, K=K, seed=7, nq=nq, pool=16, npairs=8)
     ref = oracle_blocks(cls, basis, bra, ket, q, prec="d")
     f64 = gpu_list(cls, basis, bra, ket, q)
-    assert_close(f64, ref, what=f"fp64 vs oracle {cls} K={K}")
+    e64 = assert_close(f64, ref, what=f"fp64 vs oracle {cls} K={K}")
     spl = gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT)
-    assert_close(spl, ref, atol=1e-10, rtol=1e-10, what=f"split vs oracle {cls} K={K}")
+    esp = assert_close(spl, ref, atol=1e-10, rtol=1e-10, what=f"split vs oracle {cls} K={K}")
+    print(f"{cls} K={K}: max |fp64 - oracle| = {e64:.2e}, max |split - oracle| = {esp:.2e}, "
+          f"max |oracle| = {np.abs(ref).max():.2e}")
+
+
+@pytest.mark.parametrize("cls", [(2, 2, 2, 2), (3, 3, 3, 3), (3, 3, 2, 2)])
+def test_k5_full_size_sample_against_oracle(cuda, cls):
+    """K = 5 on every shell at the benchmark's pool sizes (512 shells per l,
+    2048 pairs per side): FP64 and split over a batch of several thousand
+    quartets, compared with the oracle on a seeded sample of them."""
+    nq = {(2, 2, 2, 2): 4000, (3, 3, 3, 3): 600, (3, 3, 2, 2): 2000}[cls]
+    basis, bra, ket, q = synth.split_batch(cls, K=5, seed=11, nq=nq)
+    db = eri.DeviceBasis(basis)
+    f64 = gpu_list(cls, basis, bra, ket, q, dbasis=db)
+    spl = gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT, dbasis=db)
+    pick = np.sort(np.random.default_rng(3).choice(nq, 8, replace=False))
+    ref = oracle_blocks(cls, basis, bra, ket, q[pick], prec="d")
+    assert_close(f64[pick], ref, what=f"fp64 vs oracle {cls} K=5 sample")
+    assert_close(spl[pick], ref, atol=1e-10, rtol=1e-10, what=f"split vs oracle {cls} K=5 sample")
 
 
 @pytest.mark.parametrize("cls", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 1, 0, 2), (2, 2, 1, 1)])

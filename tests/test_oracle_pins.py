@@ -327,3 +327,21 @@ def test_double_oracle_close_to_long_double(cls):
     ld = oracle.eri_quartets(basis, qs, prec="ld").astype(np.float64)
     d = oracle.eri_quartets(basis, qs, prec="d")
     assert np.max(np.abs(d - ld) - 1e-13 * np.abs(ld)) < 1e-14
+
+
+@pytest.mark.parametrize("cls", [(2, 2, 2, 2), (3, 3, 2, 2), (3, 3, 3, 3)])
+def test_double_oracle_close_to_long_double_high_l_k5(cls):
+    """The same on the high angular momentum workload the split-precision
+    tests use (exponents log-uniform in [0.05, 50], centres in a 12-bohr
+    cube, K = 5 on every shell, L up to 12): the GPU tests of those classes
+    compare with the double build."""
+    basis, bra, ket, q = synth.split_batch(cls, K=5, seed=7, nq=64, pool=16, npairs=8)
+    qs = synth.quartet_shells(bra, ket, q)
+    # the most compact candidate (shortest |A-B| + |C-D|): integrals of order one
+    c = basis.centres[basis.shell_atom]
+    spread = np.linalg.norm(c[qs[:, 0]] - c[qs[:, 1]], axis=1) + np.linalg.norm(c[qs[:, 2]] - c[qs[:, 3]], axis=1)
+    qs = qs[np.argsort(spread)[:1]]
+    ld = oracle.eri_quartets(basis, qs, prec="ld").astype(np.float64)
+    d = oracle.eri_quartets(basis, qs, prec="d")
+    print(f"{cls} K=5: max |d - ld| = {np.max(np.abs(d - ld)):.2e}, max |ld| = {np.max(np.abs(ld)):.2e}")
+    assert np.max(np.abs(d - ld) - 1e-13 * np.abs(ld)) < 1e-14
