@@ -44,7 +44,8 @@ EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_er
            "eri_profile_enable", "eri_profile_read", "eri_launch_count", "eri_batch_noalloc", "eri_plan_create",
            "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
            "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees", "eri_batch3", "eri_solid_harmonics", "eri_batch_sph",
-           "eri_last_grad_forms", "eri_set_grad_forms"]
+           "eri_last_grad_forms", "eri_set_grad_forms", "eri_peak_probe",
+           "eri_partition", "eri_plan_set_slice", "eri_plan_slice_info"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
@@ -96,6 +97,14 @@ def lib() -> ctypes.CDLL:
             L.eri_profile_enable.restype = I
             L.eri_profile_read.argtypes = [I, P, P]
             L.eri_profile_read.restype = I
+            L.eri_partition.argtypes = [P, I64, ctypes.c_int32, P, P]
+            L.eri_partition.restype = I
+            L.eri_plan_set_slice.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P]
+            L.eri_plan_set_slice.restype = I
+            L.eri_plan_slice_info.argtypes = [P, P, P, P]
+            L.eri_plan_slice_info.restype = I
+            L.eri_peak_probe.argtypes = [I, P, P, P]
+            L.eri_peak_probe.restype = I
             L.eri_launch_count.argtypes = []
             L.eri_launch_count.restype = I64
             for f in ("eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_finalize"):
@@ -118,14 +127,43 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _ptr(t):
+def _ptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor on the current device.
+    With ``dtype`` the tensor's element type is checked too: the library reads
+    and writes raw memory, so a tensor of the wrong type or on another GPU
+    would be read or written past its end."""
     if t is None:
         return None
     if not t.is_cuda:
-        raise ValueError("expected a CUDA tensor")
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on {t.device}, but the current device is cuda:{torch.cuda.current_device()}")
     if not t.is_contiguous():
-        raise ValueError("expected a contiguous tensor")
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _pairs(t, name):
+    """A [n][2] int32 pair list (or [n] int32 shell list when 1-D)."""
+    p = _ptr(t, torch.int32, name)
+    if t.dim() == 2 and t.shape[1] != 2:
+        raise ValueError(f"{name}: expected shape [n][2], got {tuple(t.shape)}")
+    return p
+
+
+def _quartets(t, name="quartets"):
+    if t is None:
+        return None
+    p = _ptr(t, torch.int64, name)
+    if t.dim() != 2 or t.shape[1] != 2:
+        raise ValueError(f"{name}: expected shape [n][2], got {tuple(t.shape)}")
+    return p
+
+
+def _f64(t, name):
+    return _ptr(t, torch.float64, name)
 
 
 def nc(l: int) -> int:
@@ -150,8 +188,12 @@ class DeviceBasis:
     def struct(self, centres=None, exps=None) -> eri_basis_t:
         c = self.centres if centres is None else centres
         e = self.exps if exps is None else exps
-        return eri_basis_t(_ptr(c), _ptr(self.shell_atom), _ptr(self.shell_l), _ptr(self.shell_K),
-                           _ptr(self.shell_off), _ptr(e), _ptr(self.coefs), c.shape[0],
+        if c.dim() != 2 or c.shape[1] != 3:
+            raise ValueError(f"centres: expected shape [natom][3], got {tuple(c.shape)}")
+        return eri_basis_t(_f64(c, "centres"), _ptr(self.shell_atom, torch.int32, "shell_atom"),
+                           _ptr(self.shell_l, torch.int32, "shell_l"), _ptr(self.shell_K, torch.int32, "shell_K"),
+                           _ptr(self.shell_off, torch.int32, "shell_off"), _f64(e, "exps"),
+                           _f64(self.coefs, "coefs"), c.shape[0],
                            self.shell_l.shape[0], e.shape[0])
 
 
@@ -160,7 +202,9 @@ def eri_boys(mmax: int, T: torch.Tensor, out: torch.Tensor | None = None, stream
     T = T.contiguous()
     if out is None:
         out = torch.empty((T.numel(), mmax + 1), dtype=torch.float64, device=T.device)
-    _check(lib().eri_boys(mmax, _ptr(T), T.numel(), _ptr(out), _stream(stream)), "eri_boys")
+    if out.numel() < T.numel() * (mmax + 1):
+        raise ValueError(f"out: expected at least {T.numel() * (mmax + 1)} elements, got {out.numel()}")
+    _check(lib().eri_boys(mmax, _f64(T, "T"), T.numel(), _f64(out, "out"), _stream(stream)), "eri_boys")
     return out
 
 
@@ -182,9 +226,9 @@ def eri_batch(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pairs: torch
     if n == 0:  # an empty quartet list has no device pointer; nothing to compute
         return out
     b = basis.struct(centres, exps)
-    code = lib().eri_batch(eri_class_t(*cls), ctypes.byref(b), _ptr(bra_pairs), nbra, _ptr(ket_pairs), nket,
-                           _ptr(quartets), nq if nq is not None else 0, _ptr(out), out.numel(), precision,
-                           _stream(stream))
+    code = lib().eri_batch(eri_class_t(*cls), ctypes.byref(b), _pairs(bra_pairs, "bra_pairs"), nbra,
+                           _pairs(ket_pairs, "ket_pairs"), nket, _quartets(quartets), nq if nq is not None else 0,
+                           _f64(out, "out"), out.numel(), precision, _stream(stream))
     _check(code, "eri_batch")
     return out
 
@@ -202,8 +246,9 @@ def eri_batch_sph(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pairs: t
     if n == 0:
         return out
     b = basis.struct()
-    code = lib().eri_batch_sph(eri_class_t(*cls), ctypes.byref(b), _ptr(bra_pairs), nbra, _ptr(ket_pairs), nket,
-                               _ptr(quartets), nq if nq is not None else 0, _ptr(out), out.numel(), precision,
+    code = lib().eri_batch_sph(eri_class_t(*cls), ctypes.byref(b), _pairs(bra_pairs, "bra_pairs"), nbra,
+                               _pairs(ket_pairs, "ket_pairs"), nket, _quartets(quartets),
+                               nq if nq is not None else 0, _f64(out, "out"), out.numel(), precision,
                                _stream(stream))
     _check(code, "eri_batch_sph")
     return out
@@ -230,8 +275,9 @@ def eri_batch3(lx: int, lc: int, ld: int, basis: DeviceBasis, x_shells: torch.Te
     if n == 0:
         return out
     b = basis.struct()
-    code = lib().eri_batch3(lx, lc, ld, ctypes.byref(b), _ptr(x_shells), nx, _ptr(ket_pairs), nket, _ptr(triples),
-                            nt if nt is not None else 0, 1 if pure else 0, _ptr(out), out.numel(), precision,
+    code = lib().eri_batch3(lx, lc, ld, ctypes.byref(b), _ptr(x_shells, torch.int32, "x_shells"), nx,
+                            _pairs(ket_pairs, "ket_pairs"), nket, _quartets(triples, "triples"),
+                            nt if nt is not None else 0, 1 if pure else 0, _f64(out, "out"), out.numel(), precision,
                             _stream(stream))
     _check(code, "eri_batch3")
     return out
@@ -246,9 +292,15 @@ def eri_batch_grad(cls, basis: DeviceBasis, bra_pairs, ket_pairs, quartets, W: t
     if out_len(cls, nbra, nket, nq) == 0:
         return grad_centres, grad_exps
     b = basis.struct(centres, exps)
-    code = lib().eri_batch_grad(eri_class_t(*cls), ctypes.byref(b), _ptr(bra_pairs), nbra, _ptr(ket_pairs), nket,
-                                _ptr(quartets), nq if nq is not None else 0, _ptr(W.contiguous()), W.numel(),
-                                _ptr(grad_centres), _ptr(grad_exps), _stream(stream))
+    W = W.contiguous()
+    if grad_centres is not None and grad_centres.numel() != 3 * b.natom:
+        raise ValueError(f"grad_centres: expected {3 * b.natom} elements, got {grad_centres.numel()}")
+    if grad_exps is not None and grad_exps.numel() != b.nprim:
+        raise ValueError(f"grad_exps: expected {b.nprim} elements, got {grad_exps.numel()}")
+    code = lib().eri_batch_grad(eri_class_t(*cls), ctypes.byref(b), _pairs(bra_pairs, "bra_pairs"), nbra,
+                                _pairs(ket_pairs, "ket_pairs"), nket, _quartets(quartets),
+                                nq if nq is not None else 0, _f64(W, "W"), W.numel(),
+                                _f64(grad_centres, "grad_centres"), _f64(grad_exps, "grad_exps"), _stream(stream))
     _check(code, "eri_batch_grad")
     return grad_centres, grad_exps
 
@@ -307,6 +359,31 @@ def eri_profile_read() -> dict:
     return {i: (int(launches[i]), float(ms[i])) for i in range(n)}
 
 
+def partition(costs, nranks: int):
+    """(owner rank of each unit, load of each rank): the library's
+    longest-processing-time-first partition (host only, no GPU work)."""
+    import numpy as np
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    owner = np.zeros(c.size, dtype=np.int32)
+    load = np.zeros(max(int(nranks), 1), dtype=np.float64)
+    _check(lib().eri_partition(ctypes.c_void_p(c.ctypes.data), c.size, int(nranks),
+                               ctypes.c_void_p(owner.ctypes.data), ctypes.c_void_p(load.ctypes.data)),
+           "eri_partition")
+    return owner, load
+
+
+PEAK_DFMA, PEAK_DMMA, PEAK_FFMA = 0, 1, 2
+
+
+def eri_peak_probe(kind: int, stream=None) -> tuple:
+    """(GFLOP/s, SM MHz during the probe) of one arithmetic-throughput probe
+    (PEAK_DFMA, PEAK_DMMA or PEAK_FFMA) on the current device."""
+    g = ctypes.c_double()
+    mhz = ctypes.c_double()
+    _check(lib().eri_peak_probe(int(kind), ctypes.byref(g), ctypes.byref(mhz), _stream(stream)), "eri_peak_probe")
+    return g.value, mhz.value
+
+
 def eri_launch_count() -> int:
     return int(lib().eri_launch_count())
 
@@ -321,9 +398,9 @@ def eri_batch_noalloc(cls, basis: DeviceBasis, bra_pairs: torch.Tensor, ket_pair
     if out_len(cls, nbra, nket, nq) == 0:
         return out
     b = basis.struct()
-    code = lib().eri_batch_noalloc(eri_class_t(*cls), ctypes.byref(b), _ptr(bra_pairs), nbra, _ptr(ket_pairs), nket,
-                                   _ptr(quartets), nq if nq is not None else 0, _ptr(out), out.numel(),
-                                   _stream(stream))
+    code = lib().eri_batch_noalloc(eri_class_t(*cls), ctypes.byref(b), _pairs(bra_pairs, "bra_pairs"), nbra,
+                                   _pairs(ket_pairs, "ket_pairs"), nket, _quartets(quartets),
+                                   nq if nq is not None else 0, _f64(out, "out"), out.numel(), _stream(stream))
     _check(code, "eri_batch_noalloc")
     return out
 
@@ -358,10 +435,23 @@ class Plan:
                    "eri_plan_job")
         return (cls.la, cls.lb, cls.lc, cls.ld), nq.value, off.value, shells
 
+    @staticmethod
+    def _square(D, *others):
+        """D is [nbf][nbf]; every other matrix has D's shape."""
+        if D.dim() != 2 or D.shape[0] != D.shape[1]:
+            raise ValueError(f"D: expected a square matrix, got {tuple(D.shape)}")
+        for name, M in others:
+            if M is not None and tuple(M.shape) != tuple(D.shape):
+                raise ValueError(f"{name}: expected shape {tuple(D.shape)}, got {tuple(M.shape)}")
+
     def execute(self, D: torch.Tensor | None = None, energy: torch.Tensor | None = None,
                 out: torch.Tensor | None = None, stream=None):
+        if D is not None:
+            self._square(D)
+        if energy is not None and energy.numel() < 1:
+            raise ValueError("energy: expected at least one element")
         nbf = D.shape[0] if D is not None else 0
-        _check(lib().eri_plan_execute(self.ptr, _ptr(D), nbf, _ptr(energy), _ptr(out),
+        _check(lib().eri_plan_execute(self.ptr, _f64(D, "D"), nbf, _f64(energy, "energy"), _f64(out, "out"),
                                       out.numel() if out is not None else 0, _stream(stream)), "eri_plan_execute")
 
     def coulomb(self, D: torch.Tensor, J: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -369,7 +459,9 @@ class Plan:
         D = D.contiguous()
         if J is None:
             J = torch.empty_like(D)
-        _check(lib().eri_plan_coulomb(self.ptr, _ptr(D), D.shape[0], _ptr(J), _stream(stream)), "eri_plan_coulomb")
+        self._square(D, ("J", J))
+        _check(lib().eri_plan_coulomb(self.ptr, _f64(D, "D"), D.shape[0], _f64(J, "J"), _stream(stream)),
+               "eri_plan_coulomb")
         return J
 
     def jk(self, D: torch.Tensor, want_j: bool = True, want_k: bool = True, J: torch.Tensor | None = None,
@@ -382,7 +474,9 @@ class Plan:
             K = torch.empty_like(D)
         J = J if want_j else None
         K = K if want_k else None
-        _check(lib().eri_plan_jk(self.ptr, _ptr(D), D.shape[0], _ptr(J), _ptr(K), _stream(stream)), "eri_plan_jk")
+        self._square(D, ("J", J), ("K", K))
+        _check(lib().eri_plan_jk(self.ptr, _f64(D, "D"), D.shape[0], _f64(J, "J"), _f64(K, "K"), _stream(stream)),
+               "eri_plan_jk")
         return J, K
 
     def job_degrees(self, j: int):
@@ -391,6 +485,16 @@ class Plan:
         kk = ctypes.c_int32()
         _check(lib().eri_plan_job_degrees(self.ptr, int(j), ctypes.byref(kb), ctypes.byref(kk)), "eri_plan_job_degrees")
         return kb.value, kk.value
+
+    def set_slice(self, rank: int, nranks: int, stream=None):
+        """Keep the work items the cost-balanced partition gives to ``rank`` of ``nranks``."""
+        _check(lib().eri_plan_set_slice(self.ptr, int(rank), int(nranks), _stream(stream)), "eri_plan_set_slice")
+
+    def slice_info(self):
+        n, q, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().eri_plan_slice_info(self.ptr, ctypes.byref(n), ctypes.byref(q), ctypes.byref(c)),
+               "eri_plan_slice_info")
+        return {"nitems": n.value, "nquartets": q.value, "cost": c.value}
 
     def set_budget(self, cycles: int):
         _check(lib().eri_plan_set_budget(self.ptr, int(cycles)), "eri_plan_set_budget")

@@ -112,11 +112,23 @@ const ClassTables* get_class_tables_sph(int la, int lb, int lc, int ld, int hrr,
 // Real solid harmonics (Racah normalisation) as [2l+1][nc(l)] Cartesian coefficients.
 void solid_harmonic_table(int l, double* out);
 const double* get_boys_table(int L, cudaStream_t s, int* err);    // rows of F_{L+k}(T_j)/k!, plus exp
-const double* get_boys_master(cudaStream_t s, int* err);          // rows of F_0..F_kBoysMtab and exp
 const RStep* get_rsteps(cudaStream_t s, int* err);                 // recursion step table (device)
 void release_all();
 
-// Hermite numbering helpers (host)
+// Host table builders that allocate nothing (they fill the caller's
+// buffers); the cached tables above and the allocation-free entry point's
+// fixed tables both come from them.
+//   build_boys_master: [kBoysGrid][kBoysMtab + 2] rows F_0..F_kBoysMtab(T_j), exp(-T_j);
+//   boys_taylor_rows:  [kBoysGrid][8] rows F_{L+k}(T_j)/k!, k < kBoysOrder, exp(-T_j);
+//   build_rstep_table: [kNhMax] steps of the auxiliary recursion;
+//   pair_term_list:    nonzero (component pair, Hermite) terms of a Cartesian
+//                      pair (l1, l2); returns their number (null outputs: count only).
+void build_boys_master(long double* rows);
+void boys_taylor_rows(const long double* master, int L, double* out);
+void build_rstep_table(RStep* st);
+int pair_term_list(int l1, int l2, int* start, int16_t* herm, uint8_t* fac);
+
+// Hermite numbering helpers (host, closed forms)
 int herm_index(int t, int u, int v);
 void herm_tuv(int idx, int* t, int* u, int* v);
 

@@ -2,14 +2,17 @@
 // or host allocation.
 //
 // Some callers cannot allocate: a process whose device memory is owned by
-// another allocator (a serving framework's pool, an MPI library's pinned
-// pool) may not call cudaMalloc behind its back, and code that runs while a
-// stream is being captured into a CUDA graph must not allocate.  For them
-// the pair tables that eri_batch keeps in a cudaMalloc'ed workspace live
-// here in a fixed, file-scope device array instead, next to fixed arrays for
-// the constant tables (Boys function, recursion steps, class tables) and the
-// validation words.  The arrays exist on every GPU that loads the library
-// until the process exits.
+// another allocator (a serving or training framework's caching pool, an MPI
+// library's registered pool) may not call cudaMalloc behind that
+// allocator's back, since memory it does not know about can make it fail
+// its own allocations or break its accounting.  For them the pair tables
+// that eri_batch keeps in a cudaMalloc'ed workspace live here in a fixed,
+// file-scope device array instead, next to fixed arrays for the constant
+// tables (Boys function, recursion steps, class tables) and the validation
+// words.  The arrays exist on every GPU that loads the library until the
+// process exits.  The constant tables come from the same host builders as
+// eri_batch's cached ones, which fill caller-given buffers and allocate
+// nothing.
 //
 // Set-up, once per device: the first call on a device, with that device
 // current, computes the constant tables on the host into static host
@@ -50,76 +53,17 @@ struct DevPtrs {
 static DevPtrs g_dev_ptrs[kMaxDev];
 static std::mutex g_mu;
 
-// ---- host tables in static storage (no heap) --------------------------------
-static long double h_master[kBoysGrid][kBoysMtab + 2];
+// ---- host tables in static storage (no heap), filled by the library's
+// shared, allocation-free table builders
+static long double h_master[kBoysGrid * (kBoysMtab + 2)];
 static double h_boys[(kLtotMax + 1) * kBoysRows];
 static RStep h_rsteps[kNhMax];
 
-// Hermite numbering of (t,u,v), order by N = t+u+v then t, u descending.
-static int hidx(int t, int u, int v)
-{
-    const int N = t + u + v;
-    return N * (N + 1) * (N + 2) / 6 + (N - t) * (N - t + 1) / 2 + (N - t - u);
-}
-
-static void htuv(int idx, int* t, int* u, int* v)
-{
-    int N = 0;
-    while ((N + 1) * (N + 2) * (N + 3) / 6 <= idx) ++N;
-    int r = idx - N * (N + 1) * (N + 2) / 6;
-    int d = 0;  // d = N - t
-    while ((d + 1) * (d + 2) / 2 <= r) ++d;
-    const int e = r - d * (d + 1) / 2;  // e = N - t - u
-    *t = N - d;
-    *u = d - e;
-    *v = N - *t - *u;
-}
-
 static void build_constant_tables()
 {
-    // Boys: top order by its all-positive series, lower orders downward
-    for (int j = 0; j < kBoysGrid; ++j) {
-        const long double T = (long double)j / kBoysInvStep;
-        const long double eT = expl(-T);
-        long double term = 1.0L / (2 * kBoysMtab + 1), sum = term;
-        for (int k = 1; k < 10000; ++k) {
-            term *= 2.0L * T / (long double)(2 * kBoysMtab + 2 * k + 1);
-            sum += term;
-            if (term < sum * 1e-22L) break;
-        }
-        h_master[j][kBoysMtab] = eT * sum;
-        for (int m = kBoysMtab - 1; m >= 0; --m) h_master[j][m] = (2.0L * T * h_master[j][m + 1] + eT) / (2 * m + 1);
-        h_master[j][kBoysMtab + 1] = eT;
-    }
-    for (int L = 0; L <= kLtotMax; ++L) {
-        long double fact = 1;
-        for (int k = 0; k < kBoysOrder; ++k) {
-            if (k > 0) fact *= k;
-            for (int j = 0; j < kBoysGrid; ++j)
-                h_boys[(size_t)L * kBoysRows + (size_t)j * 8 + k] = (double)(h_master[j][L + k] / fact);
-        }
-        for (int j = 0; j < kBoysGrid; ++j) h_boys[(size_t)L * kBoysRows + (size_t)j * 8 + 7] = (double)h_master[j][kBoysMtab + 1];
-    }
-    // auxiliary-recursion steps (axis with r_i = 1 preferred)
-    std::memset(h_rsteps, 0, sizeof(h_rsteps));
-    for (int e = 1; e < kNhMax; ++e) {
-        int r[3];
-        htuv(e, &r[0], &r[1], &r[2]);
-        int axis = -1;
-        for (int i = 0; i < 3; ++i)
-            if (r[i] == 1) { axis = i; break; }
-        if (axis < 0)
-            for (int i = 0; i < 3; ++i)
-                if (r[i] > 0 && (axis < 0 || r[i] < r[axis])) axis = i;
-        int d1[3] = {r[0], r[1], r[2]}, d2[3] = {r[0], r[1], r[2]};
-        d1[axis] -= 1;
-        d2[axis] -= 2;
-        h_rsteps[e].axis = (int8_t)axis;
-        h_rsteps[e].coef = (int8_t)(r[axis] - 1);
-        h_rsteps[e].coefd = (double)(r[axis] - 1);
-        h_rsteps[e].src1 = (int16_t)hidx(d1[0], d1[1], d1[2]);
-        h_rsteps[e].src2 = (int16_t)(r[axis] >= 2 ? hidx(d2[0], d2[1], d2[2]) : 0);
-    }
+    build_boys_master(h_master);
+    for (int L = 0; L <= kLtotMax; ++L) boys_taylor_rows(h_master, L, h_boys + (size_t)L * kBoysRows);
+    build_rstep_table(h_rsteps);
 }
 
 static int setup_device(int dev, DevPtrs* out)
@@ -156,30 +100,6 @@ struct HostClassBlob {
 static_assert(sizeof(HostClassBlob) <= sizeof(g_class), "class blob does not fit its static array");
 static HostClassBlob h_blob;
 
-static int terms_of(int l1, int l2, int* start, int16_t* herm, uint8_t* fac)
-{
-    const int L12 = l1 + l2;
-    int n = 0, k = 0;
-    start[0] = 0;
-    for (int ax = l1; ax >= 0; --ax)
-        for (int ay = l1 - ax; ay >= 0; --ay)
-            for (int bx = l2; bx >= 0; --bx)
-                for (int by = l2 - bx; by >= 0; --by) {
-                    const int a[3] = {ax, ay, l1 - ax - ay}, b[3] = {bx, by, l2 - bx - by};
-                    for (int tx = 0; tx <= a[0] + b[0]; ++tx)
-                        for (int ty = 0; ty <= a[1] + b[1]; ++ty)
-                            for (int tz = 0; tz <= a[2] + b[2]; ++tz) {
-                                herm[n] = (int16_t)hidx(tx, ty, tz);
-                                const int tt[3] = {tx, ty, tz};
-                                for (int i = 0; i < 3; ++i)
-                                    fac[3 * n + i] = (uint8_t)((a[i] * (l2 + 1) + b[i]) * (L12 + 1) + tt[i]);
-                                ++n;
-                            }
-                    start[++k] = n;
-                }
-    return n;
-}
-
 static void class_tables(eri_class_t c, const uint8_t* dev_blob, ClassTables* t)
 {
     std::memset(t, 0, sizeof(*t));
@@ -190,14 +110,14 @@ static void class_tables(eri_class_t c, const uint8_t* dev_blob, ClassTables* t)
     t->nhb = host_nh(t->Lb); t->nhk = host_nh(t->Lk); t->nhl = host_nh(t->L);
     t->nab_f = t->nab;
     t->ncd_f = t->ncd;
-    t->Tab = terms_of(c.la, c.lb, h_blob.bstart, h_blob.bp, h_blob.bfac);
-    t->Tcd = terms_of(c.lc, c.ld, h_blob.kstart, h_blob.kq, h_blob.kfac);
+    t->Tab = pair_term_list(c.la, c.lb, h_blob.bstart, h_blob.bp, h_blob.bfac);
+    t->Tcd = pair_term_list(c.lc, c.ld, h_blob.kstart, h_blob.kq, h_blob.kfac);
     for (int p = 0; p < t->nhb; ++p)
         for (int q = 0; q < t->nhk; ++q) {
             int a, b, cc, x, y, z;
-            htuv(p, &a, &b, &cc);
-            htuv(q, &x, &y, &z);
-            h_blob.pq[p * t->nhk + q] = (int16_t)hidx(a + x, b + y, cc + z);
+            herm_tuv(p, &a, &b, &cc);
+            herm_tuv(q, &x, &y, &z);
+            h_blob.pq[p * t->nhk + q] = (int16_t)herm_index(a + x, b + y, cc + z);
         }
     const HostClassBlob* d = reinterpret_cast<const HostClassBlob*>(dev_blob);
     t->bra_start = d->bstart;

@@ -15,41 +15,27 @@
 namespace eri {
 
 // ---------------------------------------------------------------------------
-// Hermite numbering (order by total N, then t descending, then u descending)
+// Hermite numbering (order by total N, then t descending, then u descending).
+// Closed forms, no tables: the allocation-free entry point shares them.
 // ---------------------------------------------------------------------------
-static std::vector<int> g_herm_idx;   // (t,u,v) -> index, dense (kLtotMax+1)^3
-static std::vector<int> g_herm_t, g_herm_u, g_herm_v;
-static std::once_flag g_herm_once;
-
-static void build_herm()
-{
-    const int n = kLtotMax + 1;
-    g_herm_idx.assign(n * n * n, -1);
-    for (int N = 0; N <= kLtotMax; ++N)
-        for (int t = N; t >= 0; --t)
-            for (int u = N - t; u >= 0; --u) {
-                int v = N - t - u;
-                g_herm_idx[(t * n + u) * n + v] = (int)g_herm_t.size();
-                g_herm_t.push_back(t);
-                g_herm_u.push_back(u);
-                g_herm_v.push_back(v);
-            }
-}
-
 int herm_index(int t, int u, int v)
 {
-    std::call_once(g_herm_once, build_herm);
-    const int n = kLtotMax + 1;
     if (t < 0 || u < 0 || v < 0 || t + u + v > kLtotMax) return -1;
-    return g_herm_idx[(t * n + u) * n + v];
+    const int N = t + u + v, d = N - t, e = N - t - u;
+    return N * (N + 1) * (N + 2) / 6 + d * (d + 1) / 2 + e;
 }
 
 void herm_tuv(int idx, int* t, int* u, int* v)
 {
-    std::call_once(g_herm_once, build_herm);
-    *t = g_herm_t[idx];
-    *u = g_herm_u[idx];
-    *v = g_herm_v[idx];
+    int N = 0;
+    while ((N + 1) * (N + 2) * (N + 3) / 6 <= idx) ++N;
+    const int r = idx - N * (N + 1) * (N + 2) / 6;
+    int d = 0;  // d = N - t
+    while ((d + 1) * (d + 2) / 2 <= r) ++d;
+    const int e = r - d * (d + 1) / 2;  // e = N - t - u
+    *t = N - d;
+    *u = d - e;
+    *v = N - *t - *u;
 }
 
 static std::vector<std::array<int, 3>> carts(int l)
@@ -65,17 +51,9 @@ static std::vector<std::array<int, 3>> carts(int l)
 // >= 1 pick the axis that needs the fewest FP64 operations: an axis with
 // e_i = 1 needs only X_i * [e-1_i] (the e_i-1 coefficient vanishes).
 // ---------------------------------------------------------------------------
-const RStep* get_rsteps(cudaStream_t s, int* err)
+void build_rstep_table(RStep* st)
 {
-    static std::map<int, RStep*> tabs;
-    static std::mutex mu;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = tabs.find(dev);
-    if (it != tabs.end()) return it->second;
-    std::vector<RStep> st(kNhMax);
-    std::memset(st.data(), 0, sizeof(RStep) * kNhMax);
+    std::memset(st, 0, sizeof(RStep) * kNhMax);
     for (int e = 1; e < kNhMax; ++e) {
         int r[3];
         herm_tuv(e, &r[0], &r[1], &r[2]);
@@ -94,6 +72,19 @@ const RStep* get_rsteps(cudaStream_t s, int* err)
         st[e].src1 = (int16_t)herm_index(d1[0], d1[1], d1[2]);
         st[e].src2 = (int16_t)(r[axis] >= 2 ? herm_index(d2[0], d2[1], d2[2]) : 0);
     }
+}
+
+const RStep* get_rsteps(cudaStream_t s, int* err)
+{
+    static std::map<int, RStep*> tabs;
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = tabs.find(dev);
+    if (it != tabs.end()) return it->second;
+    std::vector<RStep> st(kNhMax);
+    build_rstep_table(st.data());
     RStep* d = nullptr;
     if (cudaMalloc(&d, sizeof(RStep) * kNhMax) != cudaSuccess) {
         *err = ERI_ENOMEM;
@@ -107,6 +98,36 @@ const RStep* get_rsteps(cudaStream_t s, int* err)
     }
     tabs[dev] = d;
     return d;
+}
+
+// Nonzero terms of a Cartesian pair (l1, l2): for every component pair
+// (a, b) (a-major) every Hermite function t with t_i <= a_i + b_i on each
+// axis.  start[ab]..start[ab+1]: the terms of pair ab; herm: the Hermite
+// index of t; fac[3 n + i]: the per-axis E-table index (a_i, b_i, t_i).
+// With null outputs only the count is returned.
+int pair_term_list(int l1, int l2, int* start, int16_t* herm, uint8_t* fac)
+{
+    const int L12 = l1 + l2;
+    int n = 0, k = 0;
+    if (start) start[0] = 0;
+    for (int ax = l1; ax >= 0; --ax)
+        for (int ay = l1 - ax; ay >= 0; --ay)
+            for (int bx = l2; bx >= 0; --bx)
+                for (int by = l2 - bx; by >= 0; --by) {
+                    const int a[3] = {ax, ay, l1 - ax - ay}, b[3] = {bx, by, l2 - bx - by};
+                    for (int tx = 0; tx <= a[0] + b[0]; ++tx)
+                        for (int ty = 0; ty <= a[1] + b[1]; ++ty)
+                            for (int tz = 0; tz <= a[2] + b[2]; ++tz) {
+                                if (herm) herm[n] = (int16_t)herm_index(tx, ty, tz);
+                                const int tt[3] = {tx, ty, tz};
+                                if (fac)
+                                    for (int i = 0; i < 3; ++i)
+                                        fac[3 * n + i] = (uint8_t)((a[i] * (l2 + 1) + b[i]) * (L12 + 1) + tt[i]);
+                                ++n;
+                            }
+                    if (start) start[++k] = n;
+                }
+    return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -260,20 +281,11 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
 
     auto build_terms = [](int l1, int l2, std::vector<int>& start, std::vector<int16_t>& herm,
                           std::vector<uint8_t>& fac) {
-        const int L12 = l1 + l2;
-        start.push_back(0);
-        for (auto& a : carts(l1))
-            for (auto& b : carts(l2)) {
-                for (int tx = 0; tx <= a[0] + b[0]; ++tx)
-                    for (int ty = 0; ty <= a[1] + b[1]; ++ty)
-                        for (int tz = 0; tz <= a[2] + b[2]; ++tz) {
-                            herm.push_back((int16_t)herm_index(tx, ty, tz));
-                            const int tt[3] = {tx, ty, tz};
-                            for (int i = 0; i < 3; ++i)
-                                fac.push_back((uint8_t)((a[i] * (l2 + 1) + b[i]) * (L12 + 1) + tt[i]));
-                        }
-                start.push_back((int)herm.size());
-            }
+        const int n = pair_term_list(l1, l2, nullptr, nullptr, nullptr);
+        start.resize((size_t)host_nc(l1) * host_nc(l2) + 1);
+        herm.resize(n);
+        fac.resize(3 * (size_t)n);
+        pair_term_list(l1, l2, start.data(), herm.data(), fac.data());
     };
     // E_{e,0} terms of the functions e with l1 <= |e| <= l1+l2 (table dims
     // (l1+l2+1) x 1 x (l1+l2+1)), in the order of the HRR level 0
@@ -471,13 +483,9 @@ static const ClassTables* class_tables_impl(int la, int lb, int lc, int ld, int 
 // exp(-T_j): the coefficients of the Taylor expansion about T_j used by the
 // kernels' Boys evaluation.
 // ---------------------------------------------------------------------------
-static std::vector<long double> g_master_host;
-static std::once_flag g_master_once;
-
-static void build_master()
+void build_boys_master(long double* rows)
 {
     const int W = kBoysMtab + 2;
-    g_master_host.assign((size_t)kBoysGrid * W, 0.0L);
     for (int j = 0; j < kBoysGrid; ++j) {
         const long double T = (long double)j / kBoysInvStep;
         const long double eT = expl(-T);
@@ -487,11 +495,33 @@ static void build_master()
             sum += term;
             if (term < sum * 1e-22L) break;
         }
-        long double* row = &g_master_host[(size_t)j * W];
+        long double* row = rows + (size_t)j * W;
         row[kBoysMtab] = eT * sum;
         for (int m = kBoysMtab - 1; m >= 0; --m) row[m] = (2.0L * T * row[m + 1] + eT) / (long double)(2 * m + 1);
         row[kBoysMtab + 1] = eT;
     }
+}
+
+void boys_taylor_rows(const long double* master, int L, double* out)
+{
+    const int W = kBoysMtab + 2;
+    long double fact[kBoysOrder];
+    fact[0] = 1;
+    for (int k = 1; k < kBoysOrder; ++k) fact[k] = fact[k - 1] * k;
+    for (int j = 0; j < kBoysGrid; ++j) {
+        const long double* row = master + (size_t)j * W;
+        for (int k = 0; k < kBoysOrder; ++k) out[(size_t)j * 8 + k] = (double)(row[L + k] / fact[k]);
+        out[(size_t)j * 8 + 7] = (double)row[kBoysMtab + 1];
+    }
+}
+
+static std::vector<long double> g_master_host;
+static std::once_flag g_master_once;
+
+static void build_master()
+{
+    g_master_host.assign((size_t)kBoysGrid * (kBoysMtab + 2), 0.0L);
+    build_boys_master(g_master_host.data());
 }
 
 static std::map<std::pair<int, int>, double*> g_boys_tabs;
@@ -506,16 +536,8 @@ const double* get_boys_table(int L, cudaStream_t s, int* err)
     auto key = std::make_pair(dev, L);
     auto it = g_boys_tabs.find(key);
     if (it != g_boys_tabs.end()) return it->second;
-    const int W = kBoysMtab + 2;
     std::vector<double> tab((size_t)kBoysGrid * 8);
-    long double fact[kBoysOrder];
-    fact[0] = 1;
-    for (int k = 1; k < kBoysOrder; ++k) fact[k] = fact[k - 1] * k;
-    for (int j = 0; j < kBoysGrid; ++j) {
-        const long double* row = &g_master_host[(size_t)j * W];
-        for (int k = 0; k < kBoysOrder; ++k) tab[(size_t)j * 8 + k] = (double)(row[L + k] / fact[k]);
-        tab[(size_t)j * 8 + 7] = (double)row[kBoysMtab + 1];
-    }
+    boys_taylor_rows(g_master_host.data(), L, tab.data());
     double* d = nullptr;
     if (cudaMalloc(&d, tab.size() * sizeof(double)) != cudaSuccess) {
         *err = ERI_ENOMEM;
