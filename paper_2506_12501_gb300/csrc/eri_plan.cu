@@ -32,6 +32,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <queue>
 #include <tuple>
 #include <vector>
 
@@ -94,6 +95,13 @@ struct eri_plan {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     eri::PlanParams params{};
+    // every work item of the plan (host copy, heaviest first) with its
+    // estimated cost, and the slice the device list currently holds
+    std::vector<eri::WorkItem> items;
+    std::vector<double> item_cost;
+    int32_t slice_rank = 0, slice_n = 1;
+    int64_t slice_q = 0;
+    double slice_cost = 0.0;
     // host copies for eri_plan_job / tests
     std::vector<std::vector<int32_t>> type_pairs;  // per type: sorted pairs [n][2]
     std::vector<std::vector<double>> type_q;       // per type: Schwarz factors (sorted)
@@ -618,6 +626,12 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
     p->d_items = dev_upload(items, p->owned, st, &err);
     if (err) return plan_fail(p, err);
     p->nitems = (int64_t)items.size();
+    p->item_cost.resize(items.size());
+    for (size_t i = 0; i < items.size(); ++i)
+        p->item_cost[i] = jcost[items[i].job] * (double)(items[i].k1 - items[i].k0);
+    p->slice_q = p->nquartets;
+    p->slice_cost = std::accumulate(p->item_cost.begin(), p->item_cost.end(), 0.0);
+    p->items = std::move(items);
     if (cudaMalloc(&p->d_params, sizeof(PlanParams)) != cudaSuccess ||
         cudaMalloc(&p->d_counter, 4 * sizeof(int)) != cudaSuccess)
         return plan_fail(p, ERI_ENOMEM);
@@ -728,7 +742,7 @@ extern "C" int eri_plan_info(eri_plan_t* p, int64_t* nquartets, int32_t* njobs, 
     if (!p) return ERI_EINVAL;
     if (nquartets) *nquartets = p->nquartets;
     if (njobs) *njobs = (int32_t)p->jobs.size();
-    if (nitems) *nitems = p->nitems;
+    if (nitems) *nitems = (int64_t)p->items.size();
     if (out_len) *out_len = p->out_len;
     return ERI_OK;
 }
@@ -761,6 +775,82 @@ extern "C" int eri_plan_job_degrees(eri_plan_t* p, int32_t j, int32_t* kbra, int
     if (!p || j < 0 || j >= (int32_t)p->jobs.size() || !kbra || !kket) return ERI_EINVAL;
     *kbra = p->jobs[j].args.KB;
     *kket = p->jobs[j].args.KK;
+    return ERI_OK;
+}
+
+extern "C" int eri_partition(const double* cost, int64_t n, int32_t nranks, int32_t* owner, double* load)
+{
+    if (n < 0 || nranks < 1 || (n > 0 && (!cost || !owner))) return ERI_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(cost[i] >= 0.0) || !std::isfinite(cost[i])) return ERI_EINVAL;
+    // longest processing time first: units by descending cost (ties keep
+    // their order), each to the least-loaded rank (the lowest rank on ties)
+    std::vector<int64_t> ord((size_t)n);
+    std::iota(ord.begin(), ord.end(), (int64_t)0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return cost[x] > cost[y]; });
+    using Slot = std::pair<double, int32_t>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int32_t r = 0; r < nranks; ++r) heap.push(Slot(0.0, r));
+    std::vector<double> ld((size_t)nranks, 0.0);
+    for (int64_t i : ord) {
+        Slot s = heap.top();
+        heap.pop();
+        owner[i] = s.second;
+        s.first += cost[i];
+        ld[(size_t)s.second] = s.first;
+        heap.push(s);
+    }
+    if (load)
+        for (int32_t r = 0; r < nranks; ++r) load[r] = ld[(size_t)r];
+    return ERI_OK;
+}
+
+extern "C" int eri_plan_set_slice(eri_plan_t* p, int32_t rank, int32_t nranks, void* stream)
+{
+    if (!p || nranks < 1 || rank < 0 || rank >= nranks) return ERI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = (int64_t)p->items.size();
+    std::vector<int32_t> owner((size_t)n, 0);
+    int rc = eri_partition(p->item_cost.data(), n, nranks, owner.data(), nullptr);
+    if (rc != ERI_OK) return rc;
+    // this rank's items, still heaviest first
+    std::vector<WorkItem> mine;
+    int64_t q = 0;
+    double c = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        if (owner[(size_t)i] == rank) {
+            mine.push_back(p->items[(size_t)i]);
+            q += p->items[(size_t)i].k1 - p->items[(size_t)i].k0;
+            c += p->item_cost[(size_t)i];
+        }
+    // the device list is the full list's buffer; earlier replays may still read it
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ERI_ECUDA;
+    if (!mine.empty() &&
+        cudaMemcpy(p->d_items, mine.data(), sizeof(WorkItem) * mine.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return ERI_ECUDA;
+    p->nitems = (int64_t)mine.size();
+    p->slice_rank = rank;
+    p->slice_n = nranks;
+    p->slice_q = q;
+    p->slice_cost = c;
+    // the graph holds the item count as a kernel argument: capture it again
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    if (p->graph) {
+        cudaGraphDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    return ERI_OK;
+}
+
+extern "C" int eri_plan_slice_info(eri_plan_t* p, int64_t* nitems, int64_t* nquartets, double* cost)
+{
+    if (!p) return ERI_EINVAL;
+    if (nitems) *nitems = p->nitems;
+    if (nquartets) *nquartets = p->slice_q;
+    if (cost) *cost = p->slice_cost;
     return ERI_OK;
 }
 

@@ -9,25 +9,18 @@ adds per-rank partial digests.
 """
 from __future__ import annotations
 
-import heapq
-
 import numpy as np
 
 
 def partition(costs, nranks: int) -> list[np.ndarray]:
-    """Indices of the units of each rank (LPT greedy on ``costs``)."""
-    costs = np.asarray(costs, dtype=np.float64)
+    """Indices of the units of each rank: the library's longest-processing-
+    time-first partition on ``costs`` (eri_partition, host only), the same
+    rule eri_plan_set_slice applies to a plan's work items."""
     if nranks < 1:
         raise ValueError("nranks must be >= 1")
-    order = np.argsort(-costs, kind="stable")
-    heap = [(0.0, r) for r in range(nranks)]
-    heapq.heapify(heap)
-    owner = np.empty(costs.size, dtype=np.int64)
-    for i in order:
-        load, r = heapq.heappop(heap)
-        owner[i] = r
-        heapq.heappush(heap, (load + costs[i], r))
-    return [np.sort(np.where(owner == r)[0]) for r in range(nranks)]
+    from .binding import partition as lpt
+    owner, _ = lpt(costs, nranks)
+    return [np.where(owner == r)[0] for r in range(nranks)]
 
 
 def allreduce_sum(value, dist, device=None):

@@ -344,3 +344,48 @@ def test_plan_full_size_sampled(cuda):
     assert plan.status() == eri.ERI_OK
     # the two sums take different orders over 1e7 quartets (atomics): relative round-off only
     assert abs(float(e.item()) - e_store) <= 1e-10 * max(1.0, abs(e_store)), (float(e.item()), e_store)
+
+
+def test_plan_slices_sum_to_whole_plan(cuda):
+    """Several ranks on one plan: the slices eri_plan_set_slice keeps for
+    ranks 0..n-1 partition the work items (their quartets add up to the
+    plan's), and their energies, J and K add up to the whole plan's, which
+    itself matches the oracle on the store form.  The slices run one after
+    another on one GPU (no rank waits on another)."""
+    basis = synth.molecule_basis(natom=4, radius=2.6, seed=8)
+    _, nbf = bf_offsets(basis)
+    U = np.random.default_rng(9).uniform(-1, 1, (nbf, nbf))
+    Dm = torch.as_tensor(np.triu(U) + np.triu(U, 1).T, device=cuda)
+    db = eri.DeviceBasis(basis)
+    plan = eri.Plan(db, threshold=1e-12)
+    info = plan.info()
+    e = torch.zeros(1, dtype=torch.float64, device=cuda)
+    plan.execute(D=Dm, energy=e)
+    J, K = plan.jk(Dm)
+    whole = (float(e.item()), J.clone(), K.clone())
+    for n in (2, 3):
+        tot_e, tot_q, tot_items = 0.0, 0, 0
+        tot_J = torch.zeros_like(Dm)
+        tot_K = torch.zeros_like(Dm)
+        for r in range(n):
+            plan.set_slice(r, n)
+            si = plan.slice_info()
+            assert si["nquartets"] > 0
+            tot_q += si["nquartets"]
+            tot_items += si["nitems"]
+            plan.execute(D=Dm, energy=e)
+            tot_e += float(e.item())
+            Jr, Kr = plan.jk(Dm)
+            tot_J += Jr
+            tot_K += Kr
+        assert tot_q == info["nquartets"] and tot_items == info["nitems"]
+        assert abs(tot_e - whole[0]) <= 1e-12 * max(1.0, abs(whole[0]))
+        assert float((tot_J - whole[1]).abs().max()) <= 1e-12 * float(whole[1].abs().max())
+        assert float((tot_K - whole[2]).abs().max()) <= 1e-12 * float(whole[2].abs().max())
+    plan.set_slice(0, 1)  # the whole plan again
+    assert plan.slice_info()["nquartets"] == info["nquartets"]
+    plan.execute(D=Dm, energy=e)
+    assert abs(float(e.item()) - whole[0]) <= 1e-13 * max(1.0, abs(whole[0]))
+    with pytest.raises(eri.EriError):
+        plan.set_slice(2, 2)
+    plan.destroy()

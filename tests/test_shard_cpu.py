@@ -10,6 +10,7 @@ import torch.multiprocessing as mp
 
 import oracle
 import synth
+import paper_2506_12501_gb300 as eri
 from paper_2506_12501_gb300 import opcount, shard
 
 
@@ -131,3 +132,63 @@ def test_two_rank_coulomb_matrix_equals_single_rank():
     J_single = Jp_single + Jp_single.T
     assert np.array_equal(J0, J1)
     assert np.abs(J0 - J_single).max() <= 1e-12 * np.abs(J_single).max()
+
+
+def _plan_items(basis, chunk=8):
+    """Work items shaped like a plan's: one bra pair and a run of at most
+    ``chunk`` of its kets within one class, costed like eri_plan_set_slice
+    (FP64 work per quartet times the item's quartet count)."""
+    pairs, batches = synth.all_unique_quartets(basis)
+    items, costs = [], []
+    for cls, (bra, ket, q) in batches.items():
+        qs = synth.quartet_shells(bra, ket, q)
+        for b in np.unique(q[:, 0]):
+            sel = np.where(q[:, 0] == b)[0]
+            for k0 in range(0, len(sel), chunk):
+                part = qs[sel[k0:k0 + chunk]]
+                Kb = basis.shell_K[part[0, 0]] * basis.shell_K[part[0, 1]]
+                Kk = basis.shell_K[part[:, 2]] * basis.shell_K[part[:, 3]]
+                items.append(part)
+                costs.append(sum(opcount.sparse_flops(cls, int(Kb), int(k)) for k in Kk))
+    return items, np.asarray(costs)
+
+
+def _item_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        basis = synth.molecule_basis(natom=2, radius=1.5, seed=5)
+        items, costs = _plan_items(basis)
+        nbf = int(((basis.shell_l + 1) * (basis.shell_l + 2) // 2).sum())
+        U = np.random.default_rng(3).uniform(-1, 1, (nbf, nbf))
+        D = np.triu(U) + np.triu(U, 1).T
+        owner, load = eri.partition(costs, world)
+        mine = [items[i] for i in np.where(owner == rank)[0]]
+        part = _energy(basis, np.concatenate(mine), D) if mine else 0.0
+        single = _energy(basis, np.concatenate(items), D) if rank == 0 else None
+        out[rank] = (shard.allreduce_sum(part, dist), sum(len(m) for m in mine), single, load.tolist(),
+                     float(costs.max()), len(items))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_plan_items_energy_equals_single_rank():
+    """The partition eri_plan_set_slice applies (the library's eri_partition,
+    called on the host) over plan-shaped work items of a molecule's screened
+    unique quartets: two gloo ranks digest their items with the oracle, one
+    all-reduce gives the single-rank energy, every quartet is counted once,
+    and the loads differ by at most the largest item cost."""
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    out = mp.get_context("spawn").Manager().dict()
+    mp.start_processes(_item_worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    total, single = out[0][0], out[0][2]
+    assert out[0][0] == out[1][0]
+    assert abs(total - single) <= 1e-12 * max(1.0, abs(single))
+    nq_total = sum(len(x) for x in _plan_items(synth.molecule_basis(natom=2, radius=1.5, seed=5))[0])
+    assert out[0][1] + out[1][1] == nq_total and out[0][1] > 0 and out[1][1] > 0
+    load, cmax = out[0][3], out[0][4]
+    assert abs(load[0] - load[1]) <= cmax
