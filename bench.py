@@ -1,16 +1,38 @@
-"""Benchmark of the GB300 MD ERI library on the class-sweep workload.
+"""Benchmark of the GB300 MD ERI library.
 
-One step = every class (la lb|lc ld) with l in {s, p, d} (81 classes), each a
-list-form batch of 1e5 contracted quartets (K = 3 per shell, even-tempered
-exponents 0.2*3^k, centres in a 12-bohr cube, pairs drawn from 2048 random
-pairs per side), all computed by eri_batch in FP64 and stored in HBM.
+Headline workload, one step: every class (la lb|lc ld) with l in {s, p, d}
+(81 classes), each a list-form batch of 1e5 contracted quartets (K = 3 per
+shell, even-tempered exponents 0.2*3^k, centres in a 12-bohr cube, pairs
+drawn from 2048 random pairs per side), all computed by eri_batch in FP64
+and stored in HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl library|reference]
+                  [--variants LIST|none] [--detail-out PATH]
 
-Prints one JSON line (rank 0).  Under torchrun every rank computes its own
-seeded copy of the sweep (weak scaling, no collective on the data path).
+Output: detail lines first (one JSON object each, with a "detail" key: the
+per-class rates, each measured variant, the arithmetic-throughput probes),
+then, LAST, one compact JSON line with the headline metric, the roofline of
+the dominant kernel, the CPU baseline, the end-to-end rate and the clocks.
+``--detail-out`` also writes every detail object into one JSON file.
+
+Variants, each at its stated size and timed against the plain FP64 per-class
+kernel on the same GPU:
+  split        (dd|dd), (ff|ff), (ff|dd), K = 1 and 5 per shell, 1e5 quartets
+               each, exponents log-uniform in [0.05, 50]: FP64 against FP32
+               hi+lo transforms, error of both against the oracle on a sample;
+  adjoint      all 1.08e7 unique quartets of 16 atoms (s x3 K=6,3,1, p x2
+               K=3,1, d K=1), W = D_ab D_cd: forward and gradient times;
+  batched      64 atoms, Schwarz 1e-12, energy digestion in one persistent
+               graph-replayed launch (partitioned over ranks under torchrun);
+               J and J + K on the 16-atom plan;
+  threecentre  (x|cd), x a real solid harmonic, 24 classes x 1e5 triples;
+  peaks        FP64 FMA, FP64 MMA and FP32 FMA throughput probes.
+
+Under torchrun every rank computes its own seeded copy of the class sweep
+(weak scaling, no collective on the data path); the batched variant splits
+one plan's work items over the ranks and all-reduces the energy.
 ``--impl reference`` times the CPU oracle (oracle/, double build) on a
-bounded sample of the same workload instead.
+bounded sample of the class sweep instead.
 """
 from __future__ import annotations
 
@@ -37,10 +59,23 @@ UNIT = "quartets/s"
 NQ_PER_CLASS = 100_000
 K_PER_SHELL = 3
 POOL, NPAIRS = 512, 2048
-# FP64 FMA pipe of one GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+# FP64 FMA pipe of one GB300 from unit counts and the maximum clock:
+# 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 L2_BYTES = 129 * 1024 * 1024
 WORKLOAD = "class-sweep: 81 classes (l<=2), K=3 per shell, 1e5 quartets/class, FP64"
+ALL_VARIANTS = ("peaks", "split", "adjoint", "batched", "threecentre")
+
+DETAILS: list = []
+
+
+def emit_detail(name, obj, rank=0):
+    """Print one detail object (rank 0) and keep it for --detail-out."""
+    if rank != 0:
+        return
+    d = {"detail": name, **obj}
+    DETAILS.append(d)
+    print(json.dumps(d), flush=True)
 
 
 def classes():
@@ -57,13 +92,16 @@ def sweep(seed, only=None, nq=NQ_PER_CLASS):
 # --------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------
-def oracle_sweep_rate(basis, batches, budget_s=18.0, threads=None):
-    """Quartets/s of the CPU oracle (double build, as it stands) on the sweep,
-    extrapolated from a bounded per-class sample."""
+def oracle_sweep_rate(basis, batches, budget_s=12.0, threads=None):
+    """The CPU oracle (double build, as it stands) on a bounded sample of the
+    sweep: per class a leading slice of its quartets sized to about
+    budget_s / 81 seconds on `threads` host threads.  Returns (rate over the
+    sweep's class mix in quartets/s, threads, quartets sampled, seconds spent
+    in the timed oracle calls)."""
     import oracle
     threads = threads or (os.cpu_count() or 1)
     per_class = budget_s / len(batches)
-    total_time, total_q, sampled = 0.0, 0, 0
+    total_time, total_q, sampled, spent = 0.0, 0, 0, 0.0
     for cls, (bra, ket, q) in batches.items():
         qs = synth.quartet_shells(bra, ket, q[:1])
         t0 = time.perf_counter()
@@ -75,10 +113,11 @@ def oracle_sweep_rate(basis, batches, budget_s=18.0, threads=None):
         t0 = time.perf_counter()
         oracle.eri_quartets(basis, qs, prec="d", threads=threads)
         dt = time.perf_counter() - t0
+        spent += dt
         total_time += dt / n * q.shape[0]
         total_q += q.shape[0]
         sampled += n
-    return total_q / total_time, threads, sampled
+    return total_q / total_time, threads, sampled, spent
 
 
 def run_reference(args):
@@ -88,26 +127,33 @@ def run_reference(args):
     import oracle
     oracle.build()
     basis, batches = sweep(0)
+    # each step a bounded sample sized so that the whole run takes a few minutes
+    budget = args.ref_budget or min(18.0, max(3.0, 150.0 / (args.steps + 0.25 * args.warmup)))
     for _ in range(args.warmup):
-        oracle_sweep_rate(basis, batches, budget_s=args.ref_budget / 4)
-    vals = []
-    t0 = time.perf_counter()
+        oracle_sweep_rate(basis, batches, budget_s=budget / 4)
+    vals, walls = [], []
+    sampled = cores = 0
     for _ in range(args.steps):
-        v, cores, sampled = oracle_sweep_rate(basis, batches, budget_s=args.ref_budget)
+        t0 = time.perf_counter()
+        v, cores, sampled, _ = oracle_sweep_rate(basis, batches, budget_s=budget)
+        walls.append(time.perf_counter() - t0)
         vals.append(v)
-    wall = time.perf_counter() - t0
     value = statistics.median(vals)
+    full_step_ms = 1e3 * len(batches) * NQ_PER_CLASS / value
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(batches) * NQ_PER_CLASS / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "classes": len(batches), "quartets_per_class": NQ_PER_CLASS,
                    "K_per_shell": K_PER_SHELL},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{sampled} quartets per step spread over all 81 classes, "
-                                   f"~{args.ref_budget:.0f} s of CPU work per step, extrapolated to 1e5/class"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_s": wall,
+                         "sample": f"{sampled} quartets per step spread over all 81 classes (~{budget:.1f} s of "
+                                   f"oracle work per step on {cores} threads); value = the sweep's class mix at "
+                                   f"the sampled per-class rates"},
+        "ms_per_step_note": "wall time of one sampled step; the full 8.1e6-quartet step would take "
+                            f"{full_step_ms / 1e3:.0f} s at this rate",
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "the oracle reads and writes host memory: no copies"},
     }
     print(json.dumps(line), flush=True)
 
@@ -151,7 +197,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -160,6 +206,7 @@ class ClockSampler:
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 continue
             for n, v in zip(names, f[5:9]):
@@ -168,7 +215,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_max": max(pw) if pw else None}
 
 
 KERNEL_SOURCES = ("eri_fwd.cu", "eri_tile.cuh", "eri_device.cuh", "eri_internal.h", "eri_tables.cu")
@@ -183,8 +230,10 @@ def kernel_source_sha():
 
 
 def profile_traffic():
-    """DRAM traffic per launch of the forward kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    """DRAM bytes per fwd_kernel launch of the full sweep, from the committed
+    ncu summary, if it was taken on the current kernel source (else None).
+    The summary holds the traffic of a small case (5000 quartets per class)
+    scaled to 1e5 quartets per class."""
     path = os.path.join(ROOT, "profiles", "fwd_kernel_class_sweep.md")
     try:
         text = open(path).read()
@@ -192,7 +241,7 @@ def profile_traffic():
     except OSError:
         return None
     m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"dram_bytes_per_launch_avg:\s*([0-9.eE+]+)", text)
+    t = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != sha:
         return None
     return float(t.group(1))
@@ -211,58 +260,231 @@ def job_rate(world, quartets_per_rank_step, steps, max_ms):
     return world * quartets_per_rank_step * steps / (max_ms / 1e3)
 
 
-def run_variants(args, eri, dev):
-    """The split-precision, adjoint and batched forms, each timed against the
-    plain FP64 per-class kernels on the same GPU (bounded sizes; see config)."""
+def timed(fn, reps=1, warm=True):
+    """Fastest of `reps` CUDA-event timings (ms) of fn on the current stream."""
     import torch
-
-    def timed(fn, reps=2):
+    if warm:
         fn()
         torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            b.record()
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return min(ts)
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return min(ts)
 
+
+def oracle_sample_error(cls, basis, bra, ket, q, outs, n, seed=5):
+    """Max |x - oracle| of each list-form output in `outs` on n seeded quartets."""
+    import oracle
+    nab = synth_nc(cls[0]) * synth_nc(cls[1])
+    ncd = synth_nc(cls[2]) * synth_nc(cls[3])
+    pick = np.sort(np.random.default_rng(seed).choice(len(q), n, replace=False))
+    ref = oracle.eri_quartets(basis, synth.quartet_shells(bra, ket, q[pick]), prec="d",
+                              threads=os.cpu_count() or 1).reshape(n, nab * ncd)
+    errs = []
+    for o in outs:
+        got = o.view(nab * ncd, len(q))[:, pick].T.cpu().numpy()
+        errs.append(float(np.abs(got - ref).max()))
+    return errs, float(np.abs(ref).max())
+
+
+def synth_nc(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def peaks_variant(eri):
     out = {}
-    which = set(args.variants.split(",")) if args.variants else {"split", "adjoint", "batched", "threecentre"}
-    # split precision on the high-l workload
-    split = {}
-    for cls in ([(2, 2, 2, 2), (3, 3, 3, 3), (3, 3, 2, 2)] if "split" in which else []):
-        for K, nq in ((1, 100_000), (5, args.split_nq_k5)):
+    for name, kind in (("dfma", eri.PEAK_DFMA), ("dmma", eri.PEAK_DMMA), ("ffma", eri.PEAK_FFMA)):
+        g, mhz = eri.eri_peak_probe(kind)
+        out[name] = {"gflops": g, "sm_mhz": mhz}
+    out["dfma_per_clk_per_sm"] = out["dfma"]["gflops"] * 1e9 / 2 / (out["dfma"]["sm_mhz"] * 1e6) / 152
+    out["dfma_gflops_at_max_clock"] = out["dfma"]["gflops"] * 2070.0 / out["dfma"]["sm_mhz"]
+    return out
+
+
+def split_variant(args, eri, dev):
+    """(dd|dd), (ff|ff), (ff|dd) at K = 1 and 5 per shell, 1e5 quartets each:
+    FP64 and split-precision transforms, each timed once after a warm-up
+    call on a leading slice (form choice and tile tuning), and both compared
+    with the oracle on a seeded sample."""
+    import torch
+    from paper_2506_12501_gb300 import opcount
+    res = {}
+    for cls in ((2, 2, 2, 2), (3, 3, 3, 3), (3, 3, 2, 2)):
+        for K in (1, 5):
+            nq = args.split_nq
             basis, bra, ket, q = synth.split_batch(cls, K=K, seed=0, nq=nq)
             db = eri.DeviceBasis(basis)
             b = torch.as_tensor(bra, device=dev)
             k = torch.as_tensor(ket, device=dev)
             qq = torch.as_tensor(q, device=dev)
+            warm = qq[: min(nq, 20_000)].contiguous()
             o64 = torch.empty(eri.out_len(cls, len(bra), len(ket), nq), dtype=torch.float64, device=dev)
             osp = torch.empty_like(o64)
-            t64 = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o64))
-            tsp = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=osp, precision=eri.ERI_PREC_SPLIT))
-            err = float((osp - o64).abs().max())
-            split["".join(map(str, cls)) + f"_K{K}"] = {
-                "quartets": nq, "fp64_ms": t64, "split_ms": tsp, "speedup": t64 / tsp,
+            ow = torch.empty(eri.out_len(cls, len(bra), len(ket), warm.shape[0]), dtype=torch.float64, device=dev)
+            eri.eri_batch(cls, db, b, k, warm, out=ow)
+            t64 = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o64), warm=False)
+            f64form = eri.eri_last_form()
+            eri.eri_batch(cls, db, b, k, warm, out=ow, precision=eri.ERI_PREC_SPLIT)
+            tsp = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=osp, precision=eri.ERI_PREC_SPLIT), warm=False)
+            del ow
+            nsamp = 2 if (cls == (3, 3, 3, 3) and K == 5) else (4 if K == 5 else 16)
+            (e64, esp), refmax = oracle_sample_error(cls, basis, bra, ket, q, [o64, osp], nsamp)
+            flops = opcount.sparse_flops(cls, K * K, K * K, form=f64form) * nq
+            res["".join(map(str, cls)) + f"_K{K}"] = {
+                "quartets": nq, "fp64_ms": round(t64, 3), "split_ms": round(tsp, 3), "speedup": t64 / tsp,
                 "fp64_quartets_per_s": nq / (t64 / 1e3), "split_quartets_per_s": nq / (tsp / 1e3),
-                "max_abs_err_vs_fp64": err, "max_abs_fp64": float(o64.abs().max())}
+                "fp64_gflops_sparse": flops / (t64 / 1e3) / 1e9,
+                "fp64_frac_fp64_peak": flops / (t64 / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
+                "max_abs_split_vs_fp64": float((osp - o64).abs().max()),
+                "oracle_sample": nsamp, "max_abs_fp64_vs_oracle": e64, "max_abs_split_vs_oracle": esp,
+                "max_abs_oracle_sample": refmax}
             del o64, osp
-    if split:
-        out["split"] = split
-    if "adjoint" in which:
-        out["adjoint"] = adjoint_variant(args, eri, dev, timed)
-    if "batched" in which:
-        out["batched"] = batched_variant(args, eri, dev, timed)
-    if "threecentre" in which:
-        out["threecentre"] = three_centre_variant(args, eri, dev, timed)
-    return out
+            torch.cuda.empty_cache()
+    return {"workload": f"(dd|dd), (ff|ff), (ff|dd); K = 1 and 5 per shell; {args.split_nq} quartets each; "
+                        "exponents 10^U(log 0.05, log 50); centres U[0,12]^3", "per_class": res}
 
 
-def three_centre_variant(args, eri, dev, timed):
+def adjoint_variant(args, eri, dev):
+    """The adjoint over every unique quartet of the 16-atom molecule-shaped
+    basis (1.08e7 quartets, all classes), W = D_ab D_cd: the forward pass and
+    the gradient pass timed over all classes, after one warm-up pass."""
+    import torch
+    from paper_2506_12501_gb300 import opcount
+    basis, D, bf_off = synth.adjoint_workload(natom=16, radius=4.4, seed=0)
+    pairs, batches = synth.all_unique_quartets(basis)
+    db = eri.DeviceBasis(basis)
+    data = []
+    gflop = fflop = 0.0
+    for cls, (bra, ket, q) in batches.items():
+        if args.adjoint_nq:
+            q = q[: args.adjoint_nq]
+        W = synth.density_weights(cls, bra, ket, q, D, bf_off)
+        t = [torch.as_tensor(x, device=dev) for x in (bra, ket, q, W)]
+        o = torch.empty(W.size, dtype=torch.float64, device=dev)
+        Ks = basis.shell_K
+        kb = (Ks[bra[q[:, 0], 0]] * Ks[bra[q[:, 0], 1]]).astype(np.int64)
+        kk = (Ks[ket[q[:, 1], 0]] * Ks[ket[q[:, 1], 1]]).astype(np.int64)
+        sig = np.unique(np.stack([kb, kk], 1), axis=0, return_counts=True)
+        data.append((cls, t, o, sig, len(q)))
+    gc = torch.zeros_like(db.centres)
+    ge = torch.zeros_like(db.exps)
+
+    def fwd():
+        for cls, (b, k, qq, W), o, _, _ in data:
+            eri.eri_batch(cls, db, b, k, qq, out=o)
+
+    forms = {}
+
+    def grad():
+        for cls, (b, k, qq, W), o, _, _ in data:
+            eri.eri_batch_grad(cls, db, b, k, qq, W, gc, ge)
+            forms[cls] = eri.eri_last_grad_forms()
+
+    t_f = timed(fwd)
+    t_g = timed(grad)
+    nq_tot = sum(d[4] for d in data)
+    for cls, _, _, (keys, counts), _ in data:
+        for (x, y), n in zip(keys, counts):
+            gflop += n * opcount.grad_flops(cls, int(x), int(y), forms[cls])
+            fflop += n * opcount.sparse_flops(cls, int(x), int(y), form=(False, False))
+    # kernel time of the adjoint launches, pair tables and prepass (library events)
+    torch.cuda.synchronize()
+    eri.eri_profile_read()
+    eri.eri_profile_enable(True)
+    grad()
+    torch.cuda.synchronize()
+    eri.eri_profile_enable(False)
+    prof = eri.eri_profile_read()
+    kms = prof[eri.PROF_GRAD][1]
+    return {"workload": f"16-atom molecule basis, {len(batches)} classes, {nq_tot} unique quartets, "
+                        "W = D_ab D_cd", "quartets": nq_tot, "fwd_ms": t_f, "grad_ms": t_g,
+            "grad_over_fwd": t_g / t_f, "fwd_quartets_per_s": nq_tot / (t_f / 1e3),
+            "grad_quartets_per_s": nq_tot / (t_g / 1e3),
+            "grad_gflops_sparse": gflop / (t_g / 1e3) / 1e9,
+            "grad_frac_fp64_peak_sparse": gflop / (t_g / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
+            "grad_kernel_ms": kms, "grad_pair_tables_ms": prof[eri.PROF_PAIR][1],
+            "grad_prepass_ms": prof[eri.PROF_PREPASS][1],
+            "grad_kernel_frac_fp64_peak_sparse": gflop / (kms / 1e3) / 1e9 / FP64_PEAK_GFLOPS if kms > 0 else None,
+            "fwd_frac_fp64_peak_sparse_plain": fflop / (t_f / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
+            "grad_forms": {"".join(map(str, c)): "".join("XV"[f] for f in v) for c, v in forms.items()}}
+
+
+def batched_variant(args, eri, dev, world, rank, dist):
+    """The screened molecule-shaped workload in one persistent graph launch;
+    with several ranks each executes its slice of the plan and the energy is
+    all-reduced."""
+    import torch
+    from paper_2506_12501_gb300 import opcount
+
+    def make(natom):
+        mb = synth.molecule_basis(natom=natom, radius=7.0 * (natom / 64) ** (1 / 3), seed=0)
+        mdb = eri.DeviceBasis(mb)
+        nbf = int(((mb.shell_l + 1) * (mb.shell_l + 2) // 2).sum())
+        U = np.random.default_rng(2).uniform(-1, 1, (nbf, nbf))
+        Dm = torch.as_tensor(np.triu(U) + np.triu(U, 1).T, device=dev)
+        t0 = time.perf_counter()
+        plan = eri.Plan(mdb, threshold=1e-12)
+        torch.cuda.synchronize()
+        return mdb, Dm, plan, time.perf_counter() - t0
+
+    natom = args.molecule_natom
+    mdb, Dm, plan, t_create = make(natom)
+    info = plan.info()
+    if world > 1:
+        plan.set_slice(rank, world)
+    sl = plan.slice_info()
+    flops = 0.0
+    for j in range(info["njobs"]):
+        cls, nq, _, _ = plan.job(j)
+        kb, kk = plan.job_degrees(j)
+        flops += nq * opcount.sparse_flops(cls, kb, kk, form=(False, False))
+    e = torch.zeros(1, dtype=torch.float64, device=dev)
+    plan.execute(D=Dm, energy=e)  # graph capture, outside the timed run
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed replay
+    t_exec = timed(lambda: plan.execute(D=Dm, energy=e), warm=False)
+    torch.cuda.profiler.stop()
+    energy = float(e.item())
+    if world > 1:
+        t_exec = reduce_max(t_exec, dist, dev)
+        et = torch.tensor([energy], dtype=torch.float64, device=dev)
+        dist.all_reduce(et)
+        energy = float(et.item())
+    res = {"workload": f"{natom} atoms (s x3 K=6,3,1, p x2 K=3,1, d K=1), Schwarz 1e-12, energy digestion, "
+                       f"one persistent graph-replayed launch" + (f", work items split over {world} ranks + "
+                                                                  "one all-reduce" if world > 1 else ""),
+           "quartets": info["nquartets"], "jobs": info["njobs"], "work_items": info["nitems"],
+           "slice_quartets_rank0": sl["nquartets"], "create_s": t_create, "execute_ms": t_exec,
+           "quartets_per_s": info["nquartets"] / (t_exec / 1e3), "energy": energy,
+           "gflops_sparse": flops / (t_exec / 1e3) / 1e9,
+           "frac_fp64_peak_sparse": flops / (t_exec / 1e3) / 1e9 / FP64_PEAK_GFLOPS / world,
+           "status": plan.status()}
+    plan.destroy()
+    if world == 1:
+        # J and J + K, and the energy again, on the 16-atom plan
+        mdb, Dm, plan, _ = make(16)
+        info16 = plan.info()
+        e16 = torch.zeros(1, dtype=torch.float64, device=dev)
+        t_e = timed(lambda: plan.execute(D=Dm, energy=e16), reps=3)
+        J = torch.empty_like(Dm)
+        t_j = timed(lambda: plan.coulomb(Dm, J), reps=3)
+        K = torch.empty_like(Dm)
+        t_jk = timed(lambda: plan.jk(Dm, J=J, K=K), reps=3)
+        res["atoms16"] = {"quartets": info16["nquartets"], "energy_ms": t_e, "coulomb_ms": t_j, "jk_ms": t_jk,
+                          "energy_quartets_per_s": info16["nquartets"] / (t_e / 1e3)}
+        plan.destroy()
+    return res
+
+
+def three_centre_variant(args, eri, dev):
     """3-centre integrals (x|cd), x a real solid harmonic: uncontracted
     auxiliary shells lx <= 3 against the class-sweep orbital pairs (K = 3),
     1e5 triples per class; the form (side order) each class ran and its FP64
@@ -271,7 +493,7 @@ def three_centre_variant(args, eri, dev, timed):
     from paper_2506_12501_gb300 import opcount
     basis, orb, aux = synth.three_centre_pools(seed=0, pool=512)
     db = eri.DeviceBasis(basis)
-    per, tot_ms, tot_flops, tot_n = {}, 0.0, 0.0, 0
+    tot_ms, tot_flops, tot_n = 0.0, 0.0, 0
     for lx in range(4):
         nterms = int(np.count_nonzero(np.abs(eri.solid_harmonics(lx)) > 1e-14))
         for lc, ld in ((0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)):
@@ -280,123 +502,14 @@ def three_centre_variant(args, eri, dev, timed):
             o = torch.empty(len(t) * (2 * lx + 1) * eri.nc(lc) * eri.nc(ld), dtype=torch.float64, device=dev)
             ms = timed(lambda: eri.eri_batch3(lx, lc, ld, db, xd, kd, td, pure=True, out=o), reps=2)
             sw, _ = eri.eri_last_form()
-            f = opcount.sparse_flops3((lx, lc, ld), 1, 9, True, sw, nterms) * len(t)
-            per[f"{lx}{lc}{ld}"] = {"ms": ms, "form": "swapped" if sw else "plain",
-                                    "triples_per_s": len(t) / (ms / 1e3), "gflops_sparse": f / (ms / 1e3) / 1e9}
             tot_ms += ms
-            tot_flops += f
+            tot_flops += opcount.sparse_flops3((lx, lc, ld), 1, 9, True, sw, nterms) * len(t)
             tot_n += len(t)
     return {"workload": f"x real solid harmonics lx <= 3 (K = 1, exponents 10^U(-1,1)) x orbital pairs l <= 2 "
                         f"(K = 3), 24 classes x {args.three_nt} triples",
             "triples": tot_n, "ms": tot_ms, "triples_per_s": tot_n / (tot_ms / 1e3),
             "gflops_sparse": tot_flops / (tot_ms / 1e3) / 1e9,
-            "frac_fp64_peak_sparse": tot_flops / (tot_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, "per_class": per}
-
-
-def adjoint_variant(args, eri, dev, timed):
-    """The adjoint on the 16-atom molecule-shaped basis, a sample of every class."""
-    import torch
-    basis, D, bf_off = synth.adjoint_workload(natom=16, radius=4.4, seed=0)
-    pairs, batches = synth.all_unique_quartets(basis)
-    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees this variant too
-    db = eri.DeviceBasis(basis)
-    from paper_2506_12501_gb300 import opcount
-    tf = tg = 0.0
-    gflop = 0.0
-    nq_tot = 0
-    per = {}
-    kern = {eri.PROF_GRAD: 0.0, eri.PROF_PAIR: 0.0, eri.PROF_PREPASS: 0.0}
-    for cls, (bra, ket, q) in batches.items():
-        q = q[: args.adjoint_nq]
-        W = synth.density_weights(cls, bra, ket, q, D, bf_off)
-        b = torch.as_tensor(bra, device=dev)
-        k = torch.as_tensor(ket, device=dev)
-        qq = torch.as_tensor(q, device=dev)
-        Wd = torch.as_tensor(W, device=dev)
-        o = torch.empty(W.size, dtype=torch.float64, device=dev)
-        gc = torch.zeros_like(db.centres)
-        ge = torch.zeros_like(db.exps)
-        t_f = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o), reps=1)
-        t_g = timed(lambda: eri.eri_batch_grad(cls, db, b, k, qq, Wd, gc, ge), reps=1)
-        gforms = eri.eri_last_grad_forms()
-        # the same call once more under the library's launch events: kernel time
-        # of the two adjoint launches, of the pair tables and of the prepass
-        torch.cuda.synchronize()
-        eri.eri_profile_read()
-        eri.eri_profile_enable(True)
-        eri.eri_batch_grad(cls, db, b, k, qq, Wd, gc, ge)
-        torch.cuda.synchronize()
-        eri.eri_profile_enable(False)
-        for kid, (_, ms) in eri.eri_profile_read().items():
-            if kid in kern:
-                kern[kid] += ms
-        tf += t_f
-        tg += t_g
-        per["".join(map(str, cls))] = {"quartets": len(q), "fwd_ms": t_f, "grad_ms": t_g,
-                                       "grad_forms": "".join("XV"[f] for f in gforms)}
-        nq_tot += len(q)
-        Ks = basis.shell_K
-        kb = (Ks[bra[q[:, 0], 0]] * Ks[bra[q[:, 0], 1]]).astype(np.int64)
-        kk = (Ks[ket[q[:, 1], 0]] * Ks[ket[q[:, 1], 1]]).astype(np.int64)
-        for (x, y), n in zip(*np.unique(np.stack([kb, kk], 1), axis=0, return_counts=True)):
-            gflop += n * opcount.grad_flops(cls, int(x), int(y), gforms)
-    torch.cuda.profiler.stop()
-    return {"workload": f"16-atom molecule basis, {len(batches)} classes, <= {args.adjoint_nq} "
-                        "quartets per class", "quartets": nq_tot, "fwd_ms": tf, "grad_ms": tg,
-            "grad_over_fwd": tg / tf, "grad_quartets_per_s": nq_tot / (tg / 1e3),
-            "grad_gflops_sparse": gflop / (tg / 1e3) / 1e9,
-            "grad_frac_fp64_peak_sparse": gflop / (tg / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
-            "grad_kernel_ms": kern[eri.PROF_GRAD], "grad_pair_tables_ms": kern[eri.PROF_PAIR],
-            "grad_prepass_ms": kern[eri.PROF_PREPASS],
-            "grad_kernel_frac_fp64_peak_sparse": gflop / (kern[eri.PROF_GRAD] / 1e3) / 1e9 / FP64_PEAK_GFLOPS
-            if kern[eri.PROF_GRAD] > 0 else None, "per_class": per}
-
-
-def batched_variant(args, eri, dev, timed):
-    """The screened molecule-shaped workload in one persistent graph launch."""
-    import torch
-    mb = synth.molecule_basis(natom=args.molecule_natom, radius=7.0 * (args.molecule_natom / 64) ** (1 / 3), seed=0)
-    mdb = eri.DeviceBasis(mb)
-    nbf = int(((mb.shell_l + 1) * (mb.shell_l + 2) // 2).sum())
-    rng = np.random.default_rng(2)
-    U = rng.uniform(-1, 1, (nbf, nbf))
-    Dm = torch.as_tensor(np.triu(U) + np.triu(U, 1).T, device=dev)
-    t0 = time.perf_counter()
-    plan = eri.Plan(mdb, threshold=1e-12)
-    torch.cuda.synchronize()
-    t_create = time.perf_counter() - t0
-    info = plan.info()
-    # FP64 operations of the plan's jobs (plain forms, each job's own orientation)
-    from paper_2506_12501_gb300 import opcount
-    flops = 0.0
-    for j in range(info["njobs"]):
-        cls, nq, _, _ = plan.job(j)
-        kb, kk = plan.job_degrees(j)
-        flops += nq * opcount.sparse_flops(cls, kb, kk, form=(False, False))
-    e = torch.zeros(1, dtype=torch.float64, device=dev)
-    plan.execute(D=Dm, energy=e)  # graph capture outside the profiled region
-    torch.cuda.synchronize()
-    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed replays
-    t_exec = timed(lambda: plan.execute(D=Dm, energy=e), reps=2)
-    torch.cuda.profiler.stop()
-    J = torch.empty_like(Dm)
-    t_j = timed(lambda: plan.coulomb(Dm, J), reps=2)
-    K = torch.empty_like(Dm)
-    t_jk = timed(lambda: plan.jk(Dm, J=J, K=K), reps=2)
-    res = {"workload": f"{args.molecule_natom} atoms (s x3 K=6,3,1, p x2 K=3,1, d K=1), Schwarz 1e-12, "
-                       "energy digestion, one persistent graph-captured launch",
-           "quartets": info["nquartets"], "jobs": info["njobs"], "work_items": info["nitems"],
-           "create_s": t_create, "execute_ms": t_exec,
-           "quartets_per_s": info["nquartets"] / (t_exec / 1e3), "energy": float(e.item()),
-           "gflops_sparse": flops / (t_exec / 1e3) / 1e9,
-           "frac_fp64_peak_sparse": flops / (t_exec / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
-           "coulomb_ms": t_j, "coulomb_quartets_per_s": info["nquartets"] / (t_j / 1e3),
-           "coulomb_trace_DJ": float((Dm * J).sum().item()),
-           "jk_ms": t_jk, "jk_quartets_per_s": info["nquartets"] / (t_jk / 1e3),
-           "exchange_trace_DK": float((Dm * K).sum().item()),
-           "status": plan.status()}
-    plan.destroy()
-    return res
+            "frac_fp64_peak_sparse": tot_flops / (tot_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS}
 
 
 def run_library(args):
@@ -485,11 +598,14 @@ def run_library(args):
         ms = statistics.median(a.elapsed_time(b) for a, b in timing[cls])
         qps = nq_class / (ms / 1e3)
         per_class["".join(map(str, cls))] = {
-            "ms": round(ms, 4), "quartets_per_s": qps,
+            "ms": round(ms, 4), "qps": round(qps),
             "form": ("swapped " if forms[cls][0] else "") + ("hrr" if forms[cls][1] else "plain"),
-            "gflops_sparse": sparse[cls] * qps / 1e9, "gflops_dense": dense[cls] * qps / 1e9,
-            "frac_fp64_peak_sparse": sparse[cls] * qps / 1e9 / FP64_PEAK_GFLOPS,
-            "frac_fp64_peak_dense": dense[cls] * qps / 1e9 / FP64_PEAK_GFLOPS}
+            "gflops": round(sparse[cls] * qps / 1e9, 1),
+            "frac": round(sparse[cls] * qps / 1e9 / FP64_PEAK_GFLOPS, 4),
+            "frac_dense": round(dense[cls] * qps / 1e9 / FP64_PEAK_GFLOPS, 4)}
+    emit_detail("per_class", {"note": "qps = quartets/s; gflops and frac from the sparse FP64 count of the form "
+                                      "that ran; frac_dense from the dense-GEMM count",
+                              "per_class": per_class, "step_ms": [round(x, 3) for x in step_ms]}, rank)
     fwd_launches, fwd_ms = prof[eri.PROF_FWD]
     flops_per_step = sum(sparse[c] * nq_class for c in batches)
     dense_per_step = sum(dense[c] * nq_class for c in batches)
@@ -497,15 +613,14 @@ def run_library(args):
     roofline = {"bound": "alu", "kernel": "fwd_kernel", "achieved": fwd_gflops, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "frac": (fwd_gflops / FP64_PEAK_GFLOPS) if fwd_gflops else None,
                 "traffic": profile_traffic(),
-                "peak_source": "FP64 FMA pipe, 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock); "
-                               "a DFMA microbenchmark measured 1.20 TFLOP/s at 1.99 GHz",
-                "flops_counted": "FP64 operations of the implemented sparse MD sequence (FMA=2)",
-                "fwd_launches": fwd_launches, "fwd_ms_per_launch": fwd_ms / max(fwd_launches, 1),
-                "gflops_dense_formulation": dense_per_step * args.steps / (fwd_ms / 1e3) / 1e9 if fwd_ms else None,
-                "frac_dense_formulation": (dense_per_step * args.steps / (fwd_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS)
-                if fwd_ms else None,
-                "other_kernels_ms_per_step": {"pair": prof[eri.PROF_PAIR][1] / args.steps,
-                                              "prepass": prof[eri.PROF_PREPASS][1] / args.steps}}
+                "peak_source": "derived: FP64 FMA pipe, 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "flops": "sparse FP64 count of the implemented sequence, FMA = 2",
+                "ms_per_launch": round(fwd_ms / max(fwd_launches, 1), 4),
+                "frac_dense_formulation": round(dense_per_step * args.steps / (fwd_ms / 1e3) / 1e9 /
+                                                FP64_PEAK_GFLOPS, 3) if fwd_ms else None}
+    emit_detail("roofline_other_kernels", {"pair_ms_per_step": prof[eri.PROF_PAIR][1] / args.steps,
+                                           "prepass_ms_per_step": prof[eri.PROF_PREPASS][1] / args.steps,
+                                           "fwd_launches": fwd_launches}, rank)
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -555,36 +670,64 @@ def run_library(args):
             if it > 0:
                 e_ms.append(a0.elapsed_time(a1))
         e2e = {"value": world * nq_step / (statistics.median(e_ms) / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": len(e_ms),
-               "step_ms": [round(x, 2) for x in e_ms]}
-
-    variants = None
-    if rank == 0 and not args.no_variants and (only is None or args.variants):
-        variants = run_variants(args, eri, dev)
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": len(e_ms)}
+        emit_detail("e2e", {"step_ms": [round(x, 2) for x in e_ms]}, rank)
+        del host_in, host_out
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sampled = oracle_sweep_rate(basis, batches, budget_s=args.ref_budget)
+        v, cores, sampled, spent = oracle_sweep_rate(basis, batches, budget_s=args.cpu_budget)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{sampled} quartets over all 81 classes (~{args.ref_budget:.0f} s of CPU work, "
-                         f"double build of the oracle on {cores} host threads), extrapolated to 1e5/class"}
+               "sample": f"{sampled} quartets over all 81 classes ({spent:.0f} s of oracle work, double build, "
+                         f"{cores} host threads); value = the sweep's class mix at the sampled per-class rates"}
+
+    # ---- variants (each at its stated size)
+    which = ALL_VARIANTS if args.variants is None else tuple(v for v in args.variants.split(",") if v and v != "none")
+    summary = {}
+    del outs, dev_batches, flush
+    torch.cuda.empty_cache()
+    if only is None or args.variants:
+        if "peaks" in which and rank == 0:
+            p = peaks_variant(eri)
+            emit_detail("peaks", p, rank)
+            summary["dfma_measured_gflops"] = round(p["dfma"]["gflops"], 1)
+        if "split" in which and rank == 0 and world == 1:
+            s = split_variant(args, eri, dev)
+            emit_detail("split", s, rank)
+            summary["split_speedup"] = {k: round(v["speedup"], 2) for k, v in s["per_class"].items()}
+        if "adjoint" in which and rank == 0 and world == 1:
+            a = adjoint_variant(args, eri, dev)
+            emit_detail("adjoint", a, rank)
+            summary["adjoint"] = {"grad_over_fwd": round(a["grad_over_fwd"], 2),
+                                  "grad_frac": round(a["grad_frac_fp64_peak_sparse"], 3),
+                                  "grad_qps": round(a["grad_quartets_per_s"])}
+        if "batched" in which:
+            bv = batched_variant(args, eri, dev, world, rank, dist)
+            emit_detail("batched", bv, rank)
+            summary["batched"] = {"natom": args.molecule_natom, "qps": round(bv["quartets_per_s"]),
+                                  "frac": round(bv["frac_fp64_peak_sparse"], 3)}
+        if "threecentre" in which and rank == 0 and world == 1:
+            t3 = three_centre_variant(args, eri, dev)
+            emit_detail("threecentre", t3, rank)
+            summary["threecentre_tps"] = round(t3["triples_per_s"])
 
     if world > 1:
         dist.barrier()
     if rank == 0:
+        if args.detail_out:
+            with open(args.detail_out, "w") as f:
+                json.dump(DETAILS, f, indent=1)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == eri.ERI_PREC_FP64 else "f64+f32x2",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if only is None else f"single class {args.only_class}, {nq_class} quartets",
-                       "classes": len(batches), "quartets_per_class": nq_class,
-                       "K_per_shell": K_PER_SHELL, "pairs_per_side": NPAIRS, "pool_per_l": POOL,
-                       "l2": "flushed between timed steps (256 MiB write); outputs 8 GB/step also exceed L2",
+                       "classes": len(batches), "quartets_per_class": nq_class, "K_per_shell": K_PER_SHELL,
+                       "l2": "flushed between timed steps (256 MiB write); outputs of 8 GB/step exceed L2",
                        "parallelism": f"weak x{world}: each rank its own seeded sweep"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-            "clocks": clk.summary(), "wall_s_timed": t_wall, "step_ms": step_ms, "variants": variants,
-            "per_class": per_class,
+            "clocks": clk.summary(), "variants": summary,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -600,17 +743,20 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-budget", type=float, default=18.0, help="seconds of oracle CPU work per reference step")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=None,
+                    help="seconds of oracle work per reference step (default: a few minutes in all)")
     ap.add_argument("--only-class", default=None, help="profiling aid: one class, e.g. 2222")
-    ap.add_argument("--no-variants", action="store_true", help="skip the split/adjoint/batched measurements")
-    ap.add_argument("--variants", default=None, help="comma list of split,adjoint,batched,threecentre (default: all)")
-    ap.add_argument("--split-nq-k5", type=int, default=10_000)
-    ap.add_argument("--adjoint-nq", type=int, default=20_000)
-    ap.add_argument("--molecule-natom", type=int, default=16)
+    ap.add_argument("--variants", default=None,
+                    help="comma list of " + ",".join(ALL_VARIANTS) + " (default: all; 'none' for none)")
+    ap.add_argument("--split-nq", type=int, default=100_000)
+    ap.add_argument("--adjoint-nq", type=int, default=0, help="quartets per class of the adjoint (0: all)")
+    ap.add_argument("--molecule-natom", type=int, default=64)
     ap.add_argument("--three-nt", type=int, default=100_000, help="triples per 3-centre class")
     ap.add_argument("--nq", type=int, default=NQ_PER_CLASS, help="quartets per class")
     ap.add_argument("--precision", choices=["fp64", "split"], default="fp64",
                     help="transforms of the timed sweep (profiling aid; the benchmark value is fp64)")
+    ap.add_argument("--detail-out", default=None, help="also write every detail object to this JSON file")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -230,13 +230,14 @@ int eri_batch3(int32_t lx, int32_t lc, int32_t ld, const eri_basis_t* basis,
  * memory: the paper has no counterpart of this entry point.
  *
  * Who needs it: a process whose device memory belongs to another allocator
- * (a serving or training framework's memory pool) may not call cudaMalloc
- * itself, and code running while a stream is captured into a CUDA graph
- * must not allocate.  eri_batch caches its scratch (the primitive-pair
- * tables) in memory it allocates; this entry point instead keeps that
- * scratch in a fixed device array of ERI_NOALLOC_SCRATCH_BYTES, compiled
- * into the library, and its constant tables in fixed arrays as well.  It
- * calls no cudaMalloc, cudaFree or other allocating routine.
+ * (a serving or training framework's caching pool, an MPI library's
+ * registered pool) may not call cudaMalloc itself: memory that allocator
+ * does not know about can make its own allocations fail or break its
+ * accounting.  eri_batch caches its scratch (the primitive-pair tables) in
+ * memory it allocates; this entry point instead keeps that scratch in a
+ * fixed device array of ERI_NOALLOC_SCRATCH_BYTES, compiled into the
+ * library, and its constant tables in fixed arrays as well.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  *
  * - The fixed arrays take ERI_NOALLOC_SCRATCH_BYTES (+ about 2.6 MB of
  *   tables) on every GPU that loads the library, until the process exits.
@@ -253,7 +254,13 @@ int eri_batch3(int32_t lx, int32_t lc, int32_t ld, const eri_basis_t* basis,
  *   in time (different streams, or several host threads) race on them:
  *   serialise them.
  * - Like eri_batch, each call synchronises `stream` once (validation).
- * - precision is always FP64; the sides are never swapped.
+ * - precision is always FP64; the sides are never swapped.  The bounds on
+ *   the contraction degrees are therefore those of the side order given
+ *   (the ket is transformed first, and a tile holds the auxiliary integrals
+ *   of every ket primitive pair of a quartet), which can be tighter than
+ *   eri_batch's, which takes the cheaper order: a batch no tile can hold in
+ *   this order returns ERI_EINVAL.  Exchanging the bra and ket lists (and
+ *   reading the output transposed) may make it fit.
  */
 #define ERI_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int eri_batch_noalloc(eri_class_t cls, const eri_basis_t* basis,
@@ -324,6 +331,36 @@ int eri_plan_job_degrees(eri_plan_t* plan, int32_t job, int32_t* kbra, int32_t* 
 int eri_plan_destroy(eri_plan_t* plan);
 
 /*
+ * Several GPUs on one plan (one process per GPU).  Quartets are independent
+ * units, so ranks share a plan by partitioning its work items and need one
+ * collective only for a digested result: each rank creates the same plan
+ * (same basis, threshold and flags, hence the same work items), keeps its
+ * own slice, executes it, and the per-rank energies (or J, K matrices) are
+ * summed over ranks by the caller (one all-reduce).  J and K of a slice are
+ * already symmetrised; the sum of the slices' J (K) is the plan's J (K).
+ *
+ * eri_partition -- host helper (no GPU work): longest processing time
+ * first over `n` units of cost `cost` (HOST, finite, >= 0): units in
+ * descending cost, ties in index order, each to the least-loaded rank (the
+ * lowest on ties).  owner (HOST, [n]) receives each unit's rank; load
+ * (HOST, [nranks], may be NULL) each rank's total cost.  The largest load
+ * exceeds the smallest by at most the largest cost.  ERI_EINVAL for
+ * nranks < 1, n < 0, NULL arrays with n > 0, or a negative or non-finite
+ * cost.
+ * eri_plan_set_slice -- keep the work items that eri_partition gives to
+ * `rank` of `nranks` (each item's cost is its job's FP64-work estimate per
+ * quartet times its quartet count); later eri_plan_execute, eri_plan_jk and
+ * eri_plan_coulomb calls process that slice only.  (0, 1) restores the whole
+ * plan.  Synchronises `stream`; the graph is captured again on the next
+ * execution.  In ERI_PLAN_STORE mode only the slice's integrals are written.
+ * eri_plan_slice_info -- the current slice's work items, quartets and total
+ * cost estimate (HOST pointers, each may be NULL).
+ */
+int eri_partition(const double* cost, int64_t n, int32_t nranks, int32_t* owner, double* load);
+int eri_plan_set_slice(eri_plan_t* plan, int32_t rank, int32_t nranks, void* stream);
+int eri_plan_slice_info(eri_plan_t* plan, int64_t* nitems, int64_t* nquartets, double* cost);
+
+/*
  * eri_last_form -- the form the calling thread's last successful eri_batch
  * launch ran (measurement support: operation counts depend on it).
  * *swapped = 1 when the kernel took the caller's ket as the side it
@@ -370,6 +407,19 @@ int eri_last_status(void* stream);
 int eri_profile_enable(int on);
 int eri_profile_read(int n, int64_t* launches, double* ms);
 int64_t eri_launch_count(void);
+
+/*
+ * eri_peak_probe -- measurement support: the arithmetic throughput of the
+ * current GPU, the denominator of the kernels' roofline fractions (the
+ * paper quotes fractions of FP64 peak, Section 4).  kind 0: FP64 FMA
+ * (DFMA), 1: FP64 tensor-core MMA (mma.sync m8n8k4 f64), 2: FP32 FMA.  One
+ * launch of a few CTAs per SM runs independent chains for about 100 ms; the
+ * best of three timed launches on `stream` (CUDA events) gives *gflops
+ * (HOST, GFLOP/s, FMA = 2 flops).  sm_mhz (HOST, may be NULL): the SM clock
+ * during the last launch, from the cycle counter and the global timer.
+ * Synchronises `stream`.  ERI_EINVAL for another kind or a NULL gflops.
+ */
+int eri_peak_probe(int kind, double* gflops, double* sm_mhz, void* stream);
 
 /* Human-readable text for an error code (static storage). */
 const char* eri_error_string(int code);

@@ -30,6 +30,9 @@ from .binding import (  # noqa: F401
     eri_profile_enable,
     eri_profile_read,
     eri_launch_count,
+    eri_peak_probe,
+    partition,
+    PEAK_DFMA, PEAK_DMMA, PEAK_FFMA,
     PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS,
     error_string,
     lib,
