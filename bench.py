@@ -380,14 +380,37 @@ def adjoint_variant(args, eri, dev):
             eri.eri_batch(cls, db, b, k, qq, out=o)
 
     forms = {}
+    ev = {}
 
-    def grad():
+    def grad(per=None):
         for cls, (b, k, qq, W), o, _, _ in data:
+            if per is not None:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
             eri.eri_batch_grad(cls, db, b, k, qq, W, gc, ge)
+            if per is not None:
+                e1.record()
+                per[cls] = (e0, e1)
             forms[cls] = eri.eri_last_grad_forms()
+
+    def fwd_per(per):
+        for cls, (b, k, qq, W), o, _, _ in data:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            eri.eri_batch(cls, db, b, k, qq, out=o)
+            e1.record()
+            per[cls] = (e0, e1)
 
     t_f = timed(fwd)
     t_g = timed(grad)
+    # per-class times (one more pass of each, events around every call)
+    pf, pg = {}, {}
+    fwd_per(pf)
+    grad(pg)
+    torch.cuda.synchronize()
+    per_class = {"".join(map(str, c)): {"quartets": n, "fwd_ms": round(pf[c][0].elapsed_time(pf[c][1]), 3),
+                                        "grad_ms": round(pg[c][0].elapsed_time(pg[c][1]), 3)}
+                 for c, _, _, _, n in data}
     nq_tot = sum(d[4] for d in data)
     for cls, _, _, (keys, counts), _ in data:
         for (x, y), n in zip(keys, counts):
@@ -412,7 +435,8 @@ def adjoint_variant(args, eri, dev):
             "grad_prepass_ms": prof[eri.PROF_PREPASS][1],
             "grad_kernel_frac_fp64_peak_sparse": gflop / (kms / 1e3) / 1e9 / FP64_PEAK_GFLOPS if kms > 0 else None,
             "fwd_frac_fp64_peak_sparse_plain": fflop / (t_f / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
-            "grad_forms": {"".join(map(str, c)): "".join("XV"[f] for f in v) for c, v in forms.items()}}
+            "grad_forms": {"".join(map(str, c)): "".join("XV"[f] for f in v) for c, v in forms.items()},
+            "per_class": per_class}
 
 
 def batched_variant(args, eri, dev, world, rank, dist):
@@ -530,7 +554,12 @@ def run_library(args):
 
     only = tuple(int(x) for x in args.only_class) if args.only_class else None
     prec = eri.ERI_PREC_SPLIT if args.precision == "split" else eri.ERI_PREC_FP64
-    basis, batches = sweep(seed=rank, only=only, nq=args.nq)
+    if only is not None and args.high_l_k:
+        # profiling aid: one class of the high-l workload (l up to f, K per shell)
+        hb = synth.split_batch(only, K=args.high_l_k, seed=rank, nq=args.nq)
+        basis, batches = hb[0], {only: hb[1:]}
+    else:
+        basis, batches = sweep(seed=rank, only=only, nq=args.nq)
     nq_class = args.nq
     db = eri.DeviceBasis(basis)
     dev_batches, outs = {}, {}
@@ -540,7 +569,8 @@ def run_library(args):
         outs[cls] = torch.empty(eri.out_len(cls, bra.shape[0], ket.shape[0], q.shape[0]), dtype=torch.float64,
                                 device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    dense = {c: opcount.dense_flops(c, K_PER_SHELL ** 2, K_PER_SHELL ** 2) for c in batches}
+    Kps = args.high_l_k if (only is not None and args.high_l_k) else K_PER_SHELL
+    dense = {c: opcount.dense_flops(c, Kps ** 2, Kps ** 2) for c in batches}
     stream = torch.cuda.current_stream()
     forms = {}
 
@@ -560,7 +590,7 @@ def run_library(args):
         step()
     torch.cuda.synchronize()
     # the FP64 operations of the form each class runs (chosen during warm-up)
-    sparse = {c: opcount.sparse_flops(c, K_PER_SHELL ** 2, K_PER_SHELL ** 2, form=forms[c]) for c in batches}
+    sparse = {c: opcount.sparse_flops(c, Kps ** 2, Kps ** 2, form=forms[c]) for c in batches}
     eri.eri_profile_read()
     eri.eri_profile_enable(True)
     timing = {c: [] for c in batches}
@@ -747,6 +777,9 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=None,
                     help="seconds of oracle work per reference step (default: a few minutes in all)")
     ap.add_argument("--only-class", default=None, help="profiling aid: one class, e.g. 2222")
+    ap.add_argument("--high-l-k", type=int, default=0,
+                    help="profiling aid with --only-class: the high-l workload (exponents 10^U(log 0.05, log 50)) "
+                         "with this K per shell instead of the class sweep")
     ap.add_argument("--variants", default=None,
                     help="comma list of " + ",".join(ALL_VARIANTS) + " (default: all; 'none' for none)")
     ap.add_argument("--split-nq", type=int, default=100_000)

@@ -412,11 +412,12 @@ int64_t eri_launch_count(void);
  * eri_peak_probe -- measurement support: the arithmetic throughput of the
  * current GPU, the denominator of the kernels' roofline fractions (the
  * paper quotes fractions of FP64 peak, Section 4).  kind 0: FP64 FMA
- * (DFMA), 1: FP64 tensor-core MMA (mma.sync m8n8k4 f64), 2: FP32 FMA.  One
- * launch of a few CTAs per SM runs independent chains for about 100 ms; the
- * best of three timed launches on `stream` (CUDA events) gives *gflops
- * (HOST, GFLOP/s, FMA = 2 flops).  sm_mhz (HOST, may be NULL): the SM clock
- * during the last launch, from the cycle counter and the global timer.
+ * (DFMA), 1: FP64 tensor-core MMA (mma.sync m8n8k4 f64), 2: FP32 FMA.  A
+ * launch of 2 to 8 CTAs per SM runs independent chains (4 to 16 per thread)
+ * for about 100 ms; *gflops (HOST, GFLOP/s, FMA = 2 flops) is the best, over
+ * those shapes, of three timed launches each on `stream` (CUDA events).
+ * sm_mhz (HOST, may be NULL): the SM clock during the best shape's last
+ * launch, from the cycle counter and the global timer.
  * Synchronises `stream`.  ERI_EINVAL for another kind or a NULL gflops.
  */
 int eri_peak_probe(int kind, double* gflops, double* sm_mhz, void* stream);

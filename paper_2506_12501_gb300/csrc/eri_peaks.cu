@@ -16,7 +16,6 @@
 namespace eri {
 
 constexpr int kProbeThreads = 256;
-constexpr int kProbeChains = 8;
 
 __device__ __forceinline__ uint64_t global_ns()
 {
@@ -26,7 +25,7 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // clk[blockIdx] = {cycles, ns} of the CTA; sink keeps the chains alive
-template <typename T>
+template <typename T, int CH>
 __global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(int64_t iters, T b, T c, T* sink,
                                                                   unsigned long long* clk)
 {
@@ -35,16 +34,16 @@ __global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(int64_t iters,
         t0 = global_ns();
         c0 = clock64();
     }
-    T v[kProbeChains];
+    T v[CH];
 #pragma unroll
-    for (int j = 0; j < kProbeChains; ++j) v[j] = (T)(threadIdx.x + j) * (T)1e-3;
+    for (int j = 0; j < CH; ++j) v[j] = (T)(threadIdx.x + j) * (T)1e-3;
     for (int64_t i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int j = 0; j < kProbeChains; ++j) v[j] = fma(v[j], b, c);
+        for (int j = 0; j < CH; ++j) v[j] = fma(v[j], b, c);
     }
     T s = 0;
 #pragma unroll
-    for (int j = 0; j < kProbeChains; ++j) s += v[j];
+    for (int j = 0; j < CH; ++j) s += v[j];
     if (s == (T)-12345.0) sink[threadIdx.x] = s;  // never true; keeps the arithmetic
     if (threadIdx.x == 0) {
         const uint64_t c1 = clock64(), t1 = global_ns();
@@ -89,11 +88,11 @@ __global__ void __launch_bounds__(kProbeThreads) dmma_probe_kernel(int64_t iters
 
 using namespace eri;
 
-extern "C" int eri_peak_probe(int kind, double* gflops, double* sm_mhz, void* stream)
+// One probe configuration: `per_sm` CTAs per SM, `chains` independent
+// chains per thread (MMA: per warp).  Returns ERI_OK and the GFLOP/s of the
+// best of three timed launches of about 100 ms, and the SM clock of the last.
+static int probe_once(int kind, int chains, int per_sm, cudaStream_t st, double* gflops, double* sm_mhz)
 {
-    if (kind < 0 || kind > 2 || !gflops) return ERI_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int per_sm = 4;
     const int grid = per_sm * sm_count();
     int err = ERI_OK;
     // [grid][2] clock records, then a small sink
@@ -103,23 +102,31 @@ extern "C" int eri_peak_probe(int kind, double* gflops, double* sm_mhz, void* st
     double* sink = (double*)(ws + sizeof(unsigned long long) * 2 * grid);
     auto launch = [&](int64_t iters) {
         count_launch();
-        if (kind == 0)
-            fma_probe_kernel<double><<<grid, kProbeThreads, 0, st>>>(iters, 0.999999, 1e-7, sink, clk);
-        else if (kind == 1)
+        if (kind == 1)
             dmma_probe_kernel<<<grid, kProbeThreads, 0, st>>>(iters, sink, clk);
+        else if (kind == 0 && chains == 4)
+            fma_probe_kernel<double, 4><<<grid, kProbeThreads, 0, st>>>(iters, 0.999999, 1e-7, sink, clk);
+        else if (kind == 0 && chains == 8)
+            fma_probe_kernel<double, 8><<<grid, kProbeThreads, 0, st>>>(iters, 0.999999, 1e-7, sink, clk);
+        else if (kind == 0)
+            fma_probe_kernel<double, 16><<<grid, kProbeThreads, 0, st>>>(iters, 0.999999, 1e-7, sink, clk);
+        else if (chains == 4)
+            fma_probe_kernel<float, 4><<<grid, kProbeThreads, 0, st>>>(iters, 0.9999f, 1e-4f, (float*)sink, clk);
+        else if (chains == 8)
+            fma_probe_kernel<float, 8><<<grid, kProbeThreads, 0, st>>>(iters, 0.9999f, 1e-4f, (float*)sink, clk);
         else
-            fma_probe_kernel<float><<<grid, kProbeThreads, 0, st>>>(iters, 0.9999f, 1e-4f, (float*)sink, clk);
+            fma_probe_kernel<float, 16><<<grid, kProbeThreads, 0, st>>>(iters, 0.9999f, 1e-4f, (float*)sink, clk);
     };
     // flops of one iteration of the whole grid
     const double per_iter = kind == 1 ? (double)grid * (kProbeThreads / 32) * 4 * 512.0
-                                      : (double)grid * kProbeThreads * kProbeChains * 2.0;
+                                      : (double)grid * kProbeThreads * chains * 2.0;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return ERI_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return ERI_ECUDA;
     }
-    // calibrate on a short launch, then time one of about 100 ms (best of 3)
+    // calibrate on a short launch, then time launches of about 100 ms (best of 3)
     int64_t iters = 1 << 12;
     float ms = 0.f;
     bool ok = true;
@@ -145,17 +152,38 @@ extern "C" int eri_peak_probe(int kind, double* gflops, double* sm_mhz, void* st
     cudaEventDestroy(e1);
     if (!ok || cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
     *gflops = per_iter * (double)iters / ((double)ms * 1e-3) / 1e9;
-    if (sm_mhz) {
-        // cycles over nanoseconds of the last launch, averaged over its CTAs
-        std::vector<unsigned long long> h(2 * (size_t)grid);
-        if (cudaMemcpy(h.data(), clk, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return ERI_ECUDA;
-        double cyc = 0, ns = 0;
-        for (int i = 0; i < grid; ++i) {
-            cyc += (double)h[2 * i];
-            ns += (double)h[2 * i + 1];
-        }
-        *sm_mhz = ns > 0 ? 1e3 * cyc / ns : 0.0;
+    // cycles over nanoseconds of the last launch, averaged over its CTAs
+    std::vector<unsigned long long> h(2 * (size_t)grid);
+    if (cudaMemcpy(h.data(), clk, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ERI_ECUDA;
+    double cyc = 0, ns = 0;
+    for (int i = 0; i < grid; ++i) {
+        cyc += (double)h[2 * i];
+        ns += (double)h[2 * i + 1];
     }
+    *sm_mhz = ns > 0 ? 1e3 * cyc / ns : 0.0;
+    return ERI_OK;
+}
+
+extern "C" int eri_peak_probe(int kind, double* gflops, double* sm_mhz, void* stream)
+{
+    if (kind < 0 || kind > 2 || !gflops) return ERI_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the best over a few occupancies and chain counts (MMA: four
+    // accumulators per warp, at two occupancies)
+    const int shapes[][2] = {{4, 2}, {8, 2}, {16, 2}, {4, 4}, {8, 4}, {16, 4}, {8, 8}};
+    double best = -1.0, best_mhz = 0.0;
+    for (const auto& sh : shapes) {
+        if (kind == 1 && sh[0] != 8) continue;
+        double g = 0.0, mhz = 0.0;
+        const int rc = probe_once(kind, sh[0], sh[1], st, &g, &mhz);
+        if (rc != ERI_OK) return rc;
+        if (g > best) {
+            best = g;
+            best_mhz = mhz;
+        }
+    }
+    *gflops = best;
+    if (sm_mhz) *sm_mhz = best_mhz;
     return ERI_OK;
 }
