@@ -362,6 +362,8 @@ def adjoint_variant(args, eri, dev):
     data = []
     gflop = fflop = 0.0
     for cls, (bra, ket, q) in batches.items():
+        if args.adjoint_only and "".join(map(str, cls)) not in args.adjoint_only.split(","):
+            continue
         if args.adjoint_nq:
             q = q[: args.adjoint_nq]
         W = synth.density_weights(cls, bra, ket, q, D, bf_off)
@@ -425,7 +427,7 @@ def adjoint_variant(args, eri, dev):
     eri.eri_profile_enable(False)
     prof = eri.eri_profile_read()
     kms = prof[eri.PROF_GRAD][1]
-    return {"workload": f"16-atom molecule basis, {len(batches)} classes, {nq_tot} unique quartets, "
+    return {"workload": f"16-atom molecule basis, {len(data)} classes, {nq_tot} unique quartets, "
                         "W = D_ab D_cd", "quartets": nq_tot, "fwd_ms": t_f, "grad_ms": t_g,
             "grad_over_fwd": t_g / t_f, "fwd_quartets_per_s": nq_tot / (t_f / 1e3),
             "grad_quartets_per_s": nq_tot / (t_g / 1e3),
@@ -784,6 +786,7 @@ def main():
                     help="comma list of " + ",".join(ALL_VARIANTS) + " (default: all; 'none' for none)")
     ap.add_argument("--split-nq", type=int, default=100_000)
     ap.add_argument("--adjoint-nq", type=int, default=0, help="quartets per class of the adjoint (0: all)")
+    ap.add_argument("--adjoint-only", default=None, help="profiling aid: comma list of adjoint classes, e.g. 1010")
     ap.add_argument("--molecule-natom", type=int, default=64)
     ap.add_argument("--three-nt", type=int, default=100_000, help="triples per 3-centre class")
     ap.add_argument("--nq", type=int, default=NQ_PER_CLASS, help="quartets per class")

@@ -370,6 +370,66 @@ static __device__ const double* to_solid_harmonics(const FwdArgs& a, double* con
     return buf[cur];
 }
 
+// Stage B of the split form for a wide bra Hermite range (32 < nhbu <= 32 P):
+// one warp per (quartet, cd); lane l carries the bra Hermite functions
+// p = pb0 + l + 32 j, j < P, so that every ket E value loaded (the same for
+// the whole warp) feeds P products and the loop trip counts are uniform.
+template <int P>
+__device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int IC, int ii, int KK, int KKt,
+                                                  int NIs, int ncd, int nhk, const double* sEk, const double* sR,
+                                                  double* sX, const int* s_q, const int* s_kstart,
+                                                  const int16_t* s_kq, const int16_t* s_pq)
+{
+    const ClassTables& ct = a.ct;
+    const int lane = threadIdx.x & 31, nhb = ct.nhb;
+    for (int w = threadIdx.x >> 5; w < TQ * ncd; w += kNT / 32) {
+        const int q = w % TQ, cd = w / TQ;
+        const float2* Ek = reinterpret_cast<const float2*>(
+            a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd);
+        const double* Rc = sR + (q * IC + ii) * KK;
+        int prow[P];
+        float S[P][2], c[P][2];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int p = ct.pb0 + lane + 32 * j;
+            prow[j] = (p < nhb ? p : ct.pb0) * nhk;  // lanes past the range read a valid row, results dropped
+            S[j][0] = S[j][1] = c[j][0] = c[j][1] = 0.f;
+        }
+        const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
+        for (int t = t0; t < t1; ++t) {
+            const int qv = s_kq[t];
+            const float2* Rj[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) Rj[j] = reinterpret_cast<const float2*>(Rc + (size_t)s_pq[prow[j] + qv] * NIs);
+            const float2* Ea = Ek + t * KK;
+            int k = 0;
+            for (; k + 1 < KKt; k += 2) {
+                const float2 e0 = Ea[k], e1 = Ea[k + 1];
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    ff_mac(e0, Rj[j][k], S[j][0], c[j][0]);
+                    ff_mac(e1, Rj[j][k + 1], S[j][1], c[j][1]);
+                }
+            }
+            if (k < KKt) {
+                const float2 e0 = Ea[k];
+#pragma unroll
+                for (int j = 0; j < P; ++j) ff_mac(e0, Rj[j][k], S[j][0], c[j][0]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int p = ct.pb0 + lane + 32 * j;
+            if (p >= nhb) continue;
+            // fold the two chains into one split pair (error-free sum of the highs)
+            const float t2 = __fadd_rn(S[j][0], S[j][1]), z = __fsub_rn(t2, S[j][0]);
+            const float err = __fadd_rn(__fsub_rn(S[j][0], __fsub_rn(t2, z)), __fsub_rn(S[j][1], z));
+            const float ch = __fadd_rn(__fadd_rn(c[j][0], c[j][1]), err);
+            reinterpret_cast<float2*>(sX)[(p * ncd + cd) * TQ + q] = make_float2(t2, ch);
+        }
+    }
+}
+
 // One tile: quartets q0 .. q0+nqt-1 (the class tables are already staged).
 // s_red: one shared double for the digestion sum.
 template <bool SPLIT>
@@ -516,7 +576,13 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             // only the bra Hermite functions the bra transform reads (all of
             // them, or those of order la for a solid-harmonic bra)
             const int nhbu = nhb - ct.pb0;
-            const int nB = TQ * nhbu * ncd;
+            // split form, wide bra Hermite range: warp per (quartet, cd), P functions per lane
+            const int blocked = SPLIT ? (nhbu >= 72 && nhbu <= 96 ? 3 : (nhbu >= 48 && nhbu <= 64 ? 2 : 0)) : 0;
+            if (blocked == 3)
+                split_ket_blocked<3>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq);
+            else if (blocked == 2)
+                split_ket_blocked<2>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq);
+            const int nB = blocked ? 0 : TQ * nhbu * ncd;
             for (int item = tid; item < nB; item += kNT) {
                 const int q = item % TQ, r = item / TQ, p = ct.pb0 + r % nhbu, cd = r / nhbu;
                 const double* Ek = a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd;
