@@ -42,6 +42,39 @@ __device__ __forceinline__ void ff_mac(float2 a, float2 b, float& S, float& c)
     c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, pe))));
 }
 
+// Loads and stores with an L2 eviction priority (a cache policy made by
+// createpolicy).  A large quartet's ket E products are re-read for every bra
+// primitive while its bra E products and its accumulating outputs stream
+// through: the first are marked to stay in L2, the others to leave it first.
+__device__ __forceinline__ uint64_t policy_keep()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_stream()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float2 ld_hint(const float2* p, uint64_t pol)
+{
+    float2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_hint(const double* p, uint64_t pol)
+{
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(double* p, double v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+
 struct FwdArgs {
     ClassTables ct;
     const double* boys;
@@ -382,6 +415,7 @@ __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int 
 {
     const ClassTables& ct = a.ct;
     const int lane = threadIdx.x & 31, nhb = ct.nhb;
+    const uint64_t keep = policy_keep();
     for (int w = threadIdx.x >> 5; w < TQ * ncd; w += kNT / 32) {
         const int q = w % TQ, cd = w / TQ;
         const float2* Ek = reinterpret_cast<const float2*>(
@@ -402,9 +436,10 @@ __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int 
 #pragma unroll
             for (int j = 0; j < P; ++j) Rj[j] = reinterpret_cast<const float2*>(Rc + (size_t)s_pq[prow[j] + qv] * NIs);
             const float2* Ea = Ek + t * KK;
+            const bool gl = !a.e_smem;
             int k = 0;
             for (; k + 1 < KKt; k += 2) {
-                const float2 e0 = Ea[k], e1 = Ea[k + 1];
+                const float2 e0 = gl ? ld_hint(Ea + k, keep) : Ea[k], e1 = gl ? ld_hint(Ea + k + 1, keep) : Ea[k + 1];
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
                     ff_mac(e0, Rj[j][k], S[j][0], c[j][0]);
@@ -412,7 +447,7 @@ __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int 
                 }
             }
             if (k < KKt) {
-                const float2 e0 = Ea[k];
+                const float2 e0 = gl ? ld_hint(Ea + k, keep) : Ea[k];
 #pragma unroll
                 for (int j = 0; j < P; ++j) ff_mac(e0, Rj[j][k], S[j][0], c[j][0]);
             }
@@ -682,6 +717,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     }
                 }
             } else {
+                const uint64_t stream = policy_stream();
                 for (int item = tid; item < nC; item += kNT) {
                     const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
                     if (q >= nqt) continue;
@@ -689,7 +725,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     const double v =
                         bra_sum<SPLIT>(Eb + i, KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
                     const int64_t o = out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd);
-                    a.out[o] = (i == 0) ? v : a.out[o] + v;
+                    st_hint(a.out + o, (i == 0) ? v : ld_hint(a.out + o, stream) + v, stream);
                 }
             }
             __syncthreads();
