@@ -31,6 +31,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <queue>
 #include <tuple>
@@ -41,6 +42,12 @@
 namespace eri {
 
 constexpr int64_t kChunk = 512;  // quartets per work item (at most)
+// Plan tile tuning: the heaviest jobs covering this share of the modelled
+// work are timed, each on a sample of up to kTuneItemsPerSM items per SM cut
+// to kTuneItemQ quartets; tuned shapes are kept per job signature.
+constexpr double kTuneCover = 0.97;
+constexpr int kTuneItemsPerSM = 4;
+constexpr int64_t kTuneItemQ = 64;
 // static shared memory of the plan kernel (job arguments and a few words),
 // taken off the dynamic budget that lets two CTAs share an SM
 constexpr size_t kPlanStaticSmem = 1024 + 256;
@@ -62,6 +69,10 @@ struct PlanParams {
     int* counter;
     int* status;
 };
+
+// Tuned tile shapes per (device, class, K_bra, K_ket, split) of plan jobs.
+static std::map<std::tuple<int, int, int, int, int, int, int, int>, TilePlan> g_plan_tuned;
+static std::mutex g_plan_tuned_mu;
 
 struct JobHost {
     eri_class_t cls;
@@ -301,7 +312,7 @@ static bool autotune_job(const FwdArgs& base, const std::vector<WorkItem>& sampl
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, tp.bytes);
         const int grid = std::max(1, per_sm) * sm_count();
         float ms = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {  // first run warms the caches
+        for (int rep = 0; rep < (&tp == &cands[0] ? 2 : 1); ++rep) {  // the first run warms the caches
             plan_reset_kernel<<<1, 32, 0, st>>>(d_prm);
             cudaEventRecord(e0, st);
             kern<<<grid, kNT, tp.bytes, st>>>(d_job, d_items, (int64_t)items.size(), d_prm);
@@ -587,20 +598,57 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
         bool ok = cudaMalloc(&zeroD, 8 * (size_t)nbf * nbf) == cudaSuccess && cudaMalloc(&scratch, 64) == cudaSuccess &&
                   cudaMalloc(&ctr, 16) == cudaSuccess && cudaMalloc(&prm, sizeof(PlanParams)) == cudaSuccess;
         if (ok) cudaMemsetAsync(zeroD, 0, 8 * (size_t)nbf * nbf, st);
-        for (size_t j = 0; ok && j < p->jobs.size(); ++j) {
+        // tune the heaviest jobs that together carry kTuneCover of the plan's
+        // modelled FP64 work (the rest keep the planner's shape); a job whose
+        // signature an earlier plan of this process tuned reuses that shape
+        std::vector<double> jw(p->jobs.size());
+        double total = 0.0;
+        for (size_t j = 0; j < p->jobs.size(); ++j) {
+            const FwdArgs& a = p->jobs[j].args;
+            jw[j] = ((double)a.KB * a.KK * (a.ct.nhb * a.ct.Tcd + a.ct.nhl) + (double)a.KB * a.ct.ncd * a.ct.Tab) *
+                    (double)p->jobs[j].nq;
+            total += jw[j];
+        }
+        std::vector<size_t> byw(p->jobs.size());
+        std::iota(byw.begin(), byw.end(), (size_t)0);
+        std::stable_sort(byw.begin(), byw.end(), [&](size_t x, size_t y) { return jw[x] > jw[y]; });
+        std::vector<std::vector<int64_t>> job_items(p->jobs.size());
+        for (size_t i = 0; i < items.size(); ++i) job_items[(size_t)items[i].job].push_back((int64_t)i);
+        double covered = 0.0;
+        for (size_t j : byw) {
+            if (!ok || covered >= kTuneCover * total) break;
+            covered += jw[j];
             JobHost& J = p->jobs[j];
-            if (J.nq < 4096) continue;
+            const auto key = std::make_tuple(p->dev, J.args.ct.la, J.args.ct.lb, J.args.ct.lc, J.args.ct.ld,
+                                             J.args.KB, J.args.KK, (int)split);
+            {
+                std::lock_guard<std::mutex> lk(g_plan_tuned_mu);
+                auto it = g_plan_tuned.find(key);
+                if (it != g_plan_tuned.end()) {
+                    set_tile(J.args, it->second);
+                    J.smem = it->second.bytes;
+                    continue;
+                }
+            }
+            // the sample: up to kTuneItemsPerSM items per SM spread over the
+            // job, each cut to kTuneItemQ quartets, so that every CTA of the
+            // persistent kernel takes part in the timed runs
+            const std::vector<int64_t>& ji = job_items[j];
+            const size_t want = std::min(ji.size(), (size_t)kTuneItemsPerSM * (size_t)sm_count());
             std::vector<WorkItem> sample;
             int64_t sq = 0;
-            for (const WorkItem& it : items)
-                if (it.job == (int32_t)j && sq < 4096) {
-                    sample.push_back(it);
-                    sq += it.k1 - it.k0;
-                }
+            for (size_t s = 0; s < want; ++s) {
+                WorkItem it = items[(size_t)ji[s * ji.size() / want]];
+                it.k1 = std::min(it.k1, it.k0 + kTuneItemQ);
+                sq += it.k1 - it.k0;
+                sample.push_back(it);
+            }
             TilePlan best;
             if (autotune_job(J.args, sample, sq, split, zeroD, nbf, scratch, ctr, prm, st, &best)) {
                 set_tile(J.args, best);
                 J.smem = best.bytes;
+                std::lock_guard<std::mutex> lk(g_plan_tuned_mu);
+                g_plan_tuned[key] = best;
             }
         }
         cudaStreamSynchronize(st);

@@ -70,6 +70,10 @@ __device__ __forceinline__ double ld_hint(const double* p, uint64_t pol)
     asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
     return v;
 }
+__device__ __forceinline__ void prefetch_l1(const void* p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void st_hint(double* p, double v, uint64_t pol)
 {
     asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
@@ -430,13 +434,24 @@ __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int 
             S[j][0] = S[j][1] = c[j][0] = c[j][1] = 0.f;
         }
         const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
+        const bool gl = !a.e_smem;
+        // the ket E rows of a term (KK float pairs) come from L2 or DRAM: the
+        // lanes prefetch the rows of the next two terms into L1 while the
+        // warp works on the current one
+        // (each prefetched address lies inside its row: the line of byte
+        // min(128 l, 8 KK - 8) for lane l; a row spans at most nline lines)
+        const int nline = (KK * 8 + 127) / 128 + 1;
+        if (gl && lane < 2 * nline && t0 + lane / nline < t1)
+            prefetch_l1(reinterpret_cast<const char*>(Ek + (t0 + lane / nline) * KK) +
+                        min(128 * (lane % nline), 8 * KK - 8));
         for (int t = t0; t < t1; ++t) {
+            if (gl && lane < nline && t + 2 < t1)
+                prefetch_l1(reinterpret_cast<const char*>(Ek + (t + 2) * KK) + min(128 * lane, 8 * KK - 8));
             const int qv = s_kq[t];
             const float2* Rj[P];
 #pragma unroll
             for (int j = 0; j < P; ++j) Rj[j] = reinterpret_cast<const float2*>(Rc + (size_t)s_pq[prow[j] + qv] * NIs);
             const float2* Ea = Ek + t * KK;
-            const bool gl = !a.e_smem;
             int k = 0;
             for (; k + 1 < KKt; k += 2) {
                 const float2 e0 = gl ? ld_hint(Ea + k, keep) : Ea[k], e1 = gl ? ld_hint(Ea + k + 1, keep) : Ea[k + 1];
