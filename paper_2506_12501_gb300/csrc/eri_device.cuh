@@ -132,4 +132,157 @@ __device__ __forceinline__ void r_recursion(int L, const double* base, double X,
     }
 }
 
+// ---- compile-time L: the same Boys evaluation, prefactor scaling and
+// auxiliary recursion with every loop bound known, so that the per-order
+// values stay in registers and the recursion steps fold into constants.
+
+__host__ __device__ constexpr int herm_idx_c(int t, int u, int v)
+{
+    return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
+}
+
+// (t, u, v) of Hermite index e (the tetrahedral numbering above)
+__host__ __device__ constexpr void herm_tuv_c(int e, int& t, int& u, int& v)
+{
+    int N = 0;
+    while ((N + 1) * (N + 2) * (N + 3) / 6 <= e) ++N;
+    const int r = e - N * (N + 1) * (N + 2) / 6;
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= r) ++d;
+    const int w = r - d * (d + 1) / 2;
+    t = N - d;
+    u = d - w;
+    v = N - t - u;
+}
+
+// F_0..F_L at T into F[] (registers), as boys_eval.
+template <int L>
+__device__ __forceinline__ void boys_eval_c(double T, const double* __restrict__ tab, double (&F)[L + 1])
+{
+    if (T < kBoysTmax) {
+        const float Tf = (float)T;
+        int j = __float2int_rn(Tf * (float)kBoysInvStep);
+        j = j < 0 ? 0 : (j > kBoysGrid - 1 ? kBoysGrid - 1 : j);
+        const double T0 = (double)((float)j * (float)kBoysStep);
+        const double md = T0 - T;
+        const double2* row = reinterpret_cast<const double2*>(tab + (size_t)j * 8);
+        const double2 r01 = __ldg(row), r23 = __ldg(row + 1), r45 = __ldg(row + 2), r67 = __ldg(row + 3);
+        double f = r67.x;
+        f = fma(f, md, r45.y);
+        f = fma(f, md, r45.x);
+        f = fma(f, md, r23.y);
+        f = fma(f, md, r23.x);
+        f = fma(f, md, r01.y);
+        f = fma(f, md, r01.x);
+        F[L] = f;
+        if (L == 0) return;
+        double e = 1.0 / 720.0;
+        e = fma(e, md, 1.0 / 120.0);
+        e = fma(e, md, 1.0 / 24.0);
+        e = fma(e, md, 1.0 / 6.0);
+        e = fma(e, md, 0.5);
+        e = fma(e, md, 1.0);
+        e = fma(e, md, 1.0);
+        const double eT = r67.y * e;
+        const double twoT = T + T;
+#pragma unroll
+        for (int n = L - 1; n >= 0; --n) {
+            f = fma(twoT, f, eT) * (1.0 / (2 * n + 1));
+            F[n] = f;
+        }
+    } else {
+        const double rt = rsqrt(T);
+        const double inv2T = 0.5 * rt * rt;
+        double f = kHalfSqrtPi * rt;
+        F[0] = f;
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            f = f * ((double)(2 * n + 1) * inv2T);
+            F[n + 1] = f;
+        }
+    }
+}
+
+// The auxiliary recursion of r_recursion with L known: each step's axis,
+// sources and coefficient are constants.
+template <int L, typename RPtr>
+__device__ __forceinline__ void r_recursion_c(const double (&base)[L + 1], double X, double Y, double Z, RPtr R)
+{
+    R[0] = base[L];
+#pragma unroll
+    for (int n = L - 1; n >= 0; --n) {
+        const int N = L - n;
+        const int top = (N + 1) * (N + 2) * (N + 3) / 6;
+#pragma unroll
+        for (int e = top - 1; e >= 1; --e) {
+            int r[3] = {0, 0, 0};
+            herm_tuv_c(e, r[0], r[1], r[2]);
+            int axis = r[0] == 1 ? 0 : (r[1] == 1 ? 1 : (r[2] == 1 ? 2 : -1));
+            if (axis < 0) {
+                axis = 0;
+                int best = 1 << 20;
+                for (int i = 0; i < 3; ++i)
+                    if (r[i] > 0 && r[i] < best) {
+                        best = r[i];
+                        axis = i;
+                    }
+            }
+            const int c = r[axis] - 1;
+            r[axis] -= 1;
+            const int s1 = herm_idx_c(r[0], r[1], r[2]);
+            const double x = axis == 0 ? X : (axis == 1 ? Y : Z);
+            double v = x * R[s1];
+            if (c > 0) {
+                r[axis] -= 1;
+                v = fma((double)c, R[herm_idx_c(r[0], r[1], r[2])], v);
+            }
+            R[e] = v;
+        }
+        R[0] = base[n];
+    }
+}
+
+// The auxiliary integrals of one primitive quartet (Eqs. 0m and r-rr) with
+// L known: pair scalars pb (bra) and pk (ket) as the pair kernel writes them.
+template <int L, typename RPtr>
+__device__ __forceinline__ void aux_integrals_c(const double* pb, const double* pk, const double* __restrict__ boys,
+                                                RPtr R)
+{
+    const double zp = pb[PS_P], zq = pk[PS_P];
+    const double rs = rsqrt(zp + zq);
+    const double rho = zp * zq * (rs * rs);
+    const double X = pb[PS_PX] - pk[PS_PX], Y = pb[PS_PY] - pk[PS_PY], Z = pb[PS_PZ] - pk[PS_PZ];
+    const double T = rho * fma(X, X, fma(Y, Y, Z * Z));
+    double base[L + 1];
+    boys_eval_c<L>(T, boys, base);
+    double f = pb[PS_INVP] * pk[PS_INVP] * rs;  // 2 pi^(5/2) / (zp zq sqrt(zp+zq))
+    const double m2rho = -2.0 * rho;
+#pragma unroll
+    for (int n = 0; n <= L; ++n) {
+        base[n] *= f;
+        f *= m2rho;
+    }
+    r_recursion_c<L>(base, X, Y, Z, R);
+}
+
+// Orders with a compile-time path (the setup dominates the low orders).
+constexpr int kLFixed = 6;
+
+// aux_integrals_c for the runtime L if L <= kLFixed (returns false otherwise).
+template <typename RPtr>
+__device__ __forceinline__ bool aux_integrals_fixed(int L, const double* pb, const double* pk,
+                                                    const double* __restrict__ boys, RPtr R)
+{
+    switch (L) {
+        case 0: aux_integrals_c<0>(pb, pk, boys, R); return true;
+        case 1: aux_integrals_c<1>(pb, pk, boys, R); return true;
+        case 2: aux_integrals_c<2>(pb, pk, boys, R); return true;
+        case 3: aux_integrals_c<3>(pb, pk, boys, R); return true;
+        case 4: aux_integrals_c<4>(pb, pk, boys, R); return true;
+        case 5: aux_integrals_c<5>(pb, pk, boys, R); return true;
+        case 6: aux_integrals_c<6>(pb, pk, boys, R); return true;
+        default: return false;
+    }
+}
+
 }  // namespace eri

@@ -341,6 +341,8 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
                     const double* pb = sPb + (q * KB + i) * PS_N;
                     const double* pk = sPk + (q * KK + k) * PS_N;
+                    // the compile-time path for low orders
+                    if (!coop && aux_integrals_fixed(L2, pb, pk, a.boys, R)) continue;
                     const double zp = pb[PS_P], zq = pk[PS_P];
                     const double rs = rsqrt(zp + zq);
                     const double rho = zp * zq * (rs * rs);

@@ -577,24 +577,28 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
                 const double* pb = sPb + (q * KB + i) * PS_N;
                 const double* pk = sPk + (q * KK + k) * PS_N;
-                const double zp = pb[PS_P], zq = pk[PS_P];
-                const double rs = rsqrt(zp + zq);
-                const double rho = zp * zq * (rs * rs);
-                const double X = pb[PS_PX] - pk[PS_PX], Y = pb[PS_PY] - pk[PS_PY], Z = pb[PS_PZ] - pk[PS_PZ];
-                const double PQ2 = fma(X, X, fma(Y, Y, Z * Z));
-                const double T = rho * PQ2;
-                double base[kLtotMax + 1];
-                boys_eval(ct.L, T, a.boys, base);
-                double f = pb[PS_INVP] * pk[PS_INVP] * rs;  // 2 pi^(5/2) / (zp zq sqrt(zp+zq))
-                const double m2rho = -2.0 * rho;
-                for (int n = 0; n <= ct.L; ++n) {
-                    base[n] *= f;
-                    f *= m2rho;
+                // the compile-time path for low orders; the general one above them
+                // and for the warp-shared recursion of small tiles
+                if (coop || !aux_integrals_fixed(ct.L, pb, pk, a.boys, R)) {
+                    const double zp = pb[PS_P], zq = pk[PS_P];
+                    const double rs = rsqrt(zp + zq);
+                    const double rho = zp * zq * (rs * rs);
+                    const double X = pb[PS_PX] - pk[PS_PX], Y = pb[PS_PY] - pk[PS_PY], Z = pb[PS_PZ] - pk[PS_PZ];
+                    const double PQ2 = fma(X, X, fma(Y, Y, Z * Z));
+                    const double T = rho * PQ2;
+                    double base[kLtotMax + 1];
+                    boys_eval(ct.L, T, a.boys, base);
+                    double f = pb[PS_INVP] * pk[PS_INVP] * rs;  // 2 pi^(5/2) / (zp zq sqrt(zp+zq))
+                    const double m2rho = -2.0 * rho;
+                    for (int n = 0; n <= ct.L; ++n) {
+                        base[n] *= f;
+                        f *= m2rho;
+                    }
+                    if (coop)
+                        r_recursion_warp(ct.L, base, X, Y, Z, a.rsteps, R, lane);
+                    else
+                        r_recursion(ct.L, base, X, Y, Z, a.rsteps, R);
                 }
-                if (coop)
-                    r_recursion_warp(ct.L, base, X, Y, Z, a.rsteps, R, lane);
-                else
-                    r_recursion(ct.L, base, X, Y, Z, a.rsteps, R);
                 if (SPLIT)  // each entry becomes its (hi, lo) float pair, in place
                     for (int e = e0; e < nhl; e += de) {
                         double& slot = R[e];
