@@ -151,22 +151,32 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
                    double* grad_centres, double* grad_exps, void* stream);
 
 /*
- * eri_last_grad_forms -- the forms the last eri_batch_grad call ran, for its
- * bra-channel launch and its ket-channel launch: ERI_GRAD_X (the forward ket
- * transform over the raised bra range, X'[p'][cd], contracted with W per
- * channel item) or ERI_GRAD_V (W contracted with the ket E products once per
- * quartet, V_k[ab][q], then each channel item's T from V and the auxiliary
- * integrals).  Both give the same derivatives to round-off; a cost model
- * picks the cheaper per launch.  ERI_EINVAL before any call.
- * eri_set_grad_forms -- restrict the planner to the forms in mask (bit
- * ERI_GRAD_X / ERI_GRAD_V set = allowed; 0 = both).  Returns the previous
- * mask, or ERI_EINVAL for a mask outside 0..3.  Process-wide; for testing.
- * A launch for which no tile of an allowed form fits in shared memory makes
- * eri_batch_grad return ERI_EINVAL (with both forms allowed, the X form's
- * smallest tile always fits for l <= ERI_LMAX and K <= ERI_KMAX).
+ * eri_last_grad_forms -- the forms the last eri_batch_grad call ran.
+ * The channels of a side come from one of two forms: ERI_GRAD_X (the
+ * forward ket transform over the raised bra range, X'[p'][cd], contracted
+ * with W per channel item) or ERI_GRAD_V (W contracted with the ket E
+ * products once per quartet, V_k[ab][q], then each channel item's T from V
+ * and the auxiliary integrals).  A call runs either one launch, whose bra
+ * channels take the X or V form and whose ket channels come from the same
+ * auxiliary integrals (Y'_k[ab][q'] = sum_i sum_p E^ab_{i,p} [p+q']_{ik}
+ * over the raised ket range, accumulated over the bra primitives), or two
+ * launches, the second with the sides exchanged.  *bra_form: the form of the
+ * first launch's bra channels; *ket_form: ERI_GRAD_ONE for the single
+ * launch, else the second launch's form.  All give the same derivatives to
+ * round-off; a cost model picks per call.  ERI_EINVAL before any call.
+ * eri_set_grad_forms -- restrict the planner (process-wide; for testing):
+ * bits ERI_GRAD_X and ERI_GRAD_V allow those forms, bit ERI_GRAD_ONE the
+ * single launch, bit ERI_GRAD_TWO two launches; a mask with neither of the
+ * last two bits means two launches; 0 allows everything.  Returns the
+ * previous mask, or ERI_EINVAL for a mask outside 0..15.  A call for which
+ * no tile of an allowed form fits in shared memory returns ERI_EINVAL (with
+ * everything allowed, the two-launch X form's smallest tile always fits for
+ * l <= ERI_LMAX and K <= ERI_KMAX).
  */
 #define ERI_GRAD_X 0
 #define ERI_GRAD_V 1
+#define ERI_GRAD_ONE 2
+#define ERI_GRAD_TWO 3
 int eri_last_grad_forms(int32_t* bra_form, int32_t* ket_form);
 int eri_set_grad_forms(int32_t mask);
 

@@ -49,7 +49,7 @@ EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_er
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
-ERI_GRAD_X, ERI_GRAD_V = 0, 1
+ERI_GRAD_X, ERI_GRAD_V, ERI_GRAD_ONE, ERI_GRAD_TWO = 0, 1, 2, 3
 PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS = 0, 1, 2, 3
 
 
@@ -326,7 +326,8 @@ def eri_last_form() -> tuple:
 
 
 def eri_set_grad_forms(mask: int) -> int:
-    """Restrict eri_batch_grad's forms (bit ERI_GRAD_X / ERI_GRAD_V, 0 = both); returns the previous mask."""
+    """Restrict eri_batch_grad's forms: bits ERI_GRAD_X / ERI_GRAD_V (a side's form), ERI_GRAD_ONE (single
+    launch), ERI_GRAD_TWO (two launches); no launch bit = two launches; 0 = everything.  Returns the previous mask."""
     code = lib().eri_set_grad_forms(int(mask))
     if code < 0:
         _check(code, "eri_set_grad_forms")
@@ -334,7 +335,8 @@ def eri_set_grad_forms(mask: int) -> int:
 
 
 def eri_last_grad_forms() -> tuple:
-    """(bra-channel form, ket-channel form) of the last eri_batch_grad call: ERI_GRAD_X or ERI_GRAD_V."""
+    """(bra-channel form, ket-channel form) of the last eri_batch_grad call: ERI_GRAD_X or ERI_GRAD_V, and
+    ERI_GRAD_ONE as the ket form when one launch produced every channel."""
     b = ctypes.c_int32()
     k = ctypes.c_int32()
     _check(lib().eri_last_grad_forms(ctypes.byref(b), ctypes.byref(k)), "eri_last_grad_forms")

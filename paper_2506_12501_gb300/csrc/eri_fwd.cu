@@ -672,21 +672,24 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
     const size_t nb_ps = align_up(sizeof(double) * nbra * *KB * PS_N), nb_E = align_up(sizeof(double) * nbra * *KB * ct->Tab);
     const size_t nk_ps = align_up(sizeof(double) * nket * *KK * PS_N), nk_E = align_up(sizeof(double) * nket * *KK * ct->Tcd);
     const size_t nb_k = align_up(sizeof(int32_t) * nbra), nk_k = align_up(sizeof(int32_t) * nket);
-    const int grad = ldelta > 0;
+    // ldelta 1: the raised tables of the kernel bra only (the adjoint launch
+    // for one side's channels); 2: of both sides, with the E products of
+    // both (the adjoint launch for every channel)
+    const int grad = ldelta > 0, grad_both = ldelta > 1;
     const int eaxb = (cls.la + 3) * (cls.lb + 3) * (cls.la + cls.lb + 5);
     const int eaxk = (cls.lc + 3) * (cls.ld + 3) * (cls.lc + cls.ld + 5);
     const size_t nb_ax = grad ? align_up(sizeof(double) * nbra * *KB * 3 * eaxb) : 0;
-    const size_t nk_ax = 0;  // the adjoint reads the raised tables of its (kernel) bra side only
+    const size_t nk_ax = grad_both ? align_up(sizeof(double) * nket * *KK * 3 * eaxk) : 0;
     const size_t nb_z = grad ? align_up(sizeof(double) * nbra * *KB * 2) : 0;
-    const size_t nk_z = 0;
+    const size_t nk_z = grad_both ? align_up(sizeof(double) * nket * *KK * 2) : 0;
     uint8_t* ws = (uint8_t*)workspace(nb_ps + nb_E + nk_ps + nk_E + nb_k + nk_k + nb_ax + nk_ax + nb_z + nk_z, &err);
     if (!ws) return err;
     {
         uint8_t* g0 = ws + nb_ps + nb_E + nk_ps + nk_E + nb_k + nk_k;
         pb->ax = grad ? (double*)g0 : nullptr;
-        pk->ax = nullptr;
+        pk->ax = grad_both ? (double*)(g0 + nb_ax) : nullptr;
         pb->zz = grad ? (double*)(g0 + nb_ax + nk_ax) : nullptr;
-        pk->zz = nullptr;
+        pk->zz = grad_both ? (double*)(g0 + nb_ax + nk_ax + nb_z) : nullptr;
         pb->eax = eaxb;
         pk->eax = eaxk;
     }
@@ -725,6 +728,12 @@ int prepare_batch(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra,
         const int64_t tot = p.npairs * p.KS;
         const int g = (int)std::min<int64_t>((tot + 127) / 128, 8 * sm_count());
         ProfScope ps(PROF_PAIR, st);
+        if (grad_both) {  // the E products as well as the raised tables (both write the same pair scalars)
+            PairArgs pe = p;
+            pe.ax = nullptr;
+            pe.zz = nullptr;
+            launch_pair(pe, std::max(g, 1), st);
+        }
         launch_pair(p, std::max(g, 1), st);
         if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
     }

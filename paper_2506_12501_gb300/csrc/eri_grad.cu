@@ -73,6 +73,18 @@ struct GradArgs {
     int o_V, o_pq;
     int o_q, o_W, o_Pb, o_Pk, o_Ek, o_D, o_R, o_X, o_ch;
     int64_t ntiles;
+    // one launch for every channel (both = 1): the ket's channels from the
+    // same auxiliary integrals, through
+    //   Y'_k[ab][q'] = sum_i sum_p E^ab_{i,p} [p+q']^(0)_{ik}   (q' over the raised ket range)
+    //   T_k[cd][q']  = (-1)^{|q'|} sum_ab W_abcd Y'_k[ab][q'],
+    // folded into the ket channels per (quartet, ket primitive) at the end of a tile
+    int both;
+    const int32_t* ket_sh;     // the kernel's ket pairs as shell indices [nket_k][2]
+    const int2* kitems;        // channel items of the ket class (lc, ld)
+    int nitk;
+    int NDk, PSTk;             // ket derived-table entries per axis and value; doubles per (quartet, ket primitive)
+    int Ebs, Ys;               // strides: staged bra E products per quartet, Y' per (quartet, ket primitive) (odd)
+    int o_Eb, o_Y, o_Dk, o_chk;
 };
 
 __device__ __forceinline__ void g_pairs(const GradArgs& a, int64_t qq, int* b, int* k)
@@ -196,10 +208,113 @@ __constant__ double c_int_d[8] = {0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0};
 // Forms of the last eri_batch_grad call's two launches (eri_last_grad_forms),
 // and the forms the planner may pick (eri_set_grad_forms): bit f allows form f.
 static int g_last_grad_form[2] = {-1, -1};
-static std::atomic<int> g_grad_form_mask{3};
+// bits: ERI_GRAD_X, ERI_GRAD_V (forms of a launch's own channels), 2: the
+// single launch, 3: two launches; a mask without bits 2 and 3 means two launches
+static std::atomic<int> g_grad_form_mask{0xF};
 
 // Derived-table entries per axis and value: (la+1)(lb+1)(la+lb+3).
 static int derived_entries(int la, int lb) { return (la + 1) * (lb + 1) * (la + lb + 3); }
+
+// Total order N = t+u+v of Hermite function e (tetrahedral numbering).
+__device__ __forceinline__ int herm_order(int e)
+{
+    int N = 0;
+    while ((N + 1) * (N + 2) * (N + 3) / 6 <= e) ++N;
+    return N;
+}
+
+// Folds one channel item's T value y into the 8 channel sums of its side:
+// Dx, Dy, Dz point at the item's entry of the per-axis derived tables
+// (components 0..4 at strides ND: E, the two centre-derivative factors, the
+// two exponent-derivative factors); kind as in the item table.
+__device__ __forceinline__ void fold_item(double y, const double* Dx, const double* Dy, const double* Dz, int ND,
+                                          int kind, double (&ch)[8])
+{
+    switch (kind) {
+        case 0: {  // every channel
+            const double ex = Dx[0], ey = Dy[0], ez = Dz[0];
+            const double yx = y * ex;
+            const double pyz = y * ey * ez, pxz = yx * ez, pxy = yx * ey;
+            ch[0] = fma(Dx[ND], pyz, ch[0]);
+            ch[3] = fma(Dx[2 * ND], pyz, ch[3]);
+            ch[6] = fma(Dx[3 * ND], pyz, ch[6]);
+            ch[7] = fma(Dx[4 * ND], pyz, ch[7]);
+            ch[1] = fma(Dy[ND], pxz, ch[1]);
+            ch[4] = fma(Dy[2 * ND], pxz, ch[4]);
+            ch[6] = fma(Dy[3 * ND], pxz, ch[6]);
+            ch[7] = fma(Dy[4 * ND], pxz, ch[7]);
+            ch[2] = fma(Dz[ND], pxy, ch[2]);
+            ch[5] = fma(Dz[2 * ND], pxy, ch[5]);
+            ch[6] = fma(Dz[3 * ND], pxy, ch[6]);
+            ch[7] = fma(Dz[4 * ND], pxy, ch[7]);
+            break;
+        }
+        case 1: {  // above by 1 on x: the x centre channels and the exponents
+            const double r = y * Dy[0] * Dz[0];
+            ch[0] = fma(Dx[ND], r, ch[0]);
+            ch[3] = fma(Dx[2 * ND], r, ch[3]);
+            ch[6] = fma(Dx[3 * ND], r, ch[6]);
+            ch[7] = fma(Dx[4 * ND], r, ch[7]);
+            break;
+        }
+        case 2: {
+            const double r = y * Dx[0] * Dz[0];
+            ch[1] = fma(Dy[ND], r, ch[1]);
+            ch[4] = fma(Dy[2 * ND], r, ch[4]);
+            ch[6] = fma(Dy[3 * ND], r, ch[6]);
+            ch[7] = fma(Dy[4 * ND], r, ch[7]);
+            break;
+        }
+        case 3: {
+            const double r = y * Dx[0] * Dy[0];
+            ch[2] = fma(Dz[ND], r, ch[2]);
+            ch[5] = fma(Dz[2 * ND], r, ch[5]);
+            ch[6] = fma(Dz[3 * ND], r, ch[6]);
+            ch[7] = fma(Dz[4 * ND], r, ch[7]);
+            break;
+        }
+        case 4: {  // above by 2 on x: the exponents only
+            const double r = y * Dy[0] * Dz[0];
+            ch[6] = fma(Dx[3 * ND], r, ch[6]);
+            ch[7] = fma(Dx[4 * ND], r, ch[7]);
+            break;
+        }
+        case 5: {
+            const double r = y * Dx[0] * Dz[0];
+            ch[6] = fma(Dy[3 * ND], r, ch[6]);
+            ch[7] = fma(Dy[4 * ND], r, ch[7]);
+            break;
+        }
+        default: {
+            const double r = y * Dx[0] * Dy[0];
+            ch[6] = fma(Dz[3 * ND], r, ch[6]);
+            ch[7] = fma(Dz[4 * ND], r, ch[7]);
+            break;
+        }
+    }
+}
+
+// The per-axis derived tables of one primitive pair (a side's 5 components
+// per axis, see the bra's stage in the kernel) from its raised E tables:
+// out[(x 5 + c) ND + e], e = (i nbd + j) ntd + t.
+__device__ __forceinline__ void derived_entry(const double* __restrict__ ax, const double* __restrict__ zz, int eax,
+                                              int l1, int l2, int x, int e, double* o, int ND)
+{
+    const int n2 = l2 + 3, nte = l1 + l2 + 5, nbd = l2 + 1, ntd = l1 + l2 + 3;
+    const int t = e % ntd, ij = e / ntd, jj = ij % nbd, ii = ij / nbd;
+    const double* A = ax + (size_t)x * eax + t;
+    const double tz1 = 2.0 * zz[0], tz2 = 2.0 * zz[1];
+    const int r0 = ii * n2 + jj;
+    double v1 = tz1 * A[(r0 + n2) * nte];
+    if (ii) v1 = fma(-c_int_d[ii], A[(r0 - n2) * nte], v1);
+    double v2 = tz2 * A[(r0 + 1) * nte];
+    if (jj) v2 = fma(-c_int_d[jj], A[(r0 - 1) * nte], v2);
+    o[0] = A[r0 * nte];
+    o[ND] = v1;
+    o[2 * ND] = v2;
+    o[3 * ND] = -A[(r0 + 2 * n2) * nte];
+    o[4 * ND] = -A[(r0 + 2) * nte];
+}
 
 __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
 {
@@ -229,6 +344,9 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     double* sX = sm + a.o_X;
     double* sC8 = sm + a.o_ch;
     double* sV = sm + a.o_V;
+    double* sEb = sm + a.o_Eb;
+    double* sY = sm + a.o_Y;
+    double* sCk = sm + a.o_chk;
     int16_t* s_pq = reinterpret_cast<int16_t*>(sm + a.o_pq);
     const int Vs = a.Vs;
     if (a.vform) {  // the p'+q table, read for every V-form term
@@ -294,6 +412,17 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
             sW[(size_t)q * Ws + r] = q < nqt ? a.W[g_windex(a, s_qq[q], r / ncd, r % ncd)] : 0.0;
         }
         for (int idx = tid; idx < TQ * IC * 8; idx += kGT) sC8[idx] = 0.0;
+        if (a.both) {
+            // the bra E products of the tile ([q][t][i], no sign), zeroed Y'
+            // and ket channel sums
+            const int nb = KB * ct.Tab;
+            for (int idx = tid; idx < TQ * nb; idx += kGT) {
+                const int q = idx / nb, r = idx - q * nb, i = r % KB;
+                sEb[(size_t)q * a.Ebs + r] = i < s_q[4 * q + 2] ? a.pb.E[(size_t)s_q[4 * q] * nb + r] : 0.0;
+            }
+            for (int idx = tid; idx < TQ * KK * a.Ys; idx += kGT) sY[idx] = 0.0;
+            for (int idx = tid; idx < TQ * KK * 8; idx += kGT) sCk[idx] = 0.0;
+        }
         if (a.vform) {
             // ---- V: V[q][k][ab][qh] = sum over the terms t = (cd, qh) of
             // W[q][ab][cd] E[q][t][k] (the caller's W met with the ket transform)
@@ -501,68 +630,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                             const double* Dx = Dq + (g.y & 1023);
                             const double* Dy = Dq + 5 * ND + ((g.y >> 10) & 1023);
                             const double* Dz = Dq + 10 * ND + (g.y >> 20);
-                            switch (g.x >> 20) {
-                                case 0: {  // every channel
-                                    const double ex = Dx[0], ey = Dy[0], ez = Dz[0];
-                                    const double yx = y * ex;
-                                    const double pyz = y * ey * ez, pxz = yx * ez, pxy = yx * ey;
-                                    ch[0] = fma(Dx[ND], pyz, ch[0]);
-                                    ch[3] = fma(Dx[2 * ND], pyz, ch[3]);
-                                    ch[6] = fma(Dx[3 * ND], pyz, ch[6]);
-                                    ch[7] = fma(Dx[4 * ND], pyz, ch[7]);
-                                    ch[1] = fma(Dy[ND], pxz, ch[1]);
-                                    ch[4] = fma(Dy[2 * ND], pxz, ch[4]);
-                                    ch[6] = fma(Dy[3 * ND], pxz, ch[6]);
-                                    ch[7] = fma(Dy[4 * ND], pxz, ch[7]);
-                                    ch[2] = fma(Dz[ND], pxy, ch[2]);
-                                    ch[5] = fma(Dz[2 * ND], pxy, ch[5]);
-                                    ch[6] = fma(Dz[3 * ND], pxy, ch[6]);
-                                    ch[7] = fma(Dz[4 * ND], pxy, ch[7]);
-                                    break;
-                                }
-                                case 1: {  // above by 1 on x: A_x, B_x and the exponents
-                                    const double r = y * Dy[0] * Dz[0];
-                                    ch[0] = fma(Dx[ND], r, ch[0]);
-                                    ch[3] = fma(Dx[2 * ND], r, ch[3]);
-                                    ch[6] = fma(Dx[3 * ND], r, ch[6]);
-                                    ch[7] = fma(Dx[4 * ND], r, ch[7]);
-                                    break;
-                                }
-                                case 2: {
-                                    const double r = y * Dx[0] * Dz[0];
-                                    ch[1] = fma(Dy[ND], r, ch[1]);
-                                    ch[4] = fma(Dy[2 * ND], r, ch[4]);
-                                    ch[6] = fma(Dy[3 * ND], r, ch[6]);
-                                    ch[7] = fma(Dy[4 * ND], r, ch[7]);
-                                    break;
-                                }
-                                case 3: {
-                                    const double r = y * Dx[0] * Dy[0];
-                                    ch[2] = fma(Dz[ND], r, ch[2]);
-                                    ch[5] = fma(Dz[2 * ND], r, ch[5]);
-                                    ch[6] = fma(Dz[3 * ND], r, ch[6]);
-                                    ch[7] = fma(Dz[4 * ND], r, ch[7]);
-                                    break;
-                                }
-                                case 4: {  // above by 2 on x: the exponents only
-                                    const double r = y * Dy[0] * Dz[0];
-                                    ch[6] = fma(Dx[3 * ND], r, ch[6]);
-                                    ch[7] = fma(Dx[4 * ND], r, ch[7]);
-                                    break;
-                                }
-                                case 5: {
-                                    const double r = y * Dx[0] * Dz[0];
-                                    ch[6] = fma(Dy[3 * ND], r, ch[6]);
-                                    ch[7] = fma(Dy[4 * ND], r, ch[7]);
-                                    break;
-                                }
-                                default: {
-                                    const double r = y * Dx[0] * Dy[0];
-                                    ch[6] = fma(Dz[3 * ND], r, ch[6]);
-                                    ch[7] = fma(Dz[4 * ND], r, ch[7]);
-                                    break;
-                                }
-                            }
+                            fold_item(y, Dx, Dy, Dz, ND, g.x >> 20, ch);
                         }
                     }
                     for (int o = G >> 1; o > 0; o >>= 1)
@@ -592,8 +660,131 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                         atomicAdd(&a.ge[a.shell_off[sb] + i2], e[1]);
                     }
                 }
+            if (a.both) {
+                // ---- K1: Y'[q][k][ab][q'] += sum_ii sum_{p in nz(ab)} E^ab_{i0+ii,p}
+                // R_{ii,k}[p+q'], q' over the raised ket range (the auxiliary
+                // integrals of this chunk are still in place)
+                const int nhk2 = ct.nhk2, Ys = a.Ys;
+                const int nK1 = TQ * KKt * nab * nhk2;
+                for (int item = tid; item < nK1; item += kGT) {
+                    const int q = item % TQ;
+                    int r = item / TQ;
+                    const int qp = r % nhk2;
+                    r /= nhk2;
+                    const int ab = r % nab, k = r / nab;
+                    if (k >= s_q[4 * q + 3]) continue;
+                    const double* Eq = sEb + (size_t)q * a.Ebs + i0;  // + t KB + ii
+                    const double* Rq = sR + q + (size_t)TQ * IC * k;   // + e NIs + ii TQ
+                    double y0 = 0.0, y1 = 0.0;
+                    const int t0 = __ldg(ct.bra_start + ab), t1 = __ldg(ct.bra_start + ab + 1);
+                    for (int t = t0; t < t1; ++t) {
+                        const int e = __ldg(ct.pq2k + (int)__ldg(ct.bra_p + t) * nhk2 + qp);
+                        const double* Et = Eq + t * KB;
+                        const double* Re = Rq + (size_t)e * NIs;
+                        int ii = 0;
+                        for (; ii + 1 < ICe; ii += 2) {
+                            y0 = fma(Et[ii], Re[ii * TQ], y0);
+                            y1 = fma(Et[ii + 1], Re[(ii + 1) * TQ], y1);
+                        }
+                        if (ii < ICe) y0 = fma(Et[ii], Re[ii * TQ], y0);
+                    }
+                    sY[((size_t)q * KK + k) * Ys + ab * nhk2 + qp] += y0 + y1;
+                }
+            }
         }
         __syncthreads();
+        if (a.both) {
+            // ---- K2: the ket's derived tables per (quartet, ket primitive), in
+            // the auxiliary-integral region (dead now)
+            const int NDk = a.NDk, PSTk = a.PSTk;
+            double* sDk = sR;
+            for (int idx = tid; idx < TQ * KKt * 3 * NDk; idx += kGT) {
+                const int e = idx % NDk;
+                int r = idx / NDk;
+                const int x = r % 3;
+                r /= 3;
+                const int q = r % TQ, k = r / TQ;
+                double* o = sDk + ((size_t)q * KK + k) * PSTk + x * 5 * NDk + e;
+                if (k < s_q[4 * q + 3]) {
+                    const size_t slot = (size_t)s_q[4 * q + 1] * KK + k;
+                    derived_entry(a.pk.ax + slot * 3 * a.pk.eax, a.pk.zz + 2 * slot, a.pk.eax, ct.lc, ct.ld, x, e,
+                                  o, NDk);
+                } else {
+                    for (int c = 0; c < 5; ++c) o[c * NDk] = 0.0;
+                }
+            }
+            __syncthreads();
+            // ---- K3: the ket's channel items per (quartet, ket primitive):
+            // T = (-1)^{|q'|} sum_ab W[q][ab][cd] Y'[q][k][ab][q'], folded into
+            // the 8 ket channels by lane groups as in C+D
+            const int nhk2 = ct.nhk2, Ys = a.Ys, nitk = a.nitk;
+            int G = 1;
+            {
+                int best = -1;
+                for (int g = 1; g <= 32; g *= 2) {
+                    const int c = ((TQ * KKt * g + kGT - 1) / kGT) * ((nitk + g - 1) / g) * (nab + 20) +
+                                  24 * (__ffs(g) - 1);
+                    if (best < 0 || c < best) {
+                        best = c;
+                        G = g;
+                    }
+                }
+            }
+            const int sl = tid & (G - 1), NG = kGT / G;
+            const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((tid & 31) & ~(G - 1));
+            for (int combo = tid / G; combo < TQ * KKt; combo += NG) {
+                const int q = combo % TQ, k = combo / TQ;
+                const bool live = k < s_q[4 * q + 3];  // the same for the whole group
+                double ch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                if (live) {
+                    const double* wq = sW + (size_t)q * Ws;
+                    const double* yq = sY + ((size_t)q * KK + k) * Ys;
+                    const double* Dq = sDk + ((size_t)q * KK + k) * PSTk;
+                    for (int j = sl; j < nitk; j += G) {
+                        const int2 g = __ldg(a.kitems + j);
+                        const int cd = g.x & 1023, qp = (g.x >> 10) & 1023;
+                        const double* yv = yq + qp;
+                        double ya = 0.0, yb = 0.0;
+                        int ab = 0;
+                        for (; ab + 1 < nab; ab += 2) {
+                            ya = fma(wq[ab * ncd + cd], yv[ab * nhk2], ya);
+                            yb = fma(wq[(ab + 1) * ncd + cd], yv[(ab + 1) * nhk2], yb);
+                        }
+                        if (ab < nab) ya = fma(wq[ab * ncd + cd], yv[ab * nhk2], ya);
+                        const double y = (herm_order(qp) & 1) ? -(ya + yb) : ya + yb;
+                        fold_item(y, Dq + (g.y & 1023), Dq + 5 * NDk + ((g.y >> 10) & 1023),
+                                  Dq + 10 * NDk + (g.y >> 20), NDk, g.x >> 20, ch);
+                    }
+                }
+                for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) ch[c] += __shfl_xor_sync(gmask, ch[c], o);
+                if (live && sl == 0) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) sCk[((size_t)q * KK + k) * 8 + c] = ch[c];
+                    if (a.ge) {  // exponent channels of ket primitive k
+                        const int sc = a.ket_sh[2 * s_q[4 * q + 1]], sd = a.ket_sh[2 * s_q[4 * q + 1] + 1];
+                        const int K2 = a.shell_K[sd], k1 = k / K2, k2 = k - k1 * K2;
+                        atomicAdd(&a.ge[a.shell_off[sc] + k1], ch[6]);
+                        atomicAdd(&a.ge[a.shell_off[sd] + k2], ch[7]);
+                    }
+                }
+            }
+            __syncthreads();
+            // centre channels of the ket (summed over the ket primitives)
+            if (a.gc)
+                for (int q = tid; q < nqt; q += kGT) {
+                    const int sc = a.ket_sh[2 * s_q[4 * q + 1]], sd = a.ket_sh[2 * s_q[4 * q + 1] + 1];
+                    double c6[6] = {0, 0, 0, 0, 0, 0};
+                    for (int k = 0; k < KKt; ++k)
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) c6[c] += sCk[((size_t)q * KK + k) * 8 + c];
+                    for (int x = 0; x < 3; ++x) {
+                        atomicAdd(&a.gc[3 * a.shell_atom[sc] + x], c6[x]);
+                        atomicAdd(&a.gc[3 * a.shell_atom[sd] + x], c6[3 + x]);
+                    }
+                }
+        }
         // centre channels of the tile's quartets (summed over the IC slots)
         if (a.gc)
             for (int q = tid; q < nqt; q += kGT) {
@@ -610,7 +801,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
     }
 }
 
-static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int vform, GradArgs* a,
+static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int vform, int both, GradArgs* a,
                         size_t* bytes)
 {
     size_t off = 0;
@@ -623,13 +814,19 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, i
     a->PST = (15 * a->ND) | 1;
     a->Ws = (ct.nab * ct.ncd) | 1;
     a->Eks = (KK * ct.Tcd) | 1;
+    a->NDk = derived_entries(ct.lc, ct.ld);
+    a->PSTk = (15 * a->NDk) | 1;
+    a->Ebs = both ? (KB * ct.Tab) | 1 : 0;
+    a->Ys = both ? (ct.nab * ct.nhk2) | 1 : 0;
     a->o_q = take((size_t)TQ * 3);  // (b, k, kb, kk) as int32, then the quartet index
     a->o_W = take((size_t)TQ * a->Ws);
     a->o_Pb = take((size_t)TQ * KB * PS_N);
     a->o_Pk = take((size_t)TQ * KK * PS_N);
     a->o_Ek = take((size_t)TQ * a->Eks);
     a->o_D = take((size_t)TQ * IC * a->PST);
-    a->o_R = take((size_t)ct.nhl2 * ((TQ * IC * KK) | 1));
+    // the auxiliary integrals; at the end of a tile the ket's derived tables
+    // take their place (single launch)
+    a->o_R = take(std::max((size_t)ct.nhl2 * ((TQ * IC * KK) | 1), both ? (size_t)TQ * KK * a->PSTk : 0));
     a->Xs = ct.ncd | 1;
     a->XQ = (ct.nhb2 * a->Xs) | 1;
     a->o_X = take(vform ? 0 : (size_t)a->XQ * TQ * IC);
@@ -637,10 +834,15 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, i
     a->Vs = (KK * ct.nab * ct.nhk) | 1;
     a->o_V = take(vform ? (size_t)TQ * a->Vs : 0);
     a->o_pq = take(vform ? ((size_t)ct.nhb2 * ct.nhk * 2 + 7) / 8 : 0);
+    a->o_Eb = take((size_t)TQ * a->Ebs);
+    a->o_Y = take((size_t)TQ * KK * a->Ys);
+    a->o_chk = take(both ? (size_t)TQ * KK * 8 : 0);
+    a->o_Dk = a->o_R;
     *bytes = off * 8;
     a->TQ = TQ;
     a->IC = IC;
     a->vform = vform;
+    a->both = both;
     return *bytes <= (size_t)max_smem_optin();
 }
 
@@ -650,41 +852,49 @@ static bool grad_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, i
 // barrier; a tile makes ceil(KB / IC) passes.  The X form's pass forms X'
 // over every (p', cd) and contracts it with W per channel item; the V form
 // contracts W with the ket E products once per tile and forms each channel
-// item's T from V and the auxiliary integrals.  Shapes that leave room for
-// two CTAs per SM (so one CTA's barriers overlap the other's work) are
-// preferred whenever one exists.
-static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int64_t nq, size_t limit, GradArgs* a,
-                             size_t* bytes);
+// item's T from V and the auxiliary integrals.  A single launch (both = 1)
+// adds, per pass, Y' over (k, ab, q') and, per tile, the ket's derived tables
+// and channel items.  Shapes that leave room for two CTAs per SM (so one
+// CTA's barriers overlap the other's work) are preferred whenever one exists.
+// *cost_out: the modelled time per quartet of the pick.
+static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int nitk, int64_t nq, int both,
+                             size_t limit, GradArgs* a, size_t* bytes, double* cost_out);
 
-static bool grad_plan(const ClassTables& ct, int KB, int KK, int nit, int64_t nq, GradArgs* a, size_t* bytes)
+static bool grad_plan(const ClassTables& ct, int KB, int KK, int nit, int nitk, int64_t nq, int both, GradArgs* a,
+                      size_t* bytes, double* cost_out)
 {
     const size_t two_per_sm = (size_t)smem_per_sm() / 2 - 1024;
     for (int pass = 0; pass < 2; ++pass) {
-        if (grad_plan_within(ct, KB, KK, nit, nq, pass == 0 ? two_per_sm : (size_t)max_smem_optin(), a, bytes))
+        if (grad_plan_within(ct, KB, KK, nit, nitk, nq, both, pass == 0 ? two_per_sm : (size_t)max_smem_optin(), a,
+                             bytes, cost_out))
             return true;
     }
     return false;
 }
 
-static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int64_t nq, size_t limit, GradArgs* a,
-                             size_t* bytes)
+static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int nitk, int64_t nq, int both,
+                             size_t limit, GradArgs* a, size_t* bytes, double* cost_out)
 {
     double best = -1.0;
     GradArgs pick{};
     size_t pick_bytes = 0;
-    const int ND = derived_entries(ct.la, ct.lb);
+    const int ND = derived_entries(ct.la, ct.lb), NDk = derived_entries(ct.lc, ct.ld);
+    const int forms = (g_grad_form_mask.load() & 3) ? (g_grad_form_mask.load() & 3) : 3;  // neither bit: both
     for (int vform = 0; vform < 2; ++vform)
     for (int TQ = 32; TQ >= 1; TQ /= 2) {
-        if (!(g_grad_form_mask.load() >> vform & 1)) break;
+        if (!(forms >> vform & 1)) break;
         if (TQ > 1 && TQ > nq) continue;
         for (int IC = KB; IC >= 1; IC = IC == 1 ? 0 : (IC + 1) / 2) {
             GradArgs t = *a;
             size_t b = 0;
-            if (!grad_layout(ct, KB, KK, TQ, IC, vform, &t, &b) || b > limit) continue;
+            if (!grad_layout(ct, KB, KK, TQ, IC, vform, both, &t, &b) || b > limit) continue;
             auto rounds = [](double n) { return std::ceil(n / kGT); };
             const double kBarrier = 60.0;
-            const double common = rounds((double)TQ * IC * KK) * (3.0 * ct.nhl2 + 60.0) +
-                                  rounds((double)TQ * IC * 3 * ND) * 14.0;
+            double common = rounds((double)TQ * IC * KK) * (3.0 * ct.nhl2 + 60.0) +
+                            rounds((double)TQ * IC * 3 * ND) * 14.0;
+            if (both)  // Y' of the chunk: per (q, k, ab, q') its terms over the chunk's bra primitives
+                common += rounds((double)TQ * KK * ct.nab * ct.nhk2) * ((2.0 * IC + 3.0) * ct.Tab / ct.nab + 10.0) +
+                          kBarrier;
             double cost;
             // a term's index lookup and scattered load cost about as much as
             // its FMAs over the ket primitives: weight 2 KK + 1.5 (X's ket
@@ -693,14 +903,18 @@ static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int
                 const double pass =
                     common + rounds((double)TQ * IC * ct.nhb2 * ct.ncd) * ((2.0 * KK + 1.5) * ct.Tcd / ct.ncd + 8.0) +
                     rounds((double)TQ * IC * nit) * (2.0 * ct.ncd + 40.0) + 4.0 * kBarrier;
-                cost = std::ceil((double)KB / IC) * pass / TQ;
+                cost = std::ceil((double)KB / IC) * pass;
             } else {
                 const double pass =
                     common + rounds((double)TQ * IC * nit) * ((2.0 * KK + 2.5) * ct.nhk + 40.0) + 3.0 * kBarrier;
                 const double vstage =
                     rounds((double)TQ * KK * ct.nab * ct.nhk) * (3.5 * ct.Tcd / ct.nhk + 8.0) + kBarrier;
-                cost = (vstage + std::ceil((double)KB / IC) * pass) / TQ;
+                cost = vstage + std::ceil((double)KB / IC) * pass;
             }
+            if (both)  // the ket's derived tables and channel items, once per tile
+                cost += rounds((double)TQ * KK * 3 * NDk) * 16.0 + rounds((double)TQ * KK * nitk) * (2.0 * ct.nab + 40.0) +
+                        3.0 * kBarrier;
+            cost /= TQ;
             if (best < 0 || cost < best) {
                 best = cost;
                 pick = t;
@@ -711,6 +925,7 @@ static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int
     if (best < 0) return false;
     *a = pick;
     *bytes = pick_bytes;
+    if (cost_out) *cost_out = best;
     return true;
 }
 
@@ -773,15 +988,19 @@ struct GradOrder {
 // lists (the caller's ket/bra when swap = 1); nbra_o/nket_o are the caller's.
 static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                        int64_t nket, const int64_t* quartets, int64_t nq, const double* W, double* gc, double* ge,
-                       int swap, int64_t nbra_o, int64_t nket_o, GradOrder* ord, cudaStream_t st)
+                       int swap, int64_t nbra_o, int64_t nket_o, GradOrder* ord, cudaStream_t st, int* did_both)
 {
     const ClassTables* ct = nullptr;
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
+    // the first launch may produce every channel (pair tables of both sides
+    // raised, E products of both); otherwise each launch its bra's
+    const int mask = g_grad_form_mask.load();
+    const bool allow_one = !swap && (mask & 4), allow_two = (mask & 8) || !(mask & 12);
     // the quartet indices refer to the caller's lists: validated on the first launch only
     int mixed = 0;
-    int err = prepare_batch(cls, basis, bra, nbra, ket, nket, swap ? nullptr : quartets, swap ? 0 : nq, 2, st, &ct,
-                            &pb, &pk, &KB, &KK, kmax, 0, nullptr, 0, 0, &mixed);
+    int err = prepare_batch(cls, basis, bra, nbra, ket, nket, swap ? nullptr : quartets, swap ? 0 : nq,
+                            allow_one ? 2 : 1, st, &ct, &pb, &pk, &KB, &KK, kmax, 0, nullptr, 0, 0, &mixed);
     if (err != ERI_OK) return err;
     if (ct->L + 2 > kLtotMax) return ERI_EINVAL;
     GradArgs a{};
@@ -792,6 +1011,7 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     a.pb = pb;
     a.pk = pk;
     a.bra_sh = bra;
+    a.ket_sh = ket;
     a.shell_atom = basis->shell_atom;
     a.shell_off = basis->shell_off;
     a.shell_K = basis->shell_K;
@@ -811,13 +1031,40 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     if (!items) return err;
     a.items = items->list[ct->la][ct->lb];
     a.nit = items->n[ct->la][ct->lb];
+    a.kitems = items->list[ct->lc][ct->ld];
+    a.nitk = items->n[ct->lc][ct->ld];
     const VList* vl = get_vlist(*ct, st, &err);
     if (!vl) return err;
     a.vstart = vl->vstart;
     a.vlist = vl->vlist;
     size_t bytes = 0;
-    if (!grad_plan(*ct, KB, KK, a.nit, a.nq, &a, &bytes)) return ERI_EINVAL;
+    bool one = false;
+    if (allow_one) {
+        // one launch for every channel, unless the model puts two launches
+        // (this side's channels, then the other side's) below it
+        GradArgs a1 = a;
+        size_t b1 = 0;
+        double c1 = 0.0;
+        one = grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 1, &a1, &b1, &c1);
+        if (one && allow_two) {
+            GradArgs a0 = a, as = a;
+            size_t b0 = 0, bs = 0;
+            double c0 = 0.0, cs = 0.0;
+            const ClassTables* ctk = get_class_tables(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
+            if (!ctk) return err;
+            if (grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 0, &a0, &b0, &c0) &&
+                grad_plan(*ctk, KK, KB, a.nitk, a.nit, a.nq, 0, &as, &bs, &cs) && c0 + cs < c1)
+                one = false;
+        }
+        if (one) {
+            a = a1;
+            bytes = b1;
+        }
+    }
+    if (!one && !grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 0, &a, &bytes, nullptr)) return ERI_EINVAL;
+    if (did_both) *did_both = one ? 1 : 0;
     g_last_grad_form[swap] = a.vform;
+    if (one) g_last_grad_form[1] = ERI_GRAD_ONE;
     a.ntiles = (a.nq + a.TQ - 1) / a.TQ;
     if (!ord->queue) {  // first launch: order (sorted if the batch mixes degrees); the second reuses it
         err = build_order(quartets, a.nq, nbra_o, pb.kp, pk.kp, KB, KK, swap, mixed, st, &ord->order, &ord->queue);
@@ -855,11 +1102,12 @@ extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const i
     // channels of the bra (a, b), then of the ket (c, d) with the sides exchanged
     GradOrder order;
     g_last_grad_form[0] = g_last_grad_form[1] = -1;
+    int both = 0;
     err = launch_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, grad_centres, grad_exps, 0, nbra,
-                      nket, &order, st);
-    if (err != ERI_OK) return err;
+                      nket, &order, st, &both);
+    if (err != ERI_OK || both) return err;
     return launch_grad(eri_class_t{cls.lc, cls.ld, cls.la, cls.lb}, basis, ket_pairs, nket, bra_pairs, nbra, quartets,
-                       nq, W, grad_centres, grad_exps, 1, nbra, nket, &order, st);
+                       nq, W, grad_centres, grad_exps, 1, nbra, nket, &order, st, nullptr);
 }
 
 extern "C" int eri_last_grad_forms(int32_t* bra_form, int32_t* ket_form)
@@ -873,6 +1121,6 @@ extern "C" int eri_last_grad_forms(int32_t* bra_form, int32_t* ket_form)
 
 extern "C" int eri_set_grad_forms(int32_t mask)
 {
-    if (mask < 0 || mask > 3) return ERI_EINVAL;
-    return g_grad_form_mask.exchange(mask ? mask : 3);
+    if (mask < 0 || mask > 0xF) return ERI_EINVAL;
+    return g_grad_form_mask.exchange(mask ? mask : 0xF);
 }

@@ -153,8 +153,9 @@ struct FormChoice {
 void remember_form(eri_class_t cls, int KB, int KK, int split, int kind, int form);
 
 // Prepass + pair tables shared by eri_batch, eri_batch3 and eri_batch_grad.
-// ldelta > 0 also fills the adjoint tables of the bra side (pb->ax, pb->zz;
-// the ket side's stay NULL).  Synchronises `st` once (reads
+// ldelta = 1 also fills the adjoint tables of the bra side (pb->ax, pb->zz;
+// the ket side's stay NULL, and the bra's E products are not formed);
+// ldelta = 2 fills the adjoint tables and the E products of both sides.  Synchronises `st` once (reads
 // the largest contraction degree of each centre).  allow_swap = 0: the plain
 // form as given; 1: plain or swapped; 2: any of the four forms.  kind = 0:
 // 4-centre; 1: 3-centre (the caller's bra pairs are (x, -1), -1 standing for

@@ -216,9 +216,27 @@ def _grad_launch_flops(cls, Kbra: int, Kket: int, vform: int = 0) -> int:
         Kbra * (channels + nit * 2 * ncd)
 
 
-def grad_flops(cls, Kbra: int, Kket: int, forms=(0, 0)) -> int:
-    """FP64 flops of the adjoint of one quartet: the bra channels, then the
-    ket channels in a second launch with the sides exchanged, each in its
-    form (eri_last_grad_forms)."""
+def _grad_ket_flops(cls, Kbra: int, Kket: int) -> int:
+    """FP64 flops of the ket channels in the single launch (eri_last_grad_forms
+    reports ERI_GRAD_ONE): per primitive quartet Y'[ab][q'] over the raised
+    ket range (2 Nh(lc+ld+2) Tab); per ket primitive the derived tables
+    (18 (lc+1)(ld+1)(lc+ld+3)) and, per ket channel item, T (2 nab) and its
+    channel terms (29, 10 or 6 flops by kind)."""
     la, lb, lc, ld = cls
+    nab = nc(la) * nc(lb)
+    n0, n1, n2 = grad_item_kinds(lc, ld)
+    nd = (lc + 1) * (ld + 1) * (lc + ld + 3)
+    per_k = 18 * nd + 29 * n0 + 10 * n1 + 6 * n2 + (n0 + n1 + n2) * 2 * nab
+    return Kbra * Kket * 2 * nh(lc + ld + 2) * terms(la, lb) + Kket * per_k
+
+
+def grad_flops(cls, Kbra: int, Kket: int, forms=(0, 0)) -> int:
+    """FP64 flops of the adjoint of one quartet in the forms of
+    eri_last_grad_forms: the bra channels in form forms[0]; the ket channels
+    either from the same launch (forms[1] = 2, ERI_GRAD_ONE: the auxiliary
+    integrals are computed once) or from a second launch with the sides
+    exchanged, in form forms[1]."""
+    la, lb, lc, ld = cls
+    if forms[1] == 2:
+        return _grad_launch_flops(cls, Kbra, Kket, forms[0]) + _grad_ket_flops(cls, Kbra, Kket)
     return _grad_launch_flops(cls, Kbra, Kket, forms[0]) + _grad_launch_flops((lc, ld, la, lb), Kket, Kbra, forms[1])

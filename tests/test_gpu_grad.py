@@ -40,7 +40,8 @@ def test_grad_against_oracle(cuda, cls, K):
     3 per shell (an odd K leaves a partial chunk of bra primitives), against
     the oracle's shifted-monomial derivative, in each of the two forms
     (X: ket transform over the raised bra range, then W; V: W met with the
-    ket E products first) forced in turn."""
+    ket E products first) forced in turn, each in two launches (one per
+    side's channels) and in one launch for every channel."""
     if K == 3 and sum(cls) > 6:
         pytest.skip("oracle time")
     basis, pools = synth.class_sweep_pools(seed=3, lmax=max(2, max(cls)), pool=24, K=K, cube=5.0)
@@ -53,18 +54,22 @@ def test_grad_against_oracle(cuda, cls, K):
     rc, re = oracle.eri_grad_quartets(basis, synth.quartet_shells(bra, ket, q), Wq, prec="d", threads=THREADS)
     try:
         for form in (eri.ERI_GRAD_X, eri.ERI_GRAD_V):
-            eri.eri_set_grad_forms(1 << form)
-            gc, ge = gpu_grad(cls, basis, bra, ket, q, W)
-            assert eri.eri_last_grad_forms() == (form, form)
-            grad_close(gc, rc, f"centres {cls} form {form}")
-            grad_close(ge, re, f"exponents {cls} form {form}")
-            assert abs(gc.sum(axis=0)).max() < 1e-10 * max(1.0, abs(gc).max())  # translation invariance
+            for one in (False, True):
+                # two launches (one per side's channels) or one launch for every channel
+                eri.eri_set_grad_forms((1 << form) | (1 << (eri.ERI_GRAD_ONE if one else eri.ERI_GRAD_TWO)))
+                gc, ge = gpu_grad(cls, basis, bra, ket, q, W)
+                ran = eri.eri_last_grad_forms()
+                assert ran == ((form, eri.ERI_GRAD_ONE) if one else (form, form))
+                grad_close(gc, rc, f"centres {cls} forms {ran}")
+                grad_close(ge, re, f"exponents {cls} forms {ran}")
+                assert abs(gc.sum(axis=0)).max() < 1e-10 * max(1.0, abs(gc).max())  # translation invariance
     finally:
         eri.eri_set_grad_forms(0)
 
 
+@pytest.mark.parametrize("one", [False, True])
 @pytest.mark.parametrize("form", [0, 1])
-def test_grad_mixed_K_and_product_form(cuda, form):
+def test_grad_mixed_K_and_product_form(cuda, form, one):
     basis = synth.molecule_basis(natom=5, radius=3.0, seed=2)
     pairs = synth.unique_pairs(basis)
     sel = pairs[(basis.shell_l[pairs[:, 0]] == 1) & (basis.shell_l[pairs[:, 1]] == 0)][:9]
@@ -77,9 +82,9 @@ def test_grad_mixed_K_and_product_form(cuda, form):
     gc = torch.zeros_like(db.centres)
     ge = torch.zeros_like(db.exps)
     try:
-        eri.eri_set_grad_forms(1 << form)
+        eri.eri_set_grad_forms((1 << form) | (1 << (eri.ERI_GRAD_ONE if one else eri.ERI_GRAD_TWO)))
         eri.eri_batch_grad(cls, db, b, k, None, torch.as_tensor(W, device="cuda"), gc, ge)
-        assert eri.eri_last_grad_forms() == (form, form)
+        assert eri.eri_last_grad_forms() == ((form, eri.ERI_GRAD_ONE) if one else (form, form))
     finally:
         eri.eri_set_grad_forms(0)
     q = np.array([(i, j) for j in range(ket.shape[0]) for i in range(sel.shape[0])], dtype=np.int64)

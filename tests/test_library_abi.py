@@ -74,14 +74,15 @@ def test_form_selectors_without_gpu():
     argument checks and the not-yet-run answers need no GPU."""
     import paper_2506_12501_gb300 as eri
     L = eri.lib()
-    assert L.eri_set_grad_forms(4) == eri.ERI_EINVAL
+    assert L.eri_set_grad_forms(16) == eri.ERI_EINVAL
     assert L.eri_set_grad_forms(-1) == eri.ERI_EINVAL
     prev = L.eri_set_grad_forms(1 << eri.ERI_GRAD_V)
-    assert prev in (1, 2, 3)
-    assert L.eri_set_grad_forms(0) == 1 << eri.ERI_GRAD_V  # 0 restores both forms
-    assert L.eri_set_grad_forms(0) == 3
+    assert 0 < prev <= 15
+    assert L.eri_set_grad_forms(0) == 1 << eri.ERI_GRAD_V  # 0 restores everything
+    assert L.eri_set_grad_forms((1 << eri.ERI_GRAD_X) | (1 << eri.ERI_GRAD_ONE)) == 15
+    assert L.eri_set_grad_forms(0) == (1 << eri.ERI_GRAD_X) | (1 << eri.ERI_GRAD_ONE)
     assert L.eri_set_forms(16) == eri.ERI_EINVAL
     assert L.eri_last_grad_forms(None, None) == eri.ERI_EINVAL
     b, k = ctypes.c_int32(), ctypes.c_int32()
     r = L.eri_last_grad_forms(ctypes.byref(b), ctypes.byref(k))
-    assert r == eri.ERI_EINVAL or (r == eri.ERI_OK and b.value in (0, 1) and k.value in (0, 1))
+    assert r == eri.ERI_EINVAL or (r == eri.ERI_OK and b.value in (0, 1) and k.value in (0, 1, 2))
