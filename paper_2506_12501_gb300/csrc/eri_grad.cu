@@ -663,32 +663,44 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
             if (a.both) {
                 // ---- K1: Y'[q][k][ab][q'] += sum_ii sum_{p in nz(ab)} E^ab_{i0+ii,p}
                 // R_{ii,k}[p+q'], q' over the raised ket range (the auxiliary
-                // integrals of this chunk are still in place)
+                // integrals of this chunk are still in place).  A thread takes
+                // four ket primitives of one (q, ab, q'): each term's index
+                // lookups and E value serve four products.
                 const int nhk2 = ct.nhk2, Ys = a.Ys;
-                const int nK1 = TQ * KKt * nab * nhk2;
+                const int nkb = (KKt + 3) >> 2;
+                const int nK1 = TQ * nhk2 * nab * nkb;
                 for (int item = tid; item < nK1; item += kGT) {
                     const int q = item % TQ;
                     int r = item / TQ;
                     const int qp = r % nhk2;
                     r /= nhk2;
-                    const int ab = r % nab, k = r / nab;
-                    if (k >= s_q[4 * q + 3]) continue;
+                    const int ab = r % nab, k0 = 4 * (r / nab);
+                    const int kq = s_q[4 * q + 3];
+                    if (k0 >= kq) continue;
+                    const int nk = min(4, kq - k0);
                     const double* Eq = sEb + (size_t)q * a.Ebs + i0;  // + t KB + ii
-                    const double* Rq = sR + q + (size_t)TQ * IC * k;   // + e NIs + ii TQ
-                    double y0 = 0.0, y1 = 0.0;
+                    const double* Rq = sR + q + (size_t)TQ * IC * k0;  // + e NIs + ii TQ + j TQ IC
+                    const int kst = TQ * IC;
+                    double y[4] = {0.0, 0.0, 0.0, 0.0};
                     const int t0 = __ldg(ct.bra_start + ab), t1 = __ldg(ct.bra_start + ab + 1);
                     for (int t = t0; t < t1; ++t) {
                         const int e = __ldg(ct.pq2k + (int)__ldg(ct.bra_p + t) * nhk2 + qp);
                         const double* Et = Eq + t * KB;
                         const double* Re = Rq + (size_t)e * NIs;
-                        int ii = 0;
-                        for (; ii + 1 < ICe; ii += 2) {
-                            y0 = fma(Et[ii], Re[ii * TQ], y0);
-                            y1 = fma(Et[ii + 1], Re[(ii + 1) * TQ], y1);
+                        for (int ii = 0; ii < ICe; ++ii) {
+                            const double ev = Et[ii];
+                            const double* Ri = Re + ii * TQ;
+                            // only the quartet's own ket primitives (nk of the four)
+                            y[0] = fma(ev, Ri[0], y[0]);
+                            if (nk > 1) y[1] = fma(ev, Ri[kst], y[1]);
+                            if (nk > 2) y[2] = fma(ev, Ri[2 * kst], y[2]);
+                            if (nk > 3) y[3] = fma(ev, Ri[3 * kst], y[3]);
                         }
-                        if (ii < ICe) y0 = fma(Et[ii], Re[ii * TQ], y0);
                     }
-                    sY[((size_t)q * KK + k) * Ys + ab * nhk2 + qp] += y0 + y1;
+                    double* yo = sY + ((size_t)q * KK + k0) * Ys + ab * nhk2 + qp;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (j < nk) yo[(size_t)j * Ys] += y[j];
                 }
             }
         }
@@ -892,8 +904,10 @@ static bool grad_plan_within(const ClassTables& ct, int KB, int KK, int nit, int
             const double kBarrier = 60.0;
             double common = rounds((double)TQ * IC * KK) * (3.0 * ct.nhl2 + 60.0) +
                             rounds((double)TQ * IC * 3 * ND) * 14.0;
-            if (both)  // Y' of the chunk: per (q, k, ab, q') its terms over the chunk's bra primitives
-                common += rounds((double)TQ * KK * ct.nab * ct.nhk2) * ((2.0 * IC + 3.0) * ct.Tab / ct.nab + 10.0) +
+            if (both)  // Y' of the chunk: per (q, ab, q') and four ket primitives, its terms over the chunk's
+                       // bra primitives (two lookups per term, an E value and four products per primitive)
+                common += rounds((double)TQ * ((KK + 3) / 4) * ct.nab * ct.nhk2) *
+                              ((3.0 + 6.0 * IC) * ct.Tab / ct.nab + 12.0) +
                           kBarrier;
             double cost;
             // a term's index lookup and scattered load cost about as much as
@@ -986,21 +1000,32 @@ struct GradOrder {
 
 // One launch: the channels of the kernel's bra.  bra/ket are the kernel's
 // lists (the caller's ket/bra when swap = 1); nbra_o/nket_o are the caller's.
+// What a launch_grad call did or leaves to do (its `next`).
+enum { GRAD_DONE = 0, GRAD_SECOND = 1, GRAD_ONE_SWAPPED = 2 };
+
+// One adjoint launch.  bra/ket are the kernel's lists (the caller's ket/bra
+// when swap = 1); nbra_o/nket_o are the caller's.  mode 0 (the call's first
+// launch, caller's orientation): picks, by the cost model, one launch for
+// every channel in this orientation (launched here), one in the other
+// orientation (*next = GRAD_ONE_SWAPPED, nothing launched), or two launches
+// (this side's channels here, *next = GRAD_SECOND).  mode 1: the second of
+// two launches; mode 2: one launch for every channel, in this orientation.
 static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra, int64_t nbra, const int32_t* ket,
                        int64_t nket, const int64_t* quartets, int64_t nq, const double* W, double* gc, double* ge,
-                       int swap, int64_t nbra_o, int64_t nket_o, GradOrder* ord, cudaStream_t st, int* did_both)
+                       int swap, int64_t nbra_o, int64_t nket_o, GradOrder* ord, cudaStream_t st, int mode, int* next)
 {
     const ClassTables* ct = nullptr;
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
-    // the first launch may produce every channel (pair tables of both sides
-    // raised, E products of both); otherwise each launch its bra's
+    // a single launch needs the pair tables of both sides raised and the E
+    // products of both; otherwise the kernel bra's raised tables suffice
     const int mask = g_grad_form_mask.load();
-    const bool allow_one = !swap && (mask & 4), allow_two = (mask & 8) || !(mask & 12);
-    // the quartet indices refer to the caller's lists: validated on the first launch only
+    const bool allow_one = (mask & 4) != 0, allow_two = (mask & 8) || !(mask & 12);
+    const bool may_one = mode == 2 || (mode == 0 && allow_one);
+    // the quartet indices refer to the caller's lists: validated by the first call only
     int mixed = 0;
-    int err = prepare_batch(cls, basis, bra, nbra, ket, nket, swap ? nullptr : quartets, swap ? 0 : nq,
-                            allow_one ? 2 : 1, st, &ct, &pb, &pk, &KB, &KK, kmax, 0, nullptr, 0, 0, &mixed);
+    int err = prepare_batch(cls, basis, bra, nbra, ket, nket, mode == 0 ? quartets : nullptr, mode == 0 ? nq : 0,
+                            may_one ? 2 : 1, st, &ct, &pb, &pk, &KB, &KK, kmax, 0, nullptr, 0, 0, &mixed);
     if (err != ERI_OK) return err;
     if (ct->L + 2 > kLtotMax) return ERI_EINVAL;
     GradArgs a{};
@@ -1039,34 +1064,49 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     a.vlist = vl->vlist;
     size_t bytes = 0;
     bool one = false;
-    if (allow_one) {
-        // one launch for every channel, unless the model puts two launches
-        // (this side's channels, then the other side's) below it
-        GradArgs a1 = a;
-        size_t b1 = 0;
-        double c1 = 0.0;
-        one = grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 1, &a1, &b1, &c1);
-        if (one && allow_two) {
-            GradArgs a0 = a, as = a;
-            size_t b0 = 0, bs = 0;
-            double c0 = 0.0, cs = 0.0;
-            const ClassTables* ctk = get_class_tables(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
-            if (!ctk) return err;
-            if (grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 0, &a0, &b0, &c0) &&
-                grad_plan(*ctk, KK, KB, a.nitk, a.nit, a.nq, 0, &as, &bs, &cs) && c0 + cs < c1)
-                one = false;
+    if (next) *next = GRAD_DONE;
+    if (mode == 2) {
+        one = grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 1, &a, &bytes, nullptr);
+        if (!one) return ERI_EINVAL;
+    } else if (mode == 0 && allow_one) {
+        // modelled cost per quartet of: one launch in this orientation, one in
+        // the other (the sides exchanged), two launches
+        const ClassTables* ctk = get_class_tables(cls.lc, cls.ld, cls.la, cls.lb, st, &err);
+        if (!ctk) return err;
+        GradArgs a1 = a, a0 = a, as = a, aw = a;
+        size_t b1 = 0, b0 = 0, bs = 0, bw = 0;
+        double c1 = 0.0, c0 = 0.0, cs = 0.0, cw = 0.0;
+        const bool ok1 = grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 1, &a1, &b1, &c1);
+        const bool okw = grad_plan(*ctk, KK, KB, a.nitk, a.nit, a.nq, 1, &aw, &bw, &cw);
+        const bool ok2 = allow_two && grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 0, &a0, &b0, &c0) &&
+                         grad_plan(*ctk, KK, KB, a.nitk, a.nit, a.nq, 0, &as, &bs, &cs);
+        double best = 1e300;
+        int pick = -1;  // 0: one here, 1: one swapped, 2: two
+        if (ok1 && c1 < best) { best = c1; pick = 0; }
+        if (okw && cw < best) { best = cw; pick = 1; }
+        if (ok2 && c0 + cs < best) { best = c0 + cs; pick = 2; }
+        if (pick == 1) {
+            if (next) *next = GRAD_ONE_SWAPPED;
+            return ERI_OK;  // validated; the swapped call builds its own tables and order
         }
-        if (one) {
+        if (pick == 0) {
+            one = true;
             a = a1;
             bytes = b1;
         }
     }
-    if (!one && !grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 0, &a, &bytes, nullptr)) return ERI_EINVAL;
-    if (did_both) *did_both = one ? 1 : 0;
-    g_last_grad_form[swap] = a.vform;
-    if (one) g_last_grad_form[1] = ERI_GRAD_ONE;
+    if (!one) {
+        if (!grad_plan(*ct, KB, KK, a.nit, a.nitk, a.nq, 0, &a, &bytes, nullptr)) return ERI_EINVAL;
+        if (mode == 0 && next) *next = GRAD_SECOND;
+    }
+    if (one) {
+        g_last_grad_form[0] = a.vform;
+        g_last_grad_form[1] = ERI_GRAD_ONE;
+    } else {
+        g_last_grad_form[swap] = a.vform;
+    }
     a.ntiles = (a.nq + a.TQ - 1) / a.TQ;
-    if (!ord->queue) {  // first launch: order (sorted if the batch mixes degrees); the second reuses it
+    if (!ord->queue) {  // the call's first kernel launch: order (sorted if the batch mixes degrees); a second reuses it
         err = build_order(quartets, a.nq, nbra_o, pb.kp, pk.kp, KB, KK, swap, mixed, st, &ord->order, &ord->queue);
         if (err != ERI_OK) return err;
     }
@@ -1102,12 +1142,13 @@ extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const i
     // channels of the bra (a, b), then of the ket (c, d) with the sides exchanged
     GradOrder order;
     g_last_grad_form[0] = g_last_grad_form[1] = -1;
-    int both = 0;
+    int next = GRAD_DONE;
     err = launch_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, grad_centres, grad_exps, 0, nbra,
-                      nket, &order, st, &both);
-    if (err != ERI_OK || both) return err;
+                      nket, &order, st, 0, &next);
+    if (err != ERI_OK || next == GRAD_DONE) return err;
     return launch_grad(eri_class_t{cls.lc, cls.ld, cls.la, cls.lb}, basis, ket_pairs, nket, bra_pairs, nbra, quartets,
-                       nq, W, grad_centres, grad_exps, 1, nbra, nket, &order, st, nullptr);
+                       nq, W, grad_centres, grad_exps, 1, nbra, nket, &order, st, next == GRAD_ONE_SWAPPED ? 2 : 1,
+                       nullptr);
 }
 
 extern "C" int eri_last_grad_forms(int32_t* bra_form, int32_t* ket_form)
