@@ -445,7 +445,7 @@ def adjoint_variant(args, eri, dev):
             "grad_prepass_ms": prof[eri.PROF_PREPASS][1],
             "grad_kernel_frac_fp64_peak_sparse": gflop / (kms / 1e3) / 1e9 / FP64_PEAK_GFLOPS if kms > 0 else None,
             "fwd_frac_fp64_peak_sparse_plain": fflop / (t_f / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
-            "grad_forms": {"".join(map(str, c)): "".join("XVO"[f] for f in v) for c, v in forms.items()},
+            "grad_forms": {"".join(map(str, c)): "".join("XVO?S"[f] for f in v) for c, v in forms.items()},
             "per_class": per_class}
 
 

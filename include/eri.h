@@ -161,8 +161,10 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
  * auxiliary integrals (Y'_k[ab][q'] = sum_i sum_p E^ab_{i,p} [p+q']_{ik}
  * over the raised ket range, accumulated over the bra primitives), or two
  * launches, the second with the sides exchanged.  *bra_form: the form of the
- * first launch's bra channels; *ket_form: ERI_GRAD_ONE for the single
- * launch, else the second launch's form.  All give the same derivatives to
+ * first launch's kernel-bra channels; *ket_form: ERI_GRAD_ONE for the single
+ * launch with the caller's bra as its kernel bra, ERI_GRAD_ONE_SWAPPED for
+ * the single launch with the caller's ket as its kernel bra (whose channels
+ * *bra_form then describes), else the second launch's form.  All give the same derivatives to
  * round-off; a cost model picks per call.  ERI_EINVAL before any call.
  * eri_set_grad_forms -- restrict the planner (process-wide; for testing):
  * bits ERI_GRAD_X and ERI_GRAD_V allow those forms, bit ERI_GRAD_ONE the
@@ -177,6 +179,7 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
 #define ERI_GRAD_V 1
 #define ERI_GRAD_ONE 2
 #define ERI_GRAD_TWO 3
+#define ERI_GRAD_ONE_SWAPPED 4  /* a form value of eri_last_grad_forms, not a mask bit */
 int eri_last_grad_forms(int32_t* bra_form, int32_t* ket_form);
 int eri_set_grad_forms(int32_t mask);
 

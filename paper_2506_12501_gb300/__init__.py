@@ -25,7 +25,7 @@ from .binding import (  # noqa: F401
     ERI_FORM_PLAIN, ERI_FORM_HRR,
     eri_last_grad_forms,
     eri_set_grad_forms,
-    ERI_GRAD_X, ERI_GRAD_V, ERI_GRAD_ONE, ERI_GRAD_TWO,
+    ERI_GRAD_X, ERI_GRAD_V, ERI_GRAD_ONE, ERI_GRAD_TWO, ERI_GRAD_ONE_SWAPPED,
     eri_finalize,
     eri_profile_enable,
     eri_profile_read,

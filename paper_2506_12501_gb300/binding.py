@@ -49,7 +49,7 @@ EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_er
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
-ERI_GRAD_X, ERI_GRAD_V, ERI_GRAD_ONE, ERI_GRAD_TWO = 0, 1, 2, 3
+ERI_GRAD_X, ERI_GRAD_V, ERI_GRAD_ONE, ERI_GRAD_TWO, ERI_GRAD_ONE_SWAPPED = 0, 1, 2, 3, 4
 PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS = 0, 1, 2, 3
 
 
@@ -336,7 +336,8 @@ def eri_set_grad_forms(mask: int) -> int:
 
 def eri_last_grad_forms() -> tuple:
     """(bra-channel form, ket-channel form) of the last eri_batch_grad call: ERI_GRAD_X or ERI_GRAD_V, and
-    ERI_GRAD_ONE as the ket form when one launch produced every channel."""
+    ERI_GRAD_ONE (ERI_GRAD_ONE_SWAPPED) as the ket form when one launch with the caller's bra (ket) as its
+    kernel bra produced every channel."""
     b = ctypes.c_int32()
     k = ctypes.c_int32()
     _check(lib().eri_last_grad_forms(ctypes.byref(b), ctypes.byref(k)), "eri_last_grad_forms")

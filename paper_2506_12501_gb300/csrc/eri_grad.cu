@@ -1101,7 +1101,7 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     }
     if (one) {
         g_last_grad_form[0] = a.vform;
-        g_last_grad_form[1] = ERI_GRAD_ONE;
+        g_last_grad_form[1] = swap ? ERI_GRAD_ONE_SWAPPED : ERI_GRAD_ONE;
     } else {
         g_last_grad_form[swap] = a.vform;
     }

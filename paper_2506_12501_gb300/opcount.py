@@ -234,9 +234,13 @@ def grad_flops(cls, Kbra: int, Kket: int, forms=(0, 0)) -> int:
     """FP64 flops of the adjoint of one quartet in the forms of
     eri_last_grad_forms: the bra channels in form forms[0]; the ket channels
     either from the same launch (forms[1] = 2, ERI_GRAD_ONE: the auxiliary
-    integrals are computed once) or from a second launch with the sides
-    exchanged, in form forms[1]."""
+    integrals are computed once; 4, ERI_GRAD_ONE_SWAPPED: the same with the
+    sides exchanged, forms[0] then being the form of the ket's channels) or
+    from a second launch with the sides exchanged, in form forms[1]."""
     la, lb, lc, ld = cls
     if forms[1] == 2:
         return _grad_launch_flops(cls, Kbra, Kket, forms[0]) + _grad_ket_flops(cls, Kbra, Kket)
+    if forms[1] == 4:  # ERI_GRAD_ONE_SWAPPED: the single launch with the sides exchanged
+        sw = (lc, ld, la, lb)
+        return _grad_launch_flops(sw, Kket, Kbra, forms[0]) + _grad_ket_flops(sw, Kket, Kbra)
     return _grad_launch_flops(cls, Kbra, Kket, forms[0]) + _grad_launch_flops((lc, ld, la, lb), Kket, Kbra, forms[1])
