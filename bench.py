@@ -421,6 +421,25 @@ def adjoint_variant(args, eri, dev):
     per_class = {"".join(map(str, c)): {"quartets": n, "fwd_ms": round(pf[c][0].elapsed_time(pf[c][1]), 3),
                                         "grad_ms": round(pg[c][0].elapsed_time(pg[c][1]), 3)}
                  for c, _, _, _, n in data}
+    if args.adjoint_schemes:
+        # every class once more with one launch forced (either side order) and
+        # with two launches forced (either form each); the forms of the
+        # timed default pass stay the ones counted below
+        forms_default = dict(forms)
+        for label, mask in (("grad_one_ms", (1 << eri.ERI_GRAD_X) | (1 << eri.ERI_GRAD_V) | (1 << eri.ERI_GRAD_ONE)),
+                            ("grad_two_ms", (1 << eri.ERI_GRAD_X) | (1 << eri.ERI_GRAD_V) | (1 << eri.ERI_GRAD_TWO))):
+            prev = eri.eri_set_grad_forms(mask)
+            try:
+                grad()
+                pm = {}
+                grad(pm)
+                torch.cuda.synchronize()
+            finally:
+                eri.eri_set_grad_forms(prev)
+            for c, _, _, _, _ in data:
+                per_class["".join(map(str, c))][label] = round(pm[c][0].elapsed_time(pm[c][1]), 3)
+        forms.clear()
+        forms.update(forms_default)
     nq_tot = sum(d[4] for d in data)
     for cls, _, _, (keys, counts), _ in data:
         for (x, y), n in zip(keys, counts):
@@ -795,6 +814,8 @@ def main():
     ap.add_argument("--split-nq", type=int, default=100_000)
     ap.add_argument("--adjoint-nq", type=int, default=0, help="quartets per class of the adjoint (0: all)")
     ap.add_argument("--adjoint-only", default=None, help="profiling aid: comma list of adjoint classes, e.g. 1010")
+    ap.add_argument("--adjoint-schemes", action="store_true",
+                    help="adjoint variant: also time every class with one launch and with two launches forced")
     ap.add_argument("--molecule-natom", type=int, default=64)
     ap.add_argument("--three-nt", type=int, default=100_000, help="triples per 3-centre class")
     ap.add_argument("--nq", type=int, default=NQ_PER_CLASS, help="quartets per class")
