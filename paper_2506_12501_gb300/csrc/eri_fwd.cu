@@ -431,7 +431,7 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     tp->o_q = take((size_t)TQ * 2);
     tp->o_geo = take(ct.hrr ? (size_t)TQ * 6 : 0);
     tp->o_dj = take((size_t)TQ + ct.nab_f);  // also the quartet indices of a sorted batch
-    tp->o_Ei = take(e_smem ? 0 : (size_t)TQ * ct.Tab);
+    tp->o_Ei = take(!e_smem && TQ == 1 ? (size_t)ct.Tab : 0);  // one-quartet tiles only
     tp->bytes = off * 8;
     tp->acc_regs = (TQ * ct.nab * ct.ncd <= kNT * kNACC) ? 1 : 0;
     if (ct.hrr && !tp->acc_regs) return false;

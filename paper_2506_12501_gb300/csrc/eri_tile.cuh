@@ -101,7 +101,7 @@ struct FwdArgs {
     int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;  // smem offsets (doubles)
     int o_hB, o_geo;          // horizontal-recursion form: second buffer, A-B and C-D per quartet
     int o_dj;                 // Coulomb digestion scratch: [TQ] weights, [nab] bra sums
-    int o_Ei;                 // E not staged (e_smem = 0): the bra E products of the current bra primitive, [TQ][Tab]
+    int o_Ei;                 // one-quartet tile with E not staged: the bra E products of the current bra primitive, [Tab]
     int64_t ntiles;
     // work-queue mode (plans): one bra pair, consecutive ket pairs
     int mode;                 // 0: list/product batch, 1: ranged (bra rbra, kets rk0..)
@@ -631,14 +631,13 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             // ---- B: ket transform + ket contraction
             // only the bra Hermite functions the bra transform reads (all of
             // them, or those of order la for a solid-harmonic bra)
-            if (!a.e_smem) {
-                // the bra E products of primitive i, gathered once per tile (strided
-                // in global memory: one slot of every term) for stage C
+            const bool e_row = !a.e_smem && TQ == 1;  // one-quartet tile with unstaged E
+            if (e_row) {
+                // the bra E products of primitive i, gathered once (strided in
+                // global memory: one slot of every term) for stage C
                 double* sEi = sm + a.o_Ei;
-                for (int idx = tid; idx < TQ * ct.Tab; idx += kNT) {
-                    const int q = idx / ct.Tab, t = idx - q * ct.Tab;
-                    sEi[idx] = i < s_q[4 * q + 2] ? a.bra_E[((size_t)s_q[4 * q] * ct.Tab + t) * KB + i] : 0.0;
-                }
+                for (int t = tid; t < ct.Tab; t += kNT)
+                    sEi[t] = i < s_q[2] ? a.bra_E[((size_t)s_q[0] * ct.Tab + t) * KB + i] : 0.0;
             }
             const int nhbu = nhb - ct.pb0;
             // split form, wide bra Hermite range: warp per (quartet, cd), P functions per lane
@@ -741,10 +740,11 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     const int item = tid + s * kNT;
                     if (item < nC) {
                         const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
-                        acc[s] += a.e_smem ? bra_sum<SPLIT>(sEb + q * a.sEbS + i, KB, sX, s_bstart[ab], s_bstart[ab + 1],
-                                                            s_bp, ncd, cd, TQ, q)
-                                           : bra_sum<SPLIT>(sm + a.o_Ei + q * ct.Tab, 1, sX, s_bstart[ab],
-                                                            s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
+                        const double* Eb = a.e_smem ? sEb + q * a.sEbS + i
+                                                    : (e_row ? sm + a.o_Ei
+                                                             : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab + i);
+                        acc[s] += bra_sum<SPLIT>(Eb, e_row ? 1 : KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd,
+                                                 TQ, q);
                     }
                 }
             } else {
@@ -752,11 +752,10 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 for (int item = tid; item < nC; item += kNT) {
                     const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
                     if (q >= nqt) continue;
+                    const double* Eb = a.e_smem ? sEb + q * a.sEbS + i
+                                                : (e_row ? sm + a.o_Ei : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab + i);
                     const double v =
-                        a.e_smem ? bra_sum<SPLIT>(sEb + q * a.sEbS + i, KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp,
-                                                  ncd, cd, TQ, q)
-                                 : bra_sum<SPLIT>(sm + a.o_Ei + q * ct.Tab, 1, sX, s_bstart[ab], s_bstart[ab + 1], s_bp,
-                                                  ncd, cd, TQ, q);
+                        bra_sum<SPLIT>(Eb, e_row ? 1 : KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
                     const int64_t o = out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd);
                     st_hint(a.out + o, (i == 0) ? v : ld_hint(a.out + o, stream) + v, stream);
                 }
