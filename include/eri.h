@@ -260,8 +260,7 @@ int eri_batch3(int32_t lx, int32_t lc, int32_t ld, const eri_basis_t* basis,
  *   integral kernel runs.  Split such batches.
  * - The first call on a device sets that device up (the device must be
  *   current): it fills the constant tables with synchronous copies and
- *   looks up the arrays' device addresses.  Make that first call before
- *   any stream capture begins.
+ *   looks up the arrays' device addresses.
  * - Every call uses the same arrays, which keep the last call's contents;
  *   the call clears what must start at zero.  Calls whose GPU work overlaps
  *   in time (different streams, or several host threads) race on them:
