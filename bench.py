@@ -781,8 +781,10 @@ def run_library(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == eri.ERI_PREC_FP64 else "f64+f32x2",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if only is None else f"single class {args.only_class}, {nq_class} quartets",
-                       "classes": len(batches), "quartets_per_class": nq_class, "K_per_shell": K_PER_SHELL,
+            "config": {"workload": WORKLOAD if only is None else
+                       f"single class {args.only_class}{' of the high-l workload' if args.high_l_k else ''}, "
+                       f"{nq_class} quartets",
+                       "classes": len(batches), "quartets_per_class": nq_class, "K_per_shell": Kps,
                        "l2": "flushed between timed steps (256 MiB write); outputs of 8 GB/step exceed L2",
                        "parallelism": f"weak x{world}: each rank its own seeded sweep"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,

@@ -138,10 +138,12 @@ int eri_batch(eri_class_t cls, const eri_basis_t* basis,
  * Either gradient pointer may be NULL to skip that part.
  * Its tiles hold the auxiliary integrals to order L+2 of every ket primitive
  * pair of a quartet, which bounds the contraction degrees more tightly than
- * the forward's: with the same K on all four shells, K = 8 fits for L <= 4,
- * K = 5 for L = 5, K = 3 for L = 6..9, K = 2 for L = 10 and K = 1 for
- * L = 11, 12.  Uncontracted d and f shells with s and p shells of any K
- * <= ERI_KMAX always fit.  Beyond, the call returns ERI_EINVAL.
+ * the forward's: with the same K on all four shells, every class fits
+ * K = 8 for L <= 4, K = 5 for L = 5, K = 3 for L = 6..9, K = 2 for L = 10
+ * and K = 1 for L = 11, 12.  These bounds are reached by the classes with a
+ * d-f or f-f pair; the others fit more.  Uncontracted d and f shells with s
+ * and p shells of any K <= ERI_KMAX always fit.  Beyond, the call returns
+ * ERI_EINVAL.
  */
 int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
                    const int32_t* bra_pairs, int64_t nbra,

@@ -431,11 +431,28 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     tp->o_q = take((size_t)TQ * 2);
     tp->o_geo = take(ct.hrr ? (size_t)TQ * 6 : 0);
     tp->o_dj = take((size_t)TQ + ct.nab_f);  // also the quartet indices of a sorted batch
-    tp->o_Ei = take(!e_smem && TQ == 1 ? (size_t)ct.Tab : 0);  // one-quartet tiles only
+    // one-quartet tiles only, and only where it fits: a tile without it
+    // reads the bra E products from global memory
+    tp->o_Ei = -1;
+    if (!e_smem && TQ == 1 && (off + even(ct.Tab)) * 8 <= (size_t)max_smem_optin()) tp->o_Ei = take(ct.Tab);
+    tp->o_Er = -1;  // added for the split form by add_e_ring
     tp->bytes = off * 8;
     tp->acc_regs = (TQ * ct.nab * ct.ncd <= kNT * kNACC) ? 1 : 0;
     if (ct.hrr && !tp->acc_regs) return false;
     return tp->bytes <= (size_t)max_smem_optin();
+}
+
+// Split form: when the blocked ket stage reads its ket E rows from global
+// memory, give every warp a ring of kRingRows rows (KK float pairs each) at
+// the end of the tile's shared memory, if it fits.
+static void add_e_ring(const ClassTables& ct, int KK, TilePlan* tp)
+{
+    tp->o_Er = -1;
+    if (tp->e_smem || !split_block_width(ct.nhb - ct.pb0)) return;
+    const size_t off = (tp->bytes / 8 + 1) & ~size_t(1), nd = (size_t)(kNT / 32) * kRingRows * KK;
+    if ((off + nd) * 8 > (size_t)max_smem_optin()) return;
+    tp->o_Er = (int)off;
+    tp->bytes = (off + nd) * 8;
 }
 
 bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best, size_t max_bytes)
@@ -805,6 +822,7 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
             for (int es = 1; es >= 0; --es) {
                 TilePlan tp;
                 if (tile_layout(ct, base.KB, base.KK, TQ, IC, es, &tp) && tp.acc_regs) {
+                    if (split) add_e_ring(ct, base.KK, &tp);
                     bool dup = false;
                     for (auto& c : cands) dup |= (c.TQ == TQ && c.IC == IC && c.e_smem == es);
                     if (!dup) cands.push_back(tp);
@@ -1095,6 +1113,10 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
             set_tile(a, tp);
             a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
         }
+    }
+    if (split && tp.o_Er < 0) {
+        add_e_ring(a.ct, a.KK, &tp);
+        set_tile(a, tp);
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
         return ERI_ECUDA;

@@ -193,7 +193,8 @@ struct TilePlan {
     int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;
     int o_hB, o_geo;  // horizontal-recursion form: second buffer (the first is at 0), A-B/C-D per quartet
     int o_dj;         // Coulomb digestion scratch (TQ + nab_f doubles)
-    int o_Ei;         // one-quartet tile, E not staged: the bra E products of the current bra primitive ([Tab])
+    int o_Ei;         // one-quartet tile, E not staged: the bra E products of the current bra primitive ([Tab]), or -1
+    int o_Er;         // split form, blocked ket stage, E not staged: three ket E rows per warp ([8][3][KK] float pairs), or -1
     size_t bytes;
 };
 // max_bytes > 0: only shapes whose shared memory stays within it

@@ -19,6 +19,15 @@ namespace eri {
 constexpr int kNT = 256;   // threads per CTA of the tile kernels
 constexpr int kNACC = 16;  // outputs per thread held in registers
 
+// Split form: bra Hermite functions per lane in the blocked ket stage (one
+// warp per (quartet, cd)) for a bra range of nhbu functions; 0: not blocked.
+__host__ __device__ constexpr int split_block_width(int nhbu)
+{
+    return nhbu >= 72 && nhbu <= 96 ? 3 : (nhbu >= 48 && nhbu <= 64 ? 2 : 0);
+}
+// ket E rows per warp in the ring of the blocked split stage
+constexpr int kRingRows = 3;
+
 // ---- split precision: a double x is carried as hi + lo with hi = fl32(x),
 // lo = fl32(x - hi) (about 48 significant bits); products of two such pairs
 // keep the exact error of hi*hi (from an FMA) and the two cross terms, and
@@ -74,6 +83,20 @@ __device__ __forceinline__ void prefetch_l1(const void* p)
 {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
+// 8-byte asynchronous copy global -> shared (completes per commit group)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, uint64_t pol)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void st_hint(double* p, double v, uint64_t pol)
 {
     asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
@@ -101,7 +124,8 @@ struct FwdArgs {
     int o_Eb, o_Ek, o_Pb, o_Pk, o_R, o_X, o_tab, o_q;  // smem offsets (doubles)
     int o_hB, o_geo;          // horizontal-recursion form: second buffer, A-B and C-D per quartet
     int o_dj;                 // Coulomb digestion scratch: [TQ] weights, [nab] bra sums
-    int o_Ei;                 // one-quartet tile with E not staged: the bra E products of the current bra primitive, [Tab]
+    int o_Ei;                 // one-quartet tile with E not staged: the bra E products of the current bra primitive, [Tab] (-1: none)
+    int o_Er;                 // split blocked ket stage with E not staged: a ring of three ket E rows per warp (-1: none)
     int64_t ntiles;
     // work-queue mode (plans): one bra pair, consecutive ket pairs
     int mode;                 // 0: list/product batch, 1: ranged (bra rbra, kets rk0..)
@@ -141,6 +165,7 @@ inline void set_tile(FwdArgs& a, const TilePlan& tp)
     a.o_geo = tp.o_geo;
     a.o_dj = tp.o_dj;
     a.o_Ei = tp.o_Ei;
+    a.o_Er = tp.o_Er;
 }
 
 struct Strided {
@@ -417,7 +442,7 @@ template <int P>
 __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int IC, int ii, int KK, int KKt,
                                                   int NIs, int ncd, int nhk, const double* sEk, const double* sR,
                                                   double* sX, const int* s_q, const int* s_kstart,
-                                                  const int16_t* s_kq, const int16_t* s_pq)
+                                                  const int16_t* s_kq, const int16_t* s_pq, float2* ring)
 {
     const ClassTables& ct = a.ct;
     const int lane = threadIdx.x & 31, nhb = ct.nhb;
@@ -437,16 +462,60 @@ __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int 
         }
         const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
         const bool gl = !a.e_smem;
-        // the ket E rows of a term (KK float pairs) come from L2 or DRAM: the
-        // lanes prefetch the rows of the next two terms into L1 while the
-        // warp works on the current one
+        if (ring) {
+            // the warp's ring of three ket E rows in shared memory: the rows of
+            // terms t+1 and t+2 are in flight (asynchronous copies, one commit
+            // group per row, possibly empty) while the warp works on term t
+            auto issue = [&](int t, int slot) {
+                if (t < t1)
+                    for (int k = lane; k < KKt; k += 32) cp_async8(ring + slot * KK + k, Ek + (size_t)t * KK + k, keep);
+                cp_async_commit();
+            };
+            issue(t0, 0);
+            issue(t0 + 1, 1);
+            int slot = 0;
+            for (int t = t0; t < t1; ++t) {
+                // the slot of term t+2 held term t-1, whose readers passed the
+                // warp barrier at the end of the previous term
+                issue(t + 2, slot == 0 ? 2 : slot - 1);
+                cp_async_wait<2>();
+                __syncwarp();
+                const int qv = s_kq[t];
+                const float2* Rj[P];
+#pragma unroll
+                for (int j = 0; j < P; ++j)
+                    Rj[j] = reinterpret_cast<const float2*>(Rc + (size_t)s_pq[prow[j] + qv] * NIs);
+                const float2* Ea = ring + slot * KK;
+                int k = 0;
+                for (; k + 1 < KKt; k += 2) {
+                    const float2 e0 = Ea[k], e1 = Ea[k + 1];
+#pragma unroll
+                    for (int j = 0; j < P; ++j) {
+                        ff_mac(e0, Rj[j][k], S[j][0], c[j][0]);
+                        ff_mac(e1, Rj[j][k + 1], S[j][1], c[j][1]);
+                    }
+                }
+                if (k < KKt) {
+                    const float2 e0 = Ea[k];
+#pragma unroll
+                    for (int j = 0; j < P; ++j) ff_mac(e0, Rj[j][k], S[j][0], c[j][0]);
+                }
+                __syncwarp();
+                slot = slot == 2 ? 0 : slot + 1;
+            }
+            cp_async_wait<0>();  // only empty groups can remain
+        }
+        // without a ring (or with E staged) the ket E rows of a term (KK float
+        // pairs) are read in place; from L2 or DRAM, the lanes prefetch the
+        // rows of the next two terms into L1 while the warp works on the
+        // current one
         // (each prefetched address lies inside its row: the line of byte
         // min(128 l, 8 KK - 8) for lane l; a row spans at most nline lines)
         const int nline = (KK * 8 + 127) / 128 + 1;
-        if (gl && lane < 2 * nline && t0 + lane / nline < t1)
+        if (!ring && gl && lane < 2 * nline && t0 + lane / nline < t1)
             prefetch_l1(reinterpret_cast<const char*>(Ek + (t0 + lane / nline) * KK) +
                         min(128 * (lane % nline), 8 * KK - 8));
-        for (int t = t0; t < t1; ++t) {
+        for (int t = ring ? t1 : t0; t < t1; ++t) {
             if (gl && lane < nline && t + 2 < t1)
                 prefetch_l1(reinterpret_cast<const char*>(Ek + (t + 2) * KK) + min(128 * lane, 8 * KK - 8));
             const int qv = s_kq[t];
@@ -631,7 +700,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             // ---- B: ket transform + ket contraction
             // only the bra Hermite functions the bra transform reads (all of
             // them, or those of order la for a solid-harmonic bra)
-            const bool e_row = !a.e_smem && TQ == 1;  // one-quartet tile with unstaged E
+            const bool e_row = a.o_Ei >= 0;  // one-quartet tile with unstaged E (where the row fits)
             if (e_row) {
                 // the bra E products of primitive i, gathered once (strided in
                 // global memory: one slot of every term) for stage C
@@ -641,11 +710,16 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             }
             const int nhbu = nhb - ct.pb0;
             // split form, wide bra Hermite range: warp per (quartet, cd), P functions per lane
-            const int blocked = SPLIT ? (nhbu >= 72 && nhbu <= 96 ? 3 : (nhbu >= 48 && nhbu <= 64 ? 2 : 0)) : 0;
+            const int blocked = SPLIT ? split_block_width(nhbu) : 0;
+            float2* ring = a.o_Er >= 0 && !a.e_smem
+                               ? reinterpret_cast<float2*>(sm + a.o_Er) + (size_t)(tid >> 5) * kRingRows * KK
+                               : nullptr;
             if (blocked == 3)
-                split_ket_blocked<3>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq);
+                split_ket_blocked<3>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq,
+                                     ring);
             else if (blocked == 2)
-                split_ket_blocked<2>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq);
+                split_ket_blocked<2>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq,
+                                     ring);
             const int nB = blocked ? 0 : TQ * nhbu * ncd;
             for (int item = tid; item < nB; item += kNT) {
                 const int q = item % TQ, r = item / TQ, p = ct.pb0 + r % nhbu, cd = r / nhbu;

@@ -230,3 +230,21 @@ def test_full_size_sampled(cuda, cls):
     out2 = eri.eri_batch(cls, db, b, k, qq)
     assert eri.eri_last_form() == form
     assert torch.equal(out, out2)
+
+
+@pytest.mark.parametrize("cls,K", [((3, 3, 3, 1), 8), ((3, 3, 3, 2), 7), ((3, 3, 3, 3), 6)])
+def test_contraction_degree_limits(cuda, cls, K):
+    """The largest contraction degrees eri_batch accepts with the same K on all
+    four shells (K = 8 up to L = 10, K = 7 at L = 11, K = 6 at L = 12) run in
+    FP64 and in split precision and match the oracle; one more primitive per
+    shell is refused with ERI_EINVAL (no tile holds it, or K > ERI_KMAX)."""
+    basis, bra, ket, q = synth.small_random_batch(cls, K=(K,) * 4, nq=2, seed=5)
+    ref = oracle_blocks(cls, basis, bra, ket, q, prec="d")
+    assert_close(gpu_list(cls, basis, bra, ket, q), ref, what=f"fp64 {cls} K={K}")
+    assert_close(gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT), ref, atol=1e-10, rtol=1e-10,
+                 what=f"split {cls} K={K}")
+    basis, bra, ket, q = synth.small_random_batch(cls, K=(K + 1,) * 4, nq=2, seed=5)
+    for prec in (eri.ERI_PREC_FP64, eri.ERI_PREC_SPLIT):
+        with pytest.raises(eri.EriError) as e:
+            gpu_list(cls, basis, bra, ket, q, precision=prec)
+        assert e.value.code == eri.ERI_EINVAL

@@ -145,3 +145,25 @@ def test_grad_errors(cuda):
     W = torch.zeros(eri.out_len((1, 0, 1, 0), 4, 4, 6), dtype=torch.float64, device="cuda")
     eri.eri_batch_grad((1, 0, 1, 0), db, b, k, qq, W, gc, None)   # zero weights -> zero gradient
     assert torch.all(gc == 0)
+
+
+@pytest.mark.parametrize("cls,K", [((1, 1, 1, 1), 8), ((0, 0, 2, 3), 5), ((0, 0, 3, 3), 3), ((1, 3, 3, 3), 2),
+                                   ((3, 3, 3, 3), 1)])
+def test_grad_contraction_degree_limits(cuda, cls, K):
+    """The contraction degrees eri_batch_grad guarantees with the same K on
+    all four shells (K = 8 up to L = 4, 5 at L = 5, 3 at L = 6..9, 2 at
+    L = 10, 1 at L = 11, 12), on classes that reach exactly that bound (a d-f
+    or f-f pair), match the oracle's derivative; one more primitive per shell
+    is refused with ERI_EINVAL."""
+    basis, bra, ket, q = synth.small_random_batch(cls, K=(K,) * 4, nq=2, seed=6)
+    n = eri.out_len(cls, bra.shape[0], ket.shape[0], q.shape[0])
+    W = np.random.default_rng(9).uniform(-1, 1, n)
+    Wq = W.reshape(-1, q.shape[0]).T.reshape(-1)
+    rc, re = oracle.eri_grad_quartets(basis, synth.quartet_shells(bra, ket, q), Wq, prec="d", threads=THREADS)
+    gc, ge = gpu_grad(cls, basis, bra, ket, q, W)
+    grad_close(gc, rc, f"centres {cls} K={K}")
+    grad_close(ge, re, f"exponents {cls} K={K}")
+    basis, bra, ket, q = synth.small_random_batch(cls, K=(K + 1,) * 4, nq=2, seed=6)
+    with pytest.raises(eri.EriError) as e:
+        gpu_grad(cls, basis, bra, ket, q, W)
+    assert e.value.code == eri.ERI_EINVAL
