@@ -17,9 +17,51 @@ constexpr double kTwoPi52 = 34.986836655249725693;
 // sqrt(pi)/2
 constexpr double kHalfSqrtPi = 0.88622692545275801365;
 
+// 1/sqrt(x) for x > 0, to within about one ulp, in five FP64 operations:
+// a float seed, then one third-order step of the series
+//   (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + O(e^3),   e = 1 - x y0^2
+// (Householder's iteration of order 2 for x^(-1/2)).  The seed is the float
+// reciprocal square root of x's float image (high bits, exponent rebiased),
+// widened bitwise: |e| < 2^-20, so the truncated 5e^3/16 stays below 2^-61
+// and the error is that of the roundings.  No 64-bit conversion is issued.
+// x outside the float range [2^-126, 2^127] takes the library's rsqrt.
+__device__ __forceinline__ double rsqrt_fp64(double x)
+{
+    const int hi = __double2hiint(x);
+    if (hi < (897 << 20) || hi >= (1151 << 20)) return rsqrt(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const float xf = __int_as_float(((hi - (896 << 20)) << 3) | (int)(lo >> 29));
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+    const int yb = __float_as_int(yf);
+    const double y0 = __hiloint2double((yb >> 3) + (896 << 20), yb << 29);
+    const double e = fma(-x, y0 * y0, 1.0);
+    return fma(y0 * e, fma(0.375, e, 0.5), y0);
+}
+
+// Nearest grid point of T (0 <= T < kBoysTmax): returns j = rint(T/step)
+// and sets md = T_j - T, with no 64-bit conversion (those share the FP64
+// pipe): the float image of T comes from its high bits (exponent rebiased,
+// mantissa truncated; 0 below the float range), the rounding from adding
+// 1.5 * 2^23, and T_j = j * 2^-5 is assembled bitwise, exactly, so md costs
+// one FP64 subtraction.  The truncated image is low by less than 2^-23 T,
+// i.e. 2^-9 grid steps below kBoysTmax, so |md| <= 1/64 + 2^-14.
+__device__ __forceinline__ int boys_grid(double T, double& md)
+{
+    const int hi = __double2hiint(T);
+    const unsigned lo = (unsigned)__double2loint(T);
+    const int fb = hi >= (897 << 20) ? (((hi - (896 << 20)) << 3) | (int)(lo >> 29)) : 0;
+    const float s = __fmaf_rn(__int_as_float(fb), (float)kBoysInvStep, 12582912.0f);  // 1.5 * 2^23
+    const int j = min(__float_as_int(s) - 0x4B400000, kBoysGrid - 1);
+    const int e = 31 - __clz(j);  // j = 2^e (1 + m), 0 <= e <= 13 (j > 0)
+    const int thi = j > 0 ? (((1023 - kBoysLog2InvStep + e) << 20) | ((j << (20 - e)) & 0xFFFFF)) : 0;
+    md = __hiloint2double(thi, 0) - T;
+    return j;
+}
+
 // Boys function F_0..F_L at T (Eq. boys), written to F[0..L].
 // T < kBoysTmax: F_L by its Taylor expansion about the nearest grid point
-//   F_L(T0 + d) = sum_{k<7} F_{L+k}(T0) (-d)^k / k!     (|d| <= 1/64)
+//   F_L(T0 + d) = sum_{k<7} F_{L+k}(T0) (-d)^k / k!     (|d| <= 1/64 + 2^-14)
 // (table rows hold F_{L+k}(T0)/k! and exp(-T0)), exp(-T) = exp(-T0) exp(-d)
 // with exp(-d) by its own degree-6 Taylor polynomial, then the downward
 // recursion F_n = (2T F_{n+1} + exp(-T)) / (2n+1).
@@ -30,11 +72,8 @@ constexpr double kHalfSqrtPi = 0.88622692545275801365;
 __device__ __forceinline__ void boys_eval(int L, double T, const double* __restrict__ tab, double* F)
 {
     if (T < kBoysTmax) {
-        const float Tf = (float)T;
-        int j = __float2int_rn(Tf * (float)kBoysInvStep);
-        j = j < 0 ? 0 : (j > kBoysGrid - 1 ? kBoysGrid - 1 : j);
-        const double T0 = (double)((float)j * (float)kBoysStep);  // exact
-        const double md = T0 - T;                                  // -d
+        double md;  // -d
+        const int j = boys_grid(T, md);
         const double2* row = reinterpret_cast<const double2*>(tab + (size_t)j * 8);
         const double2 r01 = __ldg(row), r23 = __ldg(row + 1), r45 = __ldg(row + 2), r67 = __ldg(row + 3);
         double f = r67.x;
@@ -60,7 +99,7 @@ __device__ __forceinline__ void boys_eval(int L, double T, const double* __restr
             F[n] = f;
         }
     } else {
-        const double rt = rsqrt(T);
+        const double rt = rsqrt_fp64(T);
         const double inv2T = 0.5 * rt * rt;
         double f = kHalfSqrtPi * rt;
         F[0] = f;
@@ -74,7 +113,8 @@ __device__ __forceinline__ void boys_eval(int L, double T, const double* __restr
 // Auxiliary integrals of one primitive quartet (Eqs. 0m and r-rr):
 //   R[e] = [r_e]^(0) for every Hermite function e of order <= L (tetrahedral
 //   numbering), given
-//   base[n] = [0]^(n) = pref (-2 rho)^n F_n(T), n = 0..L,
+//   base[n] = [0]^(n) = pref (-2 rho)^n F_n(T), n = 0..L (pref less the pair
+//   factors that the E tables carry),
 //   X = P - Q.
 // The table `st` gives for each e >= 1 the axis i and the sources e-1_i and
 // e-2_i.  Level by level, n = L-1 down to 0, all entries of order 1..L-n
@@ -160,11 +200,8 @@ template <int L>
 __device__ __forceinline__ void boys_eval_c(double T, const double* __restrict__ tab, double (&F)[L + 1])
 {
     if (T < kBoysTmax) {
-        const float Tf = (float)T;
-        int j = __float2int_rn(Tf * (float)kBoysInvStep);
-        j = j < 0 ? 0 : (j > kBoysGrid - 1 ? kBoysGrid - 1 : j);
-        const double T0 = (double)((float)j * (float)kBoysStep);
-        const double md = T0 - T;
+        double md;
+        const int j = boys_grid(T, md);
         const double2* row = reinterpret_cast<const double2*>(tab + (size_t)j * 8);
         const double2 r01 = __ldg(row), r23 = __ldg(row + 1), r45 = __ldg(row + 2), r67 = __ldg(row + 3);
         double f = r67.x;
@@ -191,7 +228,7 @@ __device__ __forceinline__ void boys_eval_c(double T, const double* __restrict__
             F[n] = f;
         }
     } else {
-        const double rt = rsqrt(T);
+        const double rt = rsqrt_fp64(T);
         const double inv2T = 0.5 * rt * rt;
         double f = kHalfSqrtPi * rt;
         F[0] = f;
@@ -249,13 +286,14 @@ __device__ __forceinline__ void aux_integrals_c(const double* pb, const double* 
                                                 RPtr R)
 {
     const double zp = pb[PS_P], zq = pk[PS_P];
-    const double rs = rsqrt(zp + zq);
+    const double rs = rsqrt_fp64(zp + zq);
     const double rho = zp * zq * (rs * rs);
     const double X = pb[PS_PX] - pk[PS_PX], Y = pb[PS_PY] - pk[PS_PY], Z = pb[PS_PZ] - pk[PS_PZ];
     const double T = rho * fma(X, X, fma(Y, Y, Z * Z));
     double base[L + 1];
     boys_eval_c<L>(T, boys, base);
-    double f = pb[PS_INVP] * pk[PS_INVP] * rs;  // 2 pi^(5/2) / (zp zq sqrt(zp+zq))
+    // 2 pi^(5/2) / (zp zq sqrt(zp+zq)), less the pair factors carried by E
+    double f = rs;
     const double m2rho = -2.0 * rho;
 #pragma unroll
     for (int n = 0; n <= L; ++n) {

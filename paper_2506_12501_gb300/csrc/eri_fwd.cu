@@ -209,7 +209,6 @@ __global__ void pair_kernel_t(PairArgs a)
             double* o = a.ps + (size_t)g * PS_N;
             o[PS_P] = 1.0;
             o[PS_PX] = o[PS_PY] = o[PS_PZ] = 0.0;
-            o[PS_INVP] = 1.0;
             continue;
         }
         const int i1 = s / K2, i2 = s - i1 * K2;
@@ -230,8 +229,12 @@ __global__ void pair_kernel_t(PairArgs a)
             AB2 = fma(d, d, AB2);
         }
         // K_AB c_1 c_2 carried by the x-axis bootstrap E_00^0 (Eq. E2-000),
-        // 1 on y and z: the products E^x E^y E^z are unchanged.
-        const double e00x = a.coefs[p1] * c2 * exp(-z1 * z2 * invp * AB2);
+        // 1 on y and z: the products E^x E^y E^z are unchanged.  So is the
+        // pair's factor of the Eq. 0m prefactor, 2 pi^(5/2) / zeta_p on the
+        // bra and 1 / zeta_q on the ket: every E of the pair (per-axis tables
+        // and products alike) carries it once, and [0]^(m) needs only the
+        // quartet's 1/sqrt(zeta_p + zeta_q).
+        const double e00x = a.coefs[p1] * c2 * exp(-z1 * z2 * invp * AB2) * (a.ket ? invp : kTwoPi52 * invp);
         const int ext = RAISED ? 2 : 0;
         // largest raised indices: the adjoint raises both by 2; the
         // horizontal-recursion form needs E_{i,0} for i <= l1 + l2
@@ -295,7 +298,6 @@ __global__ void pair_kernel_t(PairArgs a)
         o[PS_PX] = P[0];
         o[PS_PY] = P[1];
         o[PS_PZ] = P[2];
-        o[PS_INVP] = a.ket ? invp : kTwoPi52 * invp;
     }
 }
 

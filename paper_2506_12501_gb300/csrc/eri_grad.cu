@@ -473,13 +473,13 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                     // the compile-time path for low orders
                     if (!coop && aux_integrals_fixed(L2, pb, pk, a.boys, R)) continue;
                     const double zp = pb[PS_P], zq = pk[PS_P];
-                    const double rs = rsqrt(zp + zq);
+                    const double rs = rsqrt_fp64(zp + zq);
                     const double rho = zp * zq * (rs * rs);
                     const double X = pb[PS_PX] - pk[PS_PX], Y = pb[PS_PY] - pk[PS_PY], Z = pb[PS_PZ] - pk[PS_PZ];
                     const double T = rho * fma(X, X, fma(Y, Y, Z * Z));
                     double base[kLtotMax + 1];
                     boys_eval(L2, T, a.boys, base);
-                    double f = pb[PS_INVP] * pk[PS_INVP] * rs;
+                    double f = rs;  // the pair factors of Eq. 0m are in the E tables
                     const double m2rho = -2.0 * rho;
                     for (int n = 0; n <= L2; ++n) {
                         base[n] *= f;

@@ -23,8 +23,14 @@ constexpr int kNhMax = (kLtotMax + 1) * (kLtotMax + 2) * (kLtotMax + 3) / 6;
 
 // Boys-function table: grid T_j = j * kBoysStep, j = 0..kBoysGrid-1.
 constexpr int kBoysInvStep = 32;           // 1/step (a power of two: T*32 is exact)
+constexpr int kBoysLog2InvStep = 5;
+static_assert(kBoysInvStep == 1 << kBoysLog2InvStep, "the grid step is a power of two");
 constexpr double kBoysStep = 1.0 / kBoysInvStep;
-constexpr double kBoysTmax = 80.0;         // beyond: large-T form (Section 3.2.1)
+// Beyond kBoysTmax the large-T form (Section 3.2.1).  The grid reaches past
+// the arguments of most primitive quartets of compact basis sets (T = rho
+// |P-Q|^2 up to a few hundred), so that the lanes of a warp seldom split
+// between the two forms (a warp that does runs both).
+constexpr double kBoysTmax = 320.0;
 constexpr int kBoysGrid = (int)(kBoysTmax * kBoysInvStep) + 2;
 constexpr int kBoysOrder = 7;              // Taylor terms k = 0..6, |delta| <= 1/64
 constexpr int kBoysMtab = ERI_BOYS_MMAX + kBoysOrder;  // rows hold F_0..F_kBoysMtab
@@ -96,7 +102,10 @@ struct ClassTables {
 };
 
 // Primitive-pair scalars written by the pair kernel.
-enum { PS_P = 0, PS_PX, PS_PY, PS_PZ, PS_INVP, PS_N };
+// The prefactor 2 pi^(5/2) / zeta_p (bra) or 1 / zeta_q (ket) of Eq. 0m is
+// not among them: it is folded into the pair's E tables (and so into its E
+// products), so the kernels scale [0]^(m) by 1/sqrt(zeta_p + zeta_q) only.
+enum { PS_P = 0, PS_PX, PS_PY, PS_PZ, PS_N };
 
 // Device-side error word values (first error wins).
 enum { DEV_OK = 0, DEV_ECLASS = 1, DEV_EINDEX = 2, DEV_EK = 3, DEV_ETIMEOUT = 4 };

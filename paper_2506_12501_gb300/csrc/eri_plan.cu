@@ -248,6 +248,27 @@ struct TypeTables {
 int build_pair_tables_on(const eri_basis_t* basis, const int32_t* d_pairs, int64_t npairs, int l1, int l2, int KS,
                          int T, const uint8_t* fac, int ket, int split, PairTables* out, cudaStream_t st);
 
+// The plan kernels' dynamic shared-memory limit (a per-device function
+// attribute) only ever grows.  Every plan's graph launches the kernel with
+// that plan's own size, and the creation of a later plan (its tile trials,
+// its final size) must not lower the limit below a size an earlier plan's
+// replay still uses.
+static bool raise_smem_limit(bool split, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, size_t> cur;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& c = cur[std::make_pair(dev, split ? 1 : 0)];
+    if (bytes <= c) return true;
+    auto kern = split ? plan_kernel<true> : plan_kernel<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return false;
+    c = bytes;
+    return true;
+}
+
 // Autotuner: time candidate tile shapes of one job on a sample of its own
 // work items (the persistent kernel, digestion into a scratch energy with a
 // zero density) and return the fastest.  Candidates: every TQ (powers of two
@@ -306,8 +327,7 @@ static bool autotune_job(const FwdArgs& base, const std::vector<WorkItem>& sampl
         FwdArgs a = base;
         set_tile(a, tp);
         cudaMemcpyAsync(d_job, &a, sizeof(a), cudaMemcpyHostToDevice, st);
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
-            continue;
+        if (!raise_smem_limit(split, tp.bytes)) continue;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, tp.bytes);
         const int grid = std::max(1, per_sm) * sm_count();
@@ -687,8 +707,7 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
     p->owned.push_back(p->d_counter);
     auto kern = split ? plan_kernel<true> : plan_kernel<false>;
     if (p->smem > (size_t)max_smem_optin()) return plan_fail(p, ERI_EINVAL);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess)
-        return plan_fail(p, ERI_ECUDA);
+    if (!raise_smem_limit(split, p->smem)) return plan_fail(p, ERI_ECUDA);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, p->smem);
     p->grid = std::max(1, per_sm) * sm_count();
@@ -710,6 +729,7 @@ static int plan_launch(eri_plan_t* p, const PlanParams& prm_in, cudaStream_t st)
     if (cudaMemcpyAsync(p->d_params, &p->params, sizeof(PlanParams), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return ERI_ECUDA;
     const int egrid = 2 * sm_count();
+    if (!raise_smem_limit(p->flags & ERI_PLAN_SPLIT, p->smem)) return ERI_ECUDA;
     if (!p->exec) {
         cudaStream_t cs;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return ERI_ECUDA;

@@ -652,14 +652,14 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 // and for the warp-shared recursion of small tiles
                 if (coop || !aux_integrals_fixed(ct.L, pb, pk, a.boys, R)) {
                     const double zp = pb[PS_P], zq = pk[PS_P];
-                    const double rs = rsqrt(zp + zq);
+                    const double rs = rsqrt_fp64(zp + zq);
                     const double rho = zp * zq * (rs * rs);
                     const double X = pb[PS_PX] - pk[PS_PX], Y = pb[PS_PY] - pk[PS_PY], Z = pb[PS_PZ] - pk[PS_PZ];
                     const double PQ2 = fma(X, X, fma(Y, Y, Z * Z));
                     const double T = rho * PQ2;
                     double base[kLtotMax + 1];
                     boys_eval(ct.L, T, a.boys, base);
-                    double f = pb[PS_INVP] * pk[PS_INVP] * rs;  // 2 pi^(5/2) / (zp zq sqrt(zp+zq))
+                    double f = rs;  // 2 pi^(5/2) / (zp zq sqrt(zp+zq)) less the pair factors in E
                     const double m2rho = -2.0 * rho;
                     for (int n = 0; n <= ct.L; ++n) {
                         base[n] *= f;

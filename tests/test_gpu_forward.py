@@ -13,12 +13,18 @@ pytestmark = pytest.mark.gpu
 
 
 def test_boys_kernel_against_oracle(cuda):
-    """Boys function over the tabulated range, across the grid end (T = 80) and
-    far beyond, every order up to ERI_BOYS_MMAX; relative error below
-    (2 + 0.3 m) 1e-15 (the recursions add about one rounding per order)."""
+    """Boys function over the tabulated range, across the grid end (T = 320)
+    and far beyond, every order up to ERI_BOYS_MMAX; relative error below
+    (2 + 0.3 m) 1e-15 (the recursions add about one rounding per order).
+    The arguments include grid points, the midpoints between them (where the
+    grid index is decided by a truncated float image of T), tiny and
+    subnormal T."""
     rng = np.random.default_rng(0)
-    T = np.concatenate([np.linspace(0.0, 80.5, 2001), rng.uniform(0, 80, 2000), [79.999, 80.0, 80.0001],
-                        np.geomspace(1e-12, 1e5, 500)])
+    grid = np.arange(0, 320 * 32 + 1) / 32.0
+    mids = grid[:-1] + 1.0 / 64
+    T = np.concatenate([np.linspace(0.0, 320.5, 4001), rng.uniform(0, 320, 4000), [319.999, 320.0, 320.0001],
+                        grid[::7], mids[::5], np.nextafter(mids[::11], 0), np.nextafter(mids[::13], 1e9),
+                        np.geomspace(1e-12, 1e5, 500), [0.0, 5e-324, 1e-310, 1e-300]])
     for mmax in (0, 1, 4, 8, 12, 16, 20):
         got = eri.eri_boys(mmax, torch.as_tensor(T, device=cuda)).cpu().numpy()
         ref = oracle.boys(mmax, T, prec="ld").astype(np.float64)
