@@ -332,16 +332,23 @@ def split_variant(args, eri, dev):
             t64 = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=o64), warm=False)
             torch.cuda.profiler.stop()
             f64form = eri.eri_last_form()
+            f64tile = eri.eri_last_tile()
             eri.eri_batch(cls, db, b, k, warm, out=ow, precision=eri.ERI_PREC_SPLIT)
             torch.cuda.profiler.start()
             tsp = timed(lambda: eri.eri_batch(cls, db, b, k, qq, out=osp, precision=eri.ERI_PREC_SPLIT), warm=False)
             torch.cuda.profiler.stop()
+            sptile = eri.eri_last_tile()
+            spform = eri.eri_last_form()
             del ow
             nsamp = 2 if (cls == (3, 3, 3, 3) and K == 5) else (4 if K == 5 else 16)
             (e64, esp), refmax = oracle_sample_error(cls, basis, bra, ket, q, [o64, osp], nsamp)
             flops = opcount.sparse_flops(cls, K * K, K * K, form=f64form) * nq
             res["".join(map(str, cls)) + f"_K{K}"] = {
                 "quartets": nq, "fp64_ms": round(t64, 3), "split_ms": round(tsp, 3), "speedup": t64 / tsp,
+                "fp64_form": ("swapped " if f64form[0] else "") + ("hrr" if f64form[1] else "plain"),
+                "split_form": "swapped" if spform[0] else "plain",
+                "fp64_tile": "TQ{tq} IC{ic} x{threads}".format(**f64tile),
+                "split_tile": "TQ{tq} IC{ic} x{threads}".format(**sptile),
                 "fp64_quartets_per_s": nq / (t64 / 1e3), "split_quartets_per_s": nq / (tsp / 1e3),
                 "fp64_gflops_sparse": flops / (t64 / 1e3) / 1e9,
                 "fp64_frac_fp64_peak": flops / (t64 / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
@@ -602,6 +609,7 @@ def run_library(args):
     dense = {c: opcount.dense_flops(c, Kps ** 2, Kps ** 2) for c in batches}
     stream = torch.cuda.current_stream()
     forms = {}
+    tiles = {}
 
     def step(timing=None):
         for cls, (b, k, q) in dev_batches.items():
@@ -611,6 +619,7 @@ def run_library(args):
                 e0.record(stream)
             eri.eri_batch(cls, db, b, k, q, out=outs[cls], precision=prec)
             forms[cls] = eri.eri_last_form()
+            tiles[cls] = eri.eri_last_tile()
             if timing is not None:
                 e1.record(stream)
                 timing[cls].append((e0, e1))
@@ -659,6 +668,7 @@ def run_library(args):
         per_class["".join(map(str, cls))] = {
             "ms": round(ms, 4), "qps": round(qps),
             "form": ("swapped " if forms[cls][0] else "") + ("hrr" if forms[cls][1] else "plain"),
+            "tile": "TQ{tq} IC{ic} x{threads}".format(**tiles[cls]),
             "gflops": round(sparse[cls] * qps / 1e9, 1),
             "frac": round(sparse[cls] * qps / 1e9 / FP64_PEAK_GFLOPS, 4),
             "frac_dense": round(dense[cls] * qps / 1e9 / FP64_PEAK_GFLOPS, 4)}

@@ -254,9 +254,9 @@ int eri_batch3(int32_t lx, int32_t lc, int32_t ld, const eri_basis_t* basis,
  * library, and its constant tables in fixed arrays as well.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
  *
- * - The fixed arrays take ERI_NOALLOC_SCRATCH_BYTES (+ about 2.6 MB of
+ * - The fixed arrays take ERI_NOALLOC_SCRATCH_BYTES (+ about 10 MB of
  *   tables) on every GPU that loads the library, until the process exits.
- * - A batch needs 8*(nbra*KB*(T_ab+5) + nket*KK*(T_cd+5)) bytes of scratch
+ * - A batch needs 8*(nbra*KB*(T_ab+4) + nket*KK*(T_cd+4)) bytes of scratch
  *   plus small padding (KB = largest K_a*K_b, T_ab = nonzero Hermite terms
  *   of the class); a larger batch is rejected with ERI_EINVAL before any
  *   integral kernel runs.  Split such batches.
@@ -389,6 +389,17 @@ int eri_plan_slice_info(eri_plan_t* plan, int64_t* nitems, int64_t* nquartets, d
  * The paper transforms the ket first and has no recursion form (Section 3.2.2).
  */
 int eri_last_form(int32_t* swapped, int32_t* hrr);
+
+/*
+ * eri_last_tile -- the tile shape of the calling thread's last successful
+ * eri_batch launch (measurement support): *tq quartets per tile, *ic bra
+ * primitives per chunk of the auxiliary integrals, *threads per CTA (256, or
+ * 512 for a tile that fills an SM's shared memory alone), *smem_bytes of
+ * dynamic shared memory per CTA.  HOST pointers, each may be NULL.  Returns
+ * ERI_EINVAL before the thread's first eri_batch launch.  No counterpart in
+ * the paper, whose kernels run on CPU cores (Section 3).
+ */
+int eri_last_tile(int32_t* tq, int32_t* ic, int32_t* threads, int32_t* smem_bytes);
 
 /*
  * eri_set_forms -- restrict the forms later eri_batch calls (all threads)

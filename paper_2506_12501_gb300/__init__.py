@@ -21,6 +21,7 @@ from .binding import (  # noqa: F401
     ERI_NOALLOC_SCRATCH_BYTES,
     eri_last_status,
     eri_last_form,
+    eri_last_tile,
     eri_set_forms,
     ERI_FORM_PLAIN, ERI_FORM_HRR,
     eri_last_grad_forms,

@@ -45,7 +45,7 @@ EXPORTS = ["eri_boys", "eri_batch", "eri_batch_grad", "eri_last_status", "eri_er
            "eri_plan_execute", "eri_plan_set_budget", "eri_plan_status", "eri_plan_info", "eri_plan_job",
            "eri_plan_destroy", "eri_last_form", "eri_set_forms", "eri_plan_coulomb", "eri_plan_jk", "eri_plan_job_degrees", "eri_batch3", "eri_solid_harmonics", "eri_batch_sph",
            "eri_last_grad_forms", "eri_set_grad_forms", "eri_peak_probe",
-           "eri_partition", "eri_plan_set_slice", "eri_plan_slice_info"]
+           "eri_partition", "eri_plan_set_slice", "eri_plan_slice_info", "eri_last_tile"]
 ERI_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 ERI_PLAN_STORE, ERI_PLAN_SPLIT, ERI_PLAN_NO_TUNE = 1, 2, 4
 ERI_FORM_PLAIN, ERI_FORM_HRR = 0x3, 0xC
@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
                                          P, P, P]
             L.eri_last_status.argtypes = [P]
             L.eri_last_form.argtypes = [P, P]
+            L.eri_last_tile.argtypes = [P, P, P, P]
             L.eri_set_forms.argtypes = [ctypes.c_int32]
             L.eri_last_grad_forms.argtypes = [P, P]
             L.eri_set_grad_forms.argtypes = [ctypes.c_int32]
@@ -323,6 +324,14 @@ def eri_last_form() -> tuple:
     hrr = ctypes.c_int32()
     _check(lib().eri_last_form(ctypes.byref(sw), ctypes.byref(hrr)), "eri_last_form")
     return bool(sw.value), bool(hrr.value)
+
+
+def eri_last_tile() -> dict:
+    """Tile shape of this thread's last eri_batch launch: quartets per tile, bra primitives per chunk,
+    threads per CTA and dynamic shared memory (bytes)."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().eri_last_tile(*(ctypes.byref(x) for x in v)), "eri_last_tile")
+    return {"tq": v[0].value, "ic": v[1].value, "threads": v[2].value, "smem_bytes": v[3].value}
 
 
 def eri_set_grad_forms(mask: int) -> int:

@@ -311,8 +311,19 @@ static void launch_pair(const PairArgs& p, int grid, cudaStream_t st)
         pair_kernel_t<false><<<grid, 128, 0, st>>>(p);
 }
 
-static const auto fwd_kernel = fwd_kernel_t<false>;
-static const auto fwd_kernel_split = fwd_kernel_t<true>;
+static const auto fwd_kernel = fwd_kernel_t<false, kNT>;
+static const auto fwd_kernel_split = fwd_kernel_t<true, kNT>;
+
+// A tile whose shared memory leaves room for one CTA per SM (each CTA also
+// takes a 1 KB system reserve and a few bytes of static shared memory).
+static bool one_cta_per_sm(size_t bytes) { return 2 * (bytes + 1024 + 64) > (size_t)smem_per_sm(); }
+
+// The forward kernel for a precision and a CTA width (kNT or kNTWide).
+static void (*fwd_kern(int split, int nt))(FwdArgs)
+{
+    if (nt == kNTWide) return split ? fwd_kernel_t<true, kNTWide> : fwd_kernel_t<false, kNTWide>;
+    return split ? fwd_kernel_split : fwd_kernel;
+}
 
 // ---------------------------------------------------------------------------
 // Boys entry kernel
@@ -381,7 +392,7 @@ static void hrr_buffers(const ClassTables& ct, int TQ, size_t* A, size_t* B)
     }
 }
 
-bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp)
+bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp, int split)
 {
     size_t off = 0;
     auto take = [&](size_t nd) {
@@ -395,7 +406,16 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     tp->e_smem = e_smem;
     tp->sEbS = e_smem ? odd_up(KB * ct.Tab) : 0;
     tp->sEkS = e_smem ? odd_up(KK * ct.Tcd) : 0;
-    size_t r_need = (size_t)((TQ * IC * KK) | 1) * ct.nhl;  // odd row stride
+    // the paired layout of the auxiliary integrals where the split form's
+    // blocked ket stage packs two ket primitives per FP32 instruction, for
+    // tiles that accumulate in memory: with register accumulators live
+    // through the ket stage the packed loop runs short of registers (measured
+    // on (ff|dd), K = 5: 1.27 times slower than the unpacked loop; (ff|ff),
+    // K = 5, accumulating in memory: 1.06 times faster)
+    const bool acc_regs = TQ * ct.nab * ct.ncd <= kNT * kNACC;
+    tp->r_pairs = split && split_block_width(ct.nhb - ct.pb0) && KK >= 2 && !acc_regs ? 1 : 0;
+    const int KKr = tp->r_pairs ? (KK + 1) & ~1 : KK;
+    size_t r_need = (size_t)r_row_stride(TQ * IC * KKr, tp->r_pairs) * ct.nhl;
     size_t hA = 0, hB = 0;
     if (ct.hrr || ct.sph) {
         // the recursion (and solid-harmonic) buffers alias every staging
@@ -439,25 +459,26 @@ bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_sm
     if (!e_smem && TQ == 1 && (off + even(ct.Tab)) * 8 <= (size_t)max_smem_optin()) tp->o_Ei = take(ct.Tab);
     tp->o_Er = -1;  // added for the split form by add_e_ring
     tp->bytes = off * 8;
+    tp->nt = kNT;
     tp->acc_regs = (TQ * ct.nab * ct.ncd <= kNT * kNACC) ? 1 : 0;
     if (ct.hrr && !tp->acc_regs) return false;
     return tp->bytes <= (size_t)max_smem_optin();
 }
 
 // Split form: when the blocked ket stage reads its ket E rows from global
-// memory, give every warp a ring of kRingRows rows (KK float pairs each) at
-// the end of the tile's shared memory, if it fits.
+// memory, give every warp (tp->nt / 32 of them) a ring of kRingRows rows (KK
+// float pairs each) at the end of the tile's shared memory, if it fits.
 static void add_e_ring(const ClassTables& ct, int KK, TilePlan* tp)
 {
     tp->o_Er = -1;
     if (tp->e_smem || !split_block_width(ct.nhb - ct.pb0)) return;
-    const size_t off = (tp->bytes / 8 + 1) & ~size_t(1), nd = (size_t)(kNT / 32) * kRingRows * KK;
+    const size_t off = (tp->bytes / 8 + 1) & ~size_t(1), nd = (size_t)(tp->nt / 32) * kRingRows * KK;
     if ((off + nd) * 8 > (size_t)max_smem_optin()) return;
     tp->o_Er = (int)off;
     tp->bytes = (off + nd) * 8;
 }
 
-bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best, size_t max_bytes)
+bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best, size_t max_bytes, int split)
 {
     bool found = false;
     double best_score = -1.0;
@@ -467,7 +488,7 @@ bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* bes
             if (TQ > 1 && (int64_t)TQ > 2 * nq) continue;
             for (int IC = KB; IC >= 1; IC = (IC + 1) / 2 - (IC == 1)) {
                 TilePlan tp;
-                if (!tile_layout(ct, KB, KK, TQ, IC, e_smem, &tp) || (max_bytes && tp.bytes > max_bytes)) {
+                if (!tile_layout(ct, KB, KK, TQ, IC, e_smem, &tp, split) || (max_bytes && tp.bytes > max_bytes)) {
                     if (IC == 1) break;
                     continue;
                 }
@@ -801,8 +822,7 @@ constexpr int64_t kTuneQuartets = 8192;
 static std::map<std::tuple<int, int, int, int, int, int, int, int, int, int>, std::pair<TilePlan, float>> g_tuned;
 static std::mutex g_tuned_mu;
 
-static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cudaStream_t st, TilePlan* best,
-                       float* best_ms_out)
+static bool tuned_tile(const FwdArgs& base, int split, cudaStream_t st, TilePlan* best, float* best_ms_out)
 {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -823,11 +843,21 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
         for (int IC : {base.KB, (base.KB + 1) / 2, 1}) {
             for (int es = 1; es >= 0; --es) {
                 TilePlan tp;
-                if (tile_layout(ct, base.KB, base.KK, TQ, IC, es, &tp) && tp.acc_regs) {
-                    if (split) add_e_ring(ct, base.KK, &tp);
+                if (tile_layout(ct, base.KB, base.KK, TQ, IC, es, &tp, split) && tp.acc_regs) {
                     bool dup = false;
                     for (auto& c : cands) dup |= (c.TQ == TQ && c.IC == IC && c.e_smem == es);
-                    if (!dup) cands.push_back(tp);
+                    if (dup) break;
+                    // a tile that leaves room for one CTA per SM is also tried
+                    // with 512 threads (twice the warps in the same memory)
+                    const bool wide = one_cta_per_sm(tp.bytes);
+                    TilePlan tw = tp;
+                    tw.nt = kNTWide;
+                    if (split) {
+                        add_e_ring(ct, base.KK, &tp);
+                        add_e_ring(ct, base.KK, &tw);
+                    }
+                    cands.push_back(tp);
+                    if (wide && tw.bytes <= (size_t)max_smem_optin()) cands.push_back(tw);
                     break;
                 }
             }
@@ -842,10 +872,11 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
     for (const TilePlan& tp : cands) {
         FwdArgs a = base;
         set_tile(a, tp);
+        void (*kern)(FwdArgs) = fwd_kern(split, tp.nt);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
             continue;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, tp.bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tp.nt, tp.bytes);
         const int64_t slots = (int64_t)std::max(per_sm, 1) * sm_count();
         // about four waves of tiles (steady state), at least kTuneQuartets quartets
         const int64_t nq = std::min(base.nq, std::max(kTuneQuartets, 4 * slots * tp.TQ));
@@ -856,12 +887,12 @@ static bool tuned_tile(const FwdArgs& base, void (*kern)(FwdArgs), int split, cu
         float ms = 3e38f;
         bool timed = true;
         count_launch();
-        kern<<<(int)grid, kNT, tp.bytes, st>>>(a);
+        kern<<<(int)grid, tp.nt, tp.bytes, st>>>(a);
         for (int rep = 0; rep < 3 && timed; ++rep) {
             float t = 0.f;
             cudaEventRecord(e0, st);
             count_launch();
-            kern<<<(int)grid, kNT, tp.bytes, st>>>(a);
+            kern<<<(int)grid, tp.nt, tp.bytes, st>>>(a);
             cudaEventRecord(e1, st);
             timed = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
             ms = std::min(ms, t);
@@ -993,14 +1024,14 @@ extern "C" int eri_boys(int mmax, const double* T, int64_t n, double* F, void* s
 static int forward_args(const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
                         const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nqq, double* out,
                         const ClassTables* ct, const PairTables& pb, const PairTables& pk, int KB, int KK, int swapped,
-                        cudaStream_t st, FwdArgs* a, TilePlan* tp)
+                        int split, cudaStream_t st, FwdArgs* a, TilePlan* tp)
 {
     int err = ERI_OK;
     const double* boys = get_boys_table(ct->L, st, &err);
     if (!boys) return err;
     const RStep* rs = get_rsteps(st, &err);
     if (!rs) return err;
-    if (!plan_tiles(*ct, KB, KK, nqq, tp)) return ERI_EINVAL;
+    if (!plan_tiles(*ct, KB, KK, nqq, tp, 0, split)) return ERI_EINVAL;
     *a = FwdArgs{};
     a->ct = *ct;
     a->boys = boys;
@@ -1032,6 +1063,7 @@ static int forward_args(const eri_basis_t* basis, const int32_t* bra_pairs, int6
 }
 
 static thread_local int g_last_form = -1;
+static thread_local TilePlan g_last_tile{};
 
 // One forward batch of any kind (0: 4-centre; 1, 2: 3-centre with the unit
 // function as the second bra shell, Cartesian or solid-harmonic x): form
@@ -1041,7 +1073,6 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
                        int split, int kind, cudaStream_t st)
 {
     const int64_t nqq = quartets ? nq : nbra * nket;
-    void (*kern)(FwdArgs) = split ? fwd_kernel_split : fwd_kernel;
     const ClassTables* ct = nullptr;
     PairTables pb{}, pk{};
     int KB = 0, KK = 0, kmax[4];
@@ -1062,7 +1093,7 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
                               &KK, kmax, allow, f, split, kind, &mixed);
         if (e != ERI_OK) return e;
         e = forward_args(basis, bra_pairs, nbra, ket_pairs, nket, quartets, nqq, out, ct, pb, pk, KB, KK,
-                         f->form & 1, st, a, tp);
+                         f->form & 1, split, st, a, tp);
         if (e != ERI_OK) return e;
         if (mixed && !order && nqq > 1) {
             unsigned long long* queue = nullptr;
@@ -1074,6 +1105,7 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     };
     FwdArgs a;
     TilePlan tp;
+    bool from_tuner = false;
     int err = prepare(&fc, &a, &tp);
     if (err != ERI_OK) return err;
     // large batches: tile shape from the autotuner (cached per kernel class,
@@ -1083,7 +1115,7 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     if (nqq >= kTuneMinQuartets) {
         TilePlan best;
         float ms = 0.f;
-        bool tuned = tuned_tile(a, kern, split, st, &best, &ms);
+        bool tuned = tuned_tile(a, split, st, &best, &ms);
         if (!fc.cached && fc.alt >= 0) {
             const eri_class_t sig = cls;
             const int KB0 = (fc.form & 1) ? KK : KB, KK0 = (fc.form & 1) ? KB : KK;  // caller's orientation
@@ -1093,7 +1125,7 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
             TilePlan tp1, best1;
             float ms1 = 0.f;
             bool tuned1 = false;
-            if (prepare(&f1, &a1, &tp1) == ERI_OK) tuned1 = tuned_tile(a1, kern, split, st, &best1, &ms1);
+            if (prepare(&f1, &a1, &tp1) == ERI_OK) tuned1 = tuned_tile(a1, split, st, &best1, &ms1);
             const bool take_alt = tuned1 && (!tuned || ms1 < ms);
             remember_form(sig, KB0, KK0, split, kind, take_alt ? f1.form : fc.form);
             if (take_alt) {
@@ -1114,24 +1146,33 @@ static int run_forward(eri_class_t cls, const eri_basis_t* basis, const int32_t*
             tp = best;
             set_tile(a, tp);
             a.ntiles = (nqq + tp.TQ - 1) / tp.TQ;
+            from_tuner = true;
         }
     }
-    if (split && tp.o_Er < 0) {
-        add_e_ring(a.ct, a.KK, &tp);
+    if (!from_tuner) {
+        // a tile the tuner did not choose (accumulation in memory, or a small
+        // batch): 512 threads when the tile leaves room for one CTA per SM
+        // only (measured on (ff|ff): FP64 1.07 and 1.14 times faster at K = 5
+        // and 1, split 1.27 and 1.34), then, split, the ring of ket E rows;
+        // the tuner's candidates come with both settled
+        if (one_cta_per_sm(tp.bytes)) tp.nt = kNTWide;
+        if (split) add_e_ring(a.ct, a.KK, &tp);
         set_tile(a, tp);
     }
+    void (*kern)(FwdArgs) = fwd_kern(split, tp.nt);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.bytes) != cudaSuccess)
         return ERI_ECUDA;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, tp.bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tp.nt, tp.bytes);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)per_sm * sm_count());
     {
         ProfScope ps(PROF_FWD, st);
-        kern<<<(int)grid, kNT, tp.bytes, st>>>(a);
+        kern<<<(int)grid, tp.nt, tp.bytes, st>>>(a);
     }
     if (cudaGetLastError() != cudaSuccess) return ERI_ECUDA;
     g_last_form = fc.form;
+    g_last_tile = tp;
     return ERI_OK;
 }
 
@@ -1210,6 +1251,16 @@ extern "C" int eri_set_forms(int32_t mask)
 {
     if (mask < 0 || mask > 0xF) return ERI_EINVAL;
     return g_form_mask.exchange(mask ? mask : 0xF);
+}
+
+extern "C" int eri_last_tile(int32_t* tq, int32_t* ic, int32_t* threads, int32_t* smem_bytes)
+{
+    if (g_last_form < 0) return ERI_EINVAL;
+    if (tq) *tq = g_last_tile.TQ;
+    if (ic) *ic = g_last_tile.IC;
+    if (threads) *threads = g_last_tile.nt;
+    if (smem_bytes) *smem_bytes = (int32_t)g_last_tile.bytes;
+    return ERI_OK;
 }
 
 extern "C" int eri_last_form(int32_t* swapped, int32_t* hrr)

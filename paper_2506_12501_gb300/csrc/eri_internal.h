@@ -203,12 +203,30 @@ struct TilePlan {
     int o_hB, o_geo;  // horizontal-recursion form: second buffer (the first is at 0), A-B/C-D per quartet
     int o_dj;         // Coulomb digestion scratch (TQ + nab_f doubles)
     int o_Ei;         // one-quartet tile, E not staged: the bra E products of the current bra primitive ([Tab]), or -1
-    int o_Er;         // split form, blocked ket stage, E not staged: three ket E rows per warp ([8][3][KK] float pairs), or -1
+    int o_Er;         // split form, blocked ket stage, E not staged: three ket E rows per warp ([nt/32][3][KK] float pairs), or -1
     size_t bytes;
+    int nt;           // threads per CTA: 256 (two CTAs per SM fit the registers) or 512 (one CTA per SM)
+    int r_pairs;      // split form, blocked ket stage: auxiliary integrals in the paired layout (see r_row_stride)
 };
-// max_bytes > 0: only shapes whose shared memory stays within it
-bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best, size_t max_bytes = 0);
-bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp);
+// max_bytes > 0: only shapes whose shared memory stays within it; split: the
+// tile runs the split-precision transforms
+bool plan_tiles(const ClassTables& ct, int KB, int KK, int64_t nq, TilePlan* best, size_t max_bytes = 0,
+                int split = 0);
+bool tile_layout(const ClassTables& ct, int KB, int KK, int TQ, int IC, int e_smem, TilePlan* tp, int split = 0);
+
+// The tile's auxiliary integrals [r]^(0) are a table of nhl rows (Hermite
+// functions) by NI columns (quartet, bra primitive, ket primitive), ket
+// primitive fastest.  Plain layout: a double per entry, the row stride odd so
+// that the scattered 8-byte rows a warp reads spread over the banks.  Paired
+// layout (split form, blocked ket stage): the per-(quartet, bra primitive)
+// column blocks are rounded up to an even number of ket primitives, and each
+// two columns k, k+1 (16 bytes) hold the float pairs as (hi_k, hi_k+1, lo_k,
+// lo_k+1), so that one 16-byte load feeds two packed FP32 chains; the row
+// stride is twice an odd number of such pairs.
+__host__ __device__ constexpr int r_row_stride(int NI, int pairs)
+{
+    return pairs ? ((((NI + 1) >> 1) | 1) << 1) : (NI | 1);
+}
 
 // Measurement hook: events around launches of kernel `id` (eri_profile_*).
 enum { PROF_FWD = 0, PROF_GRAD = 1, PROF_PAIR = 2, PROF_PREPASS = 3, PROF_N = 8 };

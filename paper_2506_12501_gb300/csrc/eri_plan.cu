@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kNT, 2)
                 if (P.out) a.out = P.out + (int64_t)(size_t)a.out;  // stored as an offset
             }
             __syncthreads();
-            stage_class_tables(a, sm);
+            stage_class_tables<kNT>(a, sm);
             cur = it.job;
         }
         const int TQ = a.TQ;
@@ -286,7 +286,8 @@ static bool autotune_job(const FwdArgs& base, const std::vector<WorkItem>& sampl
             for (int es = 1; es >= 0; --es) {
                 TilePlan tp;
                 // shapes within half an SM's shared memory (two CTAs per SM)
-                if (tile_layout(base.ct, base.KB, base.KK, TQ, IC, es, &tp) && tp.acc_regs && tp.bytes <= half_sm) {
+                if (tile_layout(base.ct, base.KB, base.KK, TQ, IC, es, &tp, split) && tp.acc_regs &&
+                    tp.bytes <= half_sm) {
                     bool dup = false;
                     for (auto& c : cands) dup |= (c.TQ == TQ && c.IC == IC && c.e_smem == es);
                     if (!dup) cands.push_back(tp);
@@ -569,8 +570,8 @@ extern "C" int eri_plan_create(const eri_basis_t* basis, double threshold, int f
             TilePlan tp;
             // the persistent kernel runs every job with the largest job's
             // shared memory: keep each job within half an SM so two CTAs fit
-            if (!(plan_tiles(*ct, KB, KK, nq, &tp, half_sm) && tp.acc_regs) &&
-                !(plan_tiles(*ct, KB, KK, nq, &tp) && tp.acc_regs))
+            if (!(plan_tiles(*ct, KB, KK, nq, &tp, half_sm, split) && tp.acc_regs) &&
+                !(plan_tiles(*ct, KB, KK, nq, &tp, 0, split) && tp.acc_regs))
                 return plan_fail(p, ERI_EINVAL);
             FwdArgs& a = J.args;
             a = FwdArgs{};

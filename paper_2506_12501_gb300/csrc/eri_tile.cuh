@@ -16,7 +16,8 @@
 
 namespace eri {
 
-constexpr int kNT = 256;   // threads per CTA of the tile kernels
+constexpr int kNT = 256;   // threads per CTA of the tile kernels (plans; most eri_batch tiles)
+constexpr int kNTWide = 512;  // eri_batch tiles that fill an SM's shared memory alone
 constexpr int kNACC = 16;  // outputs per thread held in registers
 
 // Split form: bra Hermite functions per lane in the blocked ket stage (one
@@ -49,6 +50,60 @@ __device__ __forceinline__ void ff_mac(float2 a, float2 b, float& S, float& c)
     const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, z)), __fsub_rn(p, z));
     S = t;
     c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, pe))));
+}
+
+// ---- the same arithmetic on two independent chains at once: packed FP32
+// pairs (PTX f32x2, one 64-bit register holding two floats)
+__device__ __forceinline__ uint64_t f2_pack(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// ff_mac on two chains: (S, c) += a * b lane-wise, with a = (ah, al) and
+// b = (bh, bl) split pairs of each chain, nah = -ah.  The same operations as
+// ff_mac: q = fl(-ah bh) is the rounded product negated (exact), so the
+// exact product error is fma(ah, bh, q), and the TwoSum of S and -q is
+// written with q.
+__device__ __forceinline__ void ff_mac2(uint64_t ah, uint64_t al, uint64_t nah, uint64_t bh, uint64_t bl,
+                                        uint64_t& S, uint64_t& c)
+{
+    const uint64_t q = f2_mul(nah, bh);
+    const uint64_t pe = f2_fma(ah, bh, q);
+    const uint64_t t = f2_sub(S, q);
+    const uint64_t z = f2_sub(t, S);
+    const uint64_t err = f2_sub(f2_sub(S, f2_sub(t, z)), f2_add(q, z));
+    S = t;
+    c = f2_add(c, f2_add(err, f2_fma(ah, bl, f2_fma(al, bh, pe))));
 }
 
 // Loads and stores with an L2 eviction priority (a cache policy made by
@@ -126,6 +181,7 @@ struct FwdArgs {
     int o_dj;                 // Coulomb digestion scratch: [TQ] weights, [nab] bra sums
     int o_Ei;                 // one-quartet tile with E not staged: the bra E products of the current bra primitive, [Tab] (-1: none)
     int o_Er;                 // split blocked ket stage with E not staged: a ring of three ket E rows per warp (-1: none)
+    int r_pairs;              // auxiliary integrals in the paired layout (split form, blocked ket stage)
     int64_t ntiles;
     // work-queue mode (plans): one bra pair, consecutive ket pairs
     int mode;                 // 0: list/product batch, 1: ranged (bra rbra, kets rk0..)
@@ -166,6 +222,7 @@ inline void set_tile(FwdArgs& a, const TilePlan& tp)
     a.o_dj = tp.o_dj;
     a.o_Ei = tp.o_Ei;
     a.o_Er = tp.o_Er;
+    a.r_pairs = tp.r_pairs;
 }
 
 struct Strided {
@@ -235,6 +292,7 @@ __device__ __forceinline__ double bra_sum(const double* Eb, int KB, const double
 }
 
 // Class tables into shared memory (each CTA, whenever the class changes).
+template <int NT>
 __device__ __forceinline__ void stage_class_tables(const FwdArgs& a, double* sm)
 {
     const ClassTables& ct = a.ct;
@@ -244,11 +302,11 @@ __device__ __forceinline__ void stage_class_tables(const FwdArgs& a, double* sm)
     int16_t* s_bp = reinterpret_cast<int16_t*>(s_kstart + ct.ncd + 1);
     int16_t* s_kq = s_bp + ct.Tab;
     int16_t* s_pq = s_kq + ct.Tcd;
-    for (int i = tid; i <= ct.nab; i += kNT) s_bstart[i] = ct.bra_start[i];
-    for (int i = tid; i <= ct.ncd; i += kNT) s_kstart[i] = ct.ket_start[i];
-    for (int i = tid; i < ct.Tab; i += kNT) s_bp[i] = ct.bra_p[i];
-    for (int i = tid; i < ct.Tcd; i += kNT) s_kq[i] = ct.ket_q[i];
-    for (int i = tid; i < ct.nhb * ct.nhk; i += kNT) s_pq[i] = ct.pq[i];
+    for (int i = tid; i <= ct.nab; i += NT) s_bstart[i] = ct.bra_start[i];
+    for (int i = tid; i <= ct.ncd; i += NT) s_kstart[i] = ct.ket_start[i];
+    for (int i = tid; i < ct.Tab; i += NT) s_bp[i] = ct.bra_p[i];
+    for (int i = tid; i < ct.Tcd; i += NT) s_kq[i] = ct.ket_q[i];
+    for (int i = tid; i < ct.nhb * ct.nhk; i += NT) s_pq[i] = ct.pq[i];
 }
 
 // W_abcd = D_ab D_cd for the kernel's component pair (ab, cd) of quartet
@@ -271,6 +329,7 @@ __device__ __forceinline__ double digest_weight(const FwdArgs& a, int b, int k, 
 // and J = J' + J'^T afterwards gives J_uv = sum over all (ls) of (uv|ls) D_ls.
 // The bra sums are reduced over the tile in shared memory first (one global
 // atomic per ab), the ket sums take one global atomic per (q, cd).
+template <int NT>
 static __device__ void digest_coulomb(const FwdArgs& a, const double* V, int nqt, const int* s_q, double* s_dj)
 {
     const ClassTables& ct = a.ct;
@@ -281,7 +340,7 @@ static __device__ void digest_coulomb(const FwdArgs& a, const double* V, int nqt
     const int b = s_q[0];
     const int sa = a.bra_sh[2 * b], sb = a.bra_sh[2 * b + 1];
     const int oa = a.bf_off[sa], ob = a.bf_off[sb];
-    for (int q = tid; q < TQ; q += kNT) {
+    for (int q = tid; q < TQ; q += NT) {
         double w = 0.0;
         if (q < nqt) {
             const int k = s_q[4 * q + 1];
@@ -293,9 +352,9 @@ static __device__ void digest_coulomb(const FwdArgs& a, const double* V, int nqt
         }
         s_w[q] = w;
     }
-    for (int i = tid; i < nab; i += kNT) s_jb[i] = 0.0;
+    for (int i = tid; i < nab; i += NT) s_jb[i] = 0.0;
     __syncthreads();
-    for (int item = tid; item < TQ * ncd; item += kNT) {
+    for (int item = tid; item < TQ * ncd; item += NT) {
         const int q = item % TQ, cd = item / TQ;
         if (q >= nqt) continue;
         double sum = 0.0;
@@ -305,7 +364,7 @@ static __device__ void digest_coulomb(const FwdArgs& a, const double* V, int nqt
         const int ic = a.bf_off[a.ket_sh[2 * k]] + cd / ncdd, id = a.bf_off[a.ket_sh[2 * k + 1]] + cd % ncdd;
         atomicAdd(&a.Jmat[(size_t)ic * a.nbf + id], s_w[q] * sum);
     }
-    for (int item = tid; item < TQ * nab; item += kNT) {
+    for (int item = tid; item < TQ * nab; item += NT) {
         const int q = item % TQ, ab = item / TQ;
         if (q >= nqt) continue;
         const int k = s_q[4 * q + 1];
@@ -316,7 +375,7 @@ static __device__ void digest_coulomb(const FwdArgs& a, const double* V, int nqt
         atomicAdd(&s_jb[ab], s_w[q] * sum);
     }
     __syncthreads();
-    for (int ab = tid; ab < nab; ab += kNT)
+    for (int ab = tid; ab < nab; ab += NT)
         atomicAdd(&a.Jmat[(size_t)(oa + ab / ncb) * a.nbf + ob + ab % ncb], s_jb[ab]);
 }
 
@@ -328,6 +387,7 @@ static __device__ void digest_coulomb(const FwdArgs& a, const double* V, int nqt
 // (its images with the bra and ket exchanged are the transposes), and
 // K = K' + K'^T afterwards gives K_ul = sum over all (vs) of (uv|ls) D_vs.
 // One global atomic per (quartet, target element).
+template <int NT>
 static __device__ void digest_exchange(const FwdArgs& a, const double* V, int nqt, const int* s_q, double* s_dj)
 {
     const ClassTables& ct = a.ct;
@@ -341,7 +401,7 @@ static __device__ void digest_exchange(const FwdArgs& a, const double* V, int nq
     const double* D = a.D;
     const size_t n = (size_t)a.nbf;
     __syncthreads();  // the Coulomb digestion may still read s_dj
-    for (int q = tid; q < TQ; q += kNT) {
+    for (int q = tid; q < TQ; q += NT) {
         double w = 0.0;
         if (q < nqt) {
             const int k = s_q[4 * q + 1];
@@ -355,7 +415,7 @@ static __device__ void digest_exchange(const FwdArgs& a, const double* V, int nq
     }
     __syncthreads();
     const int n0 = na * nc, n1 = n0 + nb * nc, n2 = n1 + na * nd, n3 = n2 + nb * nd;
-    for (int item = tid; item < TQ * n3; item += kNT) {
+    for (int item = tid; item < TQ * n3; item += NT) {
         const int q = item % TQ, r = item / TQ;
         if (q >= nqt) continue;
         const int k = s_q[4 * q + 1];
@@ -394,10 +454,11 @@ static __device__ void digest_exchange(const FwdArgs& a, const double* V, int nq
 
 // One index of the contracted block mapped to solid harmonics:
 // out[(o nout + m) inner + i] = sum_k M[m][k] in[(o nin + k) inner + i].
+template <int NT>
 static __device__ void contract_index(const double* in, double* out, const double* __restrict__ M, int outer,
                                       int nin, int nout, int inner)
 {
-    for (int item = threadIdx.x; item < outer * nout * inner; item += kNT) {
+    for (int item = threadIdx.x; item < outer * nout * inner; item += NT) {
         const int i = item % inner, r = item / inner, m = r % nout, o = r / nout;
         const double* row = M + m * nin;
         const double* src = in + (size_t)o * nin * inner + i;
@@ -414,6 +475,7 @@ static __device__ void contract_index(const double* in, double* out, const doubl
 // Solid-harmonic output: the Cartesian block [ab][cd][q] in buf[cur] becomes
 // [ma mb][mc md][q] (m = -l..l on every centre), one centre at a time,
 // alternating between buf[0] and buf[1]; returns the final buffer.
+template <int NT>
 static __device__ const double* to_solid_harmonics(const FwdArgs& a, double* const buf[2], int cur)
 {
     const ClassTables& ct = a.ct;
@@ -428,7 +490,7 @@ static __device__ const double* to_solid_harmonics(const FwdArgs& a, double* con
                              {sa * sb * sc, nd, sd, TQ}};
     for (int i = 0; i < 4; ++i) {
         if (!ct.c2s[i]) continue;  // l = 0: the identity
-        contract_index(buf[cur], buf[cur ^ 1], ct.c2s[i], steps[i][0], steps[i][1], steps[i][2], steps[i][3]);
+        contract_index<NT>(buf[cur], buf[cur ^ 1], ct.c2s[i], steps[i][0], steps[i][1], steps[i][2], steps[i][3]);
         cur ^= 1;
     }
     return buf[cur];
@@ -438,7 +500,7 @@ static __device__ const double* to_solid_harmonics(const FwdArgs& a, double* con
 // one warp per (quartet, cd); lane l carries the bra Hermite functions
 // p = pb0 + l + 32 j, j < P, so that every ket E value loaded (the same for
 // the whole warp) feeds P products and the loop trip counts are uniform.
-template <int P>
+template <int P, int NT>
 __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int IC, int ii, int KK, int KKt,
                                                   int NIs, int ncd, int nhk, const double* sEk, const double* sR,
                                                   double* sX, const int* s_q, const int* s_kstart,
@@ -447,7 +509,7 @@ __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int 
     const ClassTables& ct = a.ct;
     const int lane = threadIdx.x & 31, nhb = ct.nhb;
     const uint64_t keep = policy_keep();
-    for (int w = threadIdx.x >> 5; w < TQ * ncd; w += kNT / 32) {
+    for (int w = threadIdx.x >> 5; w < TQ * ncd; w += NT / 32) {
         const int q = w % TQ, cd = w / TQ;
         const float2* Ek = reinterpret_cast<const float2*>(
             a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd);
@@ -551,17 +613,126 @@ __device__ __forceinline__ void split_ket_blocked(const FwdArgs& a, int TQ, int 
     }
 }
 
+// split_ket_blocked on the paired layout of the auxiliary integrals (r_row_stride):
+// each lane's two accumulator chains per bra function run as one packed
+// pair, chain 0 over the even ket primitives k and chain 1 over k + 1, so
+// one 16-byte load of a row gives both chains' (hi) and (lo) operands and
+// each FP32 instruction serves two products.  A tile whose own ket count
+// KKt is odd pairs its last primitive with a zero (its paired column is
+// zero, and so is the E value taken for it).
+template <int P, int NT>
+__device__ __forceinline__ void split_ket_paired(const FwdArgs& a, int TQ, int IC, int ii, int KK, int KKr,
+                                                 int KKt, int NIs, int ncd, int nhk, const double* sEk,
+                                                 const double* sR, double* sX, const int* s_q, const int* s_kstart,
+                                                 const int16_t* s_kq, const int16_t* s_pq, float2* ring)
+{
+    const ClassTables& ct = a.ct;
+    const int lane = threadIdx.x & 31, nhb = ct.nhb;
+    const uint64_t keep = policy_keep();
+    const uint64_t m1 = f2_pack(-1.f, -1.f);
+    const int KKe = KKt & ~1;  // ket primitives in full pairs
+    for (int w = threadIdx.x >> 5; w < TQ * ncd; w += NT / 32) {
+        const int q = w % TQ, cd = w / TQ;
+        const float2* Ek = reinterpret_cast<const float2*>(
+            a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd);
+        const double* Rc = sR + (q * IC + ii) * KKr;
+        int prow[P];
+        uint64_t S[P], c[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int p = ct.pb0 + lane + 32 * j;
+            prow[j] = (p < nhb ? p : ct.pb0) * nhk;  // lanes past the range read a valid row, results dropped
+            S[j] = c[j] = 0ull;
+        }
+        const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
+        const bool gl = !a.e_smem && !ring;
+        // one term: the ket E row Ea (KK float pairs) against the rows of p + q_t
+        auto term = [&](int t, const float2* Ea, bool from_global) {
+            const int qv = s_kq[t];
+            const ulonglong2* Rj[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                Rj[j] = reinterpret_cast<const ulonglong2*>(Rc + (size_t)s_pq[prow[j] + qv] * NIs);
+            auto ld = [&](int k) { return from_global ? ld_hint(Ea + k, keep) : Ea[k]; };
+            for (int k = 0; k < KKe; k += 2) {
+                const float2 e0 = ld(k), e1 = ld(k + 1);
+                const uint64_t ah = f2_pack(e0.x, e1.x), al = f2_pack(e0.y, e1.y), nah = f2_mul(ah, m1);
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    const ulonglong2 b = Rj[j][k >> 1];
+                    ff_mac2(ah, al, nah, b.x, b.y, S[j], c[j]);
+                }
+            }
+            if (KKe < KKt) {
+                const float2 e0 = ld(KKe);
+                const uint64_t ah = f2_pack(e0.x, 0.f), al = f2_pack(e0.y, 0.f), nah = f2_mul(ah, m1);
+#pragma unroll
+                for (int j = 0; j < P; ++j) {
+                    const ulonglong2 b = Rj[j][KKe >> 1];
+                    ff_mac2(ah, al, nah, b.x, b.y, S[j], c[j]);
+                }
+            }
+        };
+        if (ring) {
+            // the warp's ring of three ket E rows, as in split_ket_blocked
+            auto issue = [&](int t, int slot) {
+                if (t < t1)
+                    for (int k = lane; k < KKt; k += 32) cp_async8(ring + slot * KK + k, Ek + (size_t)t * KK + k, keep);
+                cp_async_commit();
+            };
+            issue(t0, 0);
+            issue(t0 + 1, 1);
+            int slot = 0;
+            for (int t = t0; t < t1; ++t) {
+                issue(t + 2, slot == 0 ? 2 : slot - 1);
+                cp_async_wait<2>();
+                __syncwarp();
+                term(t, ring + slot * KK, false);
+                __syncwarp();
+                slot = slot == 2 ? 0 : slot + 1;
+            }
+            cp_async_wait<0>();
+        } else {
+            const int nline = (KK * 8 + 127) / 128 + 1;
+            if (gl && lane < 2 * nline && t0 + lane / nline < t1)
+                prefetch_l1(reinterpret_cast<const char*>(Ek + (t0 + lane / nline) * KK) +
+                            min(128 * (lane % nline), 8 * KK - 8));
+            for (int t = t0; t < t1; ++t) {
+                if (gl && lane < nline && t + 2 < t1)
+                    prefetch_l1(reinterpret_cast<const char*>(Ek + (t + 2) * KK) + min(128 * lane, 8 * KK - 8));
+                term(t, Ek + t * KK, gl);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int p = ct.pb0 + lane + 32 * j;
+            if (p >= nhb) continue;
+            float s0, s1, c0, c1;
+            f2_unpack(S[j], s0, s1);
+            f2_unpack(c[j], c0, c1);
+            // fold the two chains into one split pair (error-free sum of the highs)
+            const float t2 = __fadd_rn(s0, s1), z = __fsub_rn(t2, s0);
+            const float err = __fadd_rn(__fsub_rn(s0, __fsub_rn(t2, z)), __fsub_rn(s1, z));
+            const float ch = __fadd_rn(__fadd_rn(c0, c1), err);
+            reinterpret_cast<float2*>(sX)[(p * ncd + cd) * TQ + q] = make_float2(t2, ch);
+        }
+    }
+}
+
 // One tile: quartets q0 .. q0+nqt-1 (the class tables are already staged).
 // s_red: one shared double for the digestion sum.
-template <bool SPLIT>
+template <bool SPLIT, int NT = kNT>
 __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, double* s_red)
 {
     const ClassTables& ct = a.ct;
     const int tid = threadIdx.x;
     const int TQ = a.TQ, KB = a.KB, KK = a.KK, IC = a.IC;
     const int nhl = ct.nhl, nhb = ct.nhb, nhk = ct.nhk, ncd = ct.ncd, nab = ct.nab;
-    const int NI = TQ * IC * KK;  // R columns (items of stage A)
-    const int NIs = NI | 1;       // R row stride: odd, so the scattered rows a warp reads spread over the banks
+    // R columns (items of stage A): a block of KKr ket primitives per (quartet,
+    // bra primitive), KKr = KK rounded up to even in the paired layout
+    const int KKr = a.r_pairs ? (KK + 1) & ~1 : KK;
+    const int NI = TQ * IC * KKr;
+    const int NIs = r_row_stride(NI, a.r_pairs);  // see r_row_stride
     const int* s_bstart = reinterpret_cast<const int*>(sm + a.o_tab);
     const int* s_kstart = s_bstart + nab + 1;
     const int16_t* s_bp = reinterpret_cast<const int16_t*>(s_kstart + ncd + 1);
@@ -582,7 +753,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     __syncthreads();
     {
         int mkb = 0, mkk = 0;
-        for (int q = tid; q < TQ; q += kNT) {
+        for (int q = tid; q < TQ; q += NT) {
             int b = 0, k = 0, kb = 0, kk = 0;
             const int64_t qq = q < nqt && a.order ? a.order[q0 + q] : q0 + q;
             if (q < nqt) {
@@ -610,21 +781,21 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     const int KBt = s_kmax[0], KKt = s_kmax[1];
     const int NIt = TQ * IC * KKt;  // stage-A items of this tile
     // stage primitive-pair scalars (and E products) of the tile
-    for (int idx = tid; idx < TQ * KB * PS_N; idx += kNT) {
+    for (int idx = tid; idx < TQ * KB * PS_N; idx += NT) {
         const int q = idx / (KB * PS_N), r = idx - q * KB * PS_N, i = r / PS_N;
         sPb[idx] = i < s_q[4 * q + 2] ? a.bra_ps[(size_t)s_q[4 * q] * KB * PS_N + r] : 1.0;
     }
-    for (int idx = tid; idx < TQ * KK * PS_N; idx += kNT) {
+    for (int idx = tid; idx < TQ * KK * PS_N; idx += NT) {
         const int q = idx / (KK * PS_N), r = idx - q * KK * PS_N, k = r / PS_N;
         sPk[idx] = k < s_q[4 * q + 3] ? a.ket_ps[(size_t)s_q[4 * q + 1] * KK * PS_N + r] : 1.0;
     }
     if (a.e_smem) {
         const int nb = KB * ct.Tab, nk = KK * ct.Tcd;
-        for (int idx = tid; idx < TQ * nb; idx += kNT) {
+        for (int idx = tid; idx < TQ * nb; idx += NT) {
             const int q = idx / nb, r = idx - q * nb, i = r % KB;
             sEb[q * a.sEbS + r] = i < s_q[4 * q + 2] ? a.bra_E[(size_t)s_q[4 * q] * nb + r] : 0.0;
         }
-        for (int idx = tid; idx < TQ * nk; idx += kNT) {
+        for (int idx = tid; idx < TQ * nk; idx += NT) {
             const int q = idx / nk, r = idx - q * nk, k = r % KK;
             sEk[q * a.sEkS + r] = k < s_q[4 * q + 3] ? a.ket_E[(size_t)s_q[4 * q + 1] * nk + r] : 0.0;
         }
@@ -639,11 +810,11 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
         // ---- A: auxiliary integrals of the primitive quartets (q, i0+ii, k),
         // k < KKt; few items (small tiles of high-l classes with K = 1): a warp
         // shares each item's recursion instead of leaving most threads idle
-        const bool coop = NIt * 4 < kNT;
+        const bool coop = NIt * 4 < NT;
         const int lane = tid & 31;
         auto stage_a_item = [&](int q, int ii, int k) {
             const int i = i0 + ii;
-            Strided R{sR + (q * IC + ii) * KK + k, NIs};
+            Strided R{sR + (q * IC + ii) * KKr + k, NIs};
             const int e0 = coop ? lane : 0, de = coop ? 32 : 1;
             if (i < s_q[4 * q + 2] && k < s_q[4 * q + 3]) {
                 const double* pb = sPb + (q * KB + i) * PS_N;
@@ -670,7 +841,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     else
                         r_recursion(ct.L, base, X, Y, Z, a.rsteps, R);
                 }
-                if (SPLIT)  // each entry becomes its (hi, lo) float pair, in place
+                if (SPLIT && !a.r_pairs)  // each entry becomes its (hi, lo) float pair, in place
                     for (int e = e0; e < nhl; e += de) {
                         double& slot = R[e];
                         const float2 f = split_f64(slot);
@@ -684,17 +855,31 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
         // own counts (every tile of a uniform batch) divides by the kernel
         // argument instead, which the compiler keeps in uniform registers
         if (KKt == KK) {
-            for (int item = coop ? tid >> 5 : tid; item < NIt; item += coop ? kNT / 32 : kNT) {
+            for (int item = coop ? tid >> 5 : tid; item < NIt; item += coop ? NT / 32 : NT) {
                 const int q = item / (IC * KK), r = item - q * IC * KK, ii = r / KK, k = r - ii * KK;
                 stage_a_item(q, ii, k);
             }
         } else {
-            for (int item = coop ? tid >> 5 : tid; item < NIt; item += coop ? kNT / 32 : kNT) {
+            for (int item = coop ? tid >> 5 : tid; item < NIt; item += coop ? NT / 32 : NT) {
                 const int q = item / (IC * KKt), r = item - q * IC * KKt, ii = r / KKt, k = r - ii * KKt;
                 stage_a_item(q, ii, k);
             }
         }
         __syncthreads();
+        if (SPLIT && a.r_pairs) {
+            // into the paired layout: columns k, k+1 of a block become (hi_k,
+            // hi_k+1, lo_k, lo_k+1); a column at or past the tile's ket count
+            // (the block's padding, or one stage A left untouched) pairs as zero
+            const int npr = NI >> 1, hb = KKr >> 1;
+            for (int idx = tid; idx < nhl * npr; idx += NT) {
+                const int e = idx / npr, m = idx - e * npr, k0 = 2 * (m % hb);
+                if (k0 >= KKt) continue;
+                double* d = sR + (size_t)e * NIs + 2 * m;
+                const float2 f0 = split_f64(d[0]), f1 = split_f64(k0 + 1 < KKt ? d[1] : 0.0);
+                *reinterpret_cast<float4*>(d) = make_float4(f0.x, f1.x, f0.y, f1.y);
+            }
+            __syncthreads();
+        }
         for (int ii = 0; ii < IC && i0 + ii < KBt; ++ii) {
             const int i = i0 + ii;
             // ---- B: ket transform + ket contraction
@@ -705,7 +890,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 // the bra E products of primitive i, gathered once (strided in
                 // global memory: one slot of every term) for stage C
                 double* sEi = sm + a.o_Ei;
-                for (int t = tid; t < ct.Tab; t += kNT)
+                for (int t = tid; t < ct.Tab; t += NT)
                     sEi[t] = i < s_q[2] ? a.bra_E[((size_t)s_q[0] * ct.Tab + t) * KB + i] : 0.0;
             }
             const int nhbu = nhb - ct.pb0;
@@ -714,17 +899,23 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             float2* ring = a.o_Er >= 0 && !a.e_smem
                                ? reinterpret_cast<float2*>(sm + a.o_Er) + (size_t)(tid >> 5) * kRingRows * KK
                                : nullptr;
-            if (blocked == 3)
-                split_ket_blocked<3>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq,
+            if (a.r_pairs && blocked == 3)
+                split_ket_paired<3, NT>(a, TQ, IC, ii, KK, KKr, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq,
+                                        s_pq, ring);
+            else if (a.r_pairs && blocked == 2)
+                split_ket_paired<2, NT>(a, TQ, IC, ii, KK, KKr, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq,
+                                        s_pq, ring);
+            else if (blocked == 3)
+                split_ket_blocked<3, NT>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq,
                                      ring);
             else if (blocked == 2)
-                split_ket_blocked<2>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq,
+                split_ket_blocked<2, NT>(a, TQ, IC, ii, KK, KKt, NIs, ncd, nhk, sEk, sR, sX, s_q, s_kstart, s_kq, s_pq,
                                      ring);
             const int nB = blocked ? 0 : TQ * nhbu * ncd;
-            for (int item = tid; item < nB; item += kNT) {
+            for (int item = tid; item < nB; item += NT) {
                 const int q = item % TQ, r = item / TQ, p = ct.pb0 + r % nhbu, cd = r / nhbu;
                 const double* Ek = a.e_smem ? sEk + q * a.sEkS : a.ket_E + (size_t)s_q[4 * q + 1] * KK * ct.Tcd;
-                const double* Rc = sR + (q * IC + ii) * KK;  // + e * NIs + k
+                const double* Rc = sR + (q * IC + ii) * KKr;  // + e * NIs + k
                 const int16_t* pqrow = s_pq + p * nhk;
                 const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
                 // terms outer, ket primitives inner: one p+q lookup per term
@@ -811,7 +1002,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             if (a.acc_regs) {
 #pragma unroll
                 for (int s = 0; s < kNACC; ++s) {
-                    const int item = tid + s * kNT;
+                    const int item = tid + s * NT;
                     if (item < nC) {
                         const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
                         const double* Eb = a.e_smem ? sEb + q * a.sEbS + i
@@ -823,7 +1014,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 }
             } else {
                 const uint64_t stream = policy_stream();
-                for (int item = tid; item < nC; item += kNT) {
+                for (int item = tid; item < nC; item += NT) {
                     const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
                     if (q >= nqt) continue;
                     const double* Eb = a.e_smem ? sEb + q * a.sEbS + i
@@ -844,12 +1035,12 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             double* buf[2] = {sm, sm + a.o_hB};
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
-                const int item = tid + s * kNT;
+                const int item = tid + s * NT;
                 if (item < nC) buf[0][item] = acc[s];
             }
             __syncthreads();
-            const double* fin = to_solid_harmonics(a, buf, 0);
-            for (int item = tid; item < TQ * ct.nab_s * ct.ncd_s; item += kNT) {
+            const double* fin = to_solid_harmonics<NT>(a, buf, 0);
+            for (int item = tid; item < TQ * ct.nab_s * ct.ncd_s; item += NT) {
                 const int q = item % TQ, r = item / TQ, cd = r % ct.ncd_s, ab = r / ct.ncd_s;
                 if (q < nqt) a.out[out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd)] = fin[item];
             }
@@ -857,16 +1048,16 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             // the values go to shared memory (the staging regions are dead)
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
-                const int item = tid + s * kNT;
+                const int item = tid + s * NT;
                 if (item < nC) sm[item] = acc[s];
             }
             __syncthreads();
-            if (a.Jmat) digest_coulomb(a, sm, nqt, s_q, sm + a.o_dj);
-            if (a.Kmat) digest_exchange(a, sm, nqt, s_q, sm + a.o_dj);
+            if (a.Jmat) digest_coulomb<NT>(a, sm, nqt, s_q, sm + a.o_dj);
+            if (a.Kmat) digest_exchange<NT>(a, sm, nqt, s_q, sm + a.o_dj);
         } else if (!ct.hrr) {
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
-                const int item = tid + s * kNT;
+                const int item = tid + s * NT;
                 if (item < nC) {
                     const int q = item % TQ, r = item / TQ, cd = r % ncd, ab = r / ncd;
                     if (q < nqt) {
@@ -886,10 +1077,10 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             double* s_geo = sm + a.o_geo;  // [q][6]: A-B, C-D
 #pragma unroll
             for (int s = 0; s < kNACC; ++s) {
-                const int item = tid + s * kNT;
+                const int item = tid + s * NT;
                 if (item < nC) hbuf[0][item] = acc[s];
             }
-            for (int q = tid; q < TQ; q += kNT) {
+            for (int q = tid; q < TQ; q += NT) {
                 const int b = s_q[4 * q], k = s_q[4 * q + 1];
                 const double* A = a.centres + 3 * a.shell_atom[a.bra_sh[2 * b]];
                 const double* B = a.centres + 3 * a.shell_atom[a.bra_sh[2 * b + 1]];
@@ -907,7 +1098,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 double* dst = hbuf[(g + 1) & 1];
                 const int np = ct.kn[j - 1], nn = ct.kn[j];
                 const int16_t* st = ct.ksteps + 3 * ct.koff[j];
-                for (int item = tid; item < TQ * nab * nn; item += kNT) {
+                for (int item = tid; item < TQ * nab * nn; item += NT) {
                     const int q = item % TQ, r = item / TQ, o = r % nn, f = r / nn;
                     const int16_t* s3 = st + 3 * o;
                     const double* row = src + (size_t)f * np * TQ + q;
@@ -920,7 +1111,7 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 const double* src = hbuf[g & 1];
                 double* dst = hbuf[(g + 1) & 1];
                 const int16_t* st = ct.bsteps + 3 * ct.boff[j];
-                for (int item = tid; item < TQ * ncf * ct.bn[j]; item += kNT) {
+                for (int item = tid; item < TQ * ncf * ct.bn[j]; item += NT) {
                     const int q = item % TQ, r = item / TQ, cd = r % ncf, o = r / ncf;
                     const int16_t* s3 = st + 3 * o;
                     const double* col = src + (size_t)cd * TQ + q;
@@ -930,16 +1121,16 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
             }
             const double* fin = hbuf[g & 1];  // [ab][cd][q]
             if (ct.sph) {
-                const double* fs = to_solid_harmonics(a, hbuf, g & 1);
-                for (int item = tid; item < TQ * ct.nab_s * ct.ncd_s; item += kNT) {
+                const double* fs = to_solid_harmonics<NT>(a, hbuf, g & 1);
+                for (int item = tid; item < TQ * ct.nab_s * ct.ncd_s; item += NT) {
                     const int q = item % TQ, r = item / TQ, cd = r % ct.ncd_s, ab = r / ct.ncd_s;
                     if (q < nqt) a.out[out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd)] = fs[item];
                 }
             } else if (a.Jmat || a.Kmat) {
-                if (a.Jmat) digest_coulomb(a, fin, nqt, s_q, sm + a.o_dj);
-                if (a.Kmat) digest_exchange(a, fin, nqt, s_q, sm + a.o_dj);
+                if (a.Jmat) digest_coulomb<NT>(a, fin, nqt, s_q, sm + a.o_dj);
+                if (a.Kmat) digest_exchange<NT>(a, fin, nqt, s_q, sm + a.o_dj);
             } else {
-                for (int item = tid; item < TQ * ct.nab_f * ncf; item += kNT) {
+                for (int item = tid; item < TQ * ct.nab_f * ncf; item += NT) {
                     const int q = item % TQ, r = item / TQ, cd = r % ncf, ab = r / ncf;
                     if (q >= nqt) continue;
                     if (a.energy)
@@ -961,16 +1152,17 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
     }
 }
 
-template <bool SPLIT>
-__global__ void __launch_bounds__(kNT, 2) fwd_kernel_t(FwdArgs a)
+// NT = kNT: two CTAs per SM (128 registers a thread); kNTWide: one.
+template <bool SPLIT, int NT>
+__global__ void __launch_bounds__(NT, NT == kNT ? 2 : 1) fwd_kernel_t(FwdArgs a)
 {
     extern __shared__ __align__(16) double sm[];
     __shared__ double s_red;
     if (threadIdx.x == 0) s_red = 0.0;
-    stage_class_tables(a, sm);
+    stage_class_tables<NT>(a, sm);
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         const int64_t q0 = tile * a.TQ;
-        tile_body<SPLIT>(a, q0, (int)min((int64_t)a.TQ, a.nq - q0), sm, &s_red);
+        tile_body<SPLIT, NT>(a, q0, (int)min((int64_t)a.TQ, a.nq - q0), sm, &s_red);
     }
 }
 
