@@ -436,19 +436,15 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 const int ab = r % nab, k = r / nab;
                 const double* w = sW + (size_t)q * Ws + ab * ncd;
                 const double* Ek = sEk + (size_t)q * Eks + k;
-                double va = 0.0, vb = 0.0;
-                int e = __ldg(a.vstart + qh);
+                // one accumulator chain: a dependent DFMA chain runs at the
+                // FP64 pipe's full rate, and needs no DADD to join
+                double v = 0.0;
                 const int e1 = __ldg(a.vstart + qh + 1);
-                for (; e + 1 < e1; e += 2) {
-                    const int g0 = __ldg(a.vlist + e), g1 = __ldg(a.vlist + e + 1);
-                    va = fma(w[g0 >> 16], Ek[(g0 & 0xffff) * KK], va);
-                    vb = fma(w[g1 >> 16], Ek[(g1 & 0xffff) * KK], vb);
-                }
-                if (e < e1) {
+                for (int e = __ldg(a.vstart + qh); e < e1; ++e) {
                     const int g0 = __ldg(a.vlist + e);
-                    va = fma(w[g0 >> 16], Ek[(g0 & 0xffff) * KK], va);
+                    v = fma(w[g0 >> 16], Ek[(g0 & 0xffff) * KK], v);
                 }
-                sV[(size_t)q * Vs + (k * nab + ab) * nhk + qh] = va + vb;
+                sV[(size_t)q * Vs + (k * nab + ab) * nhk + qh] = v;
             }
         }
 
@@ -527,7 +523,7 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
             }
             __syncthreads();
             const int ICe = min(IC, KBt - i0);
-            // ---- B': X'[ii][q][p'][cd] over the raised bra range (four chains)
+            // ---- B': X'[ii][q][p'][cd] over the raised bra range (one chain)
             for (int item = tid; item < (a.vform ? 0 : TQ * ICe * nhb2 * ncd); item += kGT) {
                 const int q = item % TQ;
                 int r = item / TQ;
@@ -538,31 +534,13 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                 const double* Rc = sR + ii * TQ + q;
                 const int16_t* row = ct.pq2b + (size_t)p * nhk;
                 const int t0 = ct.ket_start[cd], t1 = ct.ket_start[cd + 1];
-                double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-                int t = t0;
-                for (; t + 1 < t1; t += 2) {
-                    const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NIs;
-                    const double* Rb = Rc + (size_t)row[ct.ket_q[t + 1]] * NIs;
-                    const double* Ea = Ek + t * KK;
-                    const double* Eb = Ea + KK;
-                    int k = 0;
-                    for (; k + 1 < KKt; k += 2) {
-                        v0 = fma(Ea[k], Ra[k * ICT], v0);
-                        v1 = fma(Ea[k + 1], Ra[(k + 1) * ICT], v1);
-                        v2 = fma(Eb[k], Rb[k * ICT], v2);
-                        v3 = fma(Eb[k + 1], Rb[(k + 1) * ICT], v3);
-                    }
-                    if (k < KKt) {
-                        v0 = fma(Ea[k], Ra[k * ICT], v0);
-                        v2 = fma(Eb[k], Rb[k * ICT], v2);
-                    }
-                }
-                if (t < t1) {
+                double v = 0.0;
+                for (int t = t0; t < t1; ++t) {
                     const double* Ra = Rc + (size_t)row[ct.ket_q[t]] * NIs;
                     const double* Ea = Ek + t * KK;
-                    for (int k = 0; k < KKt; ++k) v0 = fma(Ea[k], Ra[k * ICT], v0);
+                    for (int k = 0; k < KKt; ++k) v = fma(Ea[k], Ra[k * ICT], v);
                 }
-                sX[(size_t)(ii * TQ + q) * XQ + p * Xs + cd] = (v0 + v1) + (v2 + v3);
+                sX[(size_t)(ii * TQ + q) * XQ + p * Xs + cd] = v;
             }
             if (!a.vform) __syncthreads();
             // ---- C+D.  Each (q, ii) of the chunk is taken by a group of G
@@ -596,37 +574,22 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                         const double* Dq = sD + (size_t)(ii * TQ + q) * PST;
                         for (int j = s; j < nit; j += G) {
                             const int2 g = __ldg(a.items + j);
-                            double ya = 0.0, yb = 0.0;
+                            double y = 0.0;  // one chain (see stage V)
                             if (!a.vform) {
                                 const double* w = wq + (g.x & 1023) * ncd;
                                 const double* xv = xq + ((g.x >> 10) & 1023) * Xs;
-                                int cd = 0;
-                                for (; cd + 1 < ncd; cd += 2) {
-                                    ya = fma(w[cd], xv[cd], ya);
-                                    yb = fma(w[cd + 1], xv[cd + 1], yb);
-                                }
-                                if (cd < ncd) ya = fma(w[cd], xv[cd], ya);
+                                for (int cd = 0; cd < ncd; ++cd) y = fma(w[cd], xv[cd], y);
                             } else {
                                 // T = sum_qh sum_k V[q][k][ab][qh] R_{ii,k}[p'+qh]
                                 const double* vq = sV + (size_t)q * Vs + (g.x & 1023) * nhk;
                                 const int16_t* pqr = s_pq + ((g.x >> 10) & 1023) * nhk;
                                 const double* Rq = sR + ii * TQ + q;
                                 const int VK = nab * nhk;
-                                int qh = 0;
-                                for (; qh + 1 < nhk; qh += 2) {
+                                for (int qh = 0; qh < nhk; ++qh) {
                                     const double* Ra = Rq + (size_t)pqr[qh] * NIs;
-                                    const double* Rb = Rq + (size_t)pqr[qh + 1] * NIs;
-                                    for (int k = 0; k < KKt; ++k) {
-                                        ya = fma(vq[k * VK + qh], Ra[k * ICT], ya);
-                                        yb = fma(vq[k * VK + qh + 1], Rb[k * ICT], yb);
-                                    }
-                                }
-                                if (qh < nhk) {
-                                    const double* Ra = Rq + (size_t)pqr[qh] * NIs;
-                                    for (int k = 0; k < KKt; ++k) ya = fma(vq[k * VK + qh], Ra[k * ICT], ya);
+                                    for (int k = 0; k < KKt; ++k) y = fma(vq[k * VK + qh], Ra[k * ICT], y);
                                 }
                             }
-                            const double y = ya + yb;
                             const double* Dx = Dq + (g.y & 1023);
                             const double* Dy = Dq + 5 * ND + ((g.y >> 10) & 1023);
                             const double* Dz = Dq + 10 * ND + (g.y >> 20);
@@ -756,14 +719,9 @@ __global__ void __launch_bounds__(kGT, 2) grad_tile_kernel(GradArgs a)
                         const int2 g = __ldg(a.kitems + j);
                         const int cd = g.x & 1023, qp = (g.x >> 10) & 1023;
                         const double* yv = yq + qp;
-                        double ya = 0.0, yb = 0.0;
-                        int ab = 0;
-                        for (; ab + 1 < nab; ab += 2) {
-                            ya = fma(wq[ab * ncd + cd], yv[ab * nhk2], ya);
-                            yb = fma(wq[(ab + 1) * ncd + cd], yv[(ab + 1) * nhk2], yb);
-                        }
-                        if (ab < nab) ya = fma(wq[ab * ncd + cd], yv[ab * nhk2], ya);
-                        const double y = (herm_order(qp) & 1) ? -(ya + yb) : ya + yb;
+                        double ya = 0.0;
+                        for (int ab = 0; ab < nab; ++ab) ya = fma(wq[ab * ncd + cd], yv[ab * nhk2], ya);
+                        const double y = (herm_order(qp) & 1) ? -ya : ya;
                         fold_item(y, Dq + (g.y & 1023), Dq + 5 * NDk + ((g.y >> 10) & 1023),
                                   Dq + 10 * NDk + (g.y >> 20), NDk, g.x >> 20, ch);
                     }

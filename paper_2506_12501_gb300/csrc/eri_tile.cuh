@@ -261,22 +261,18 @@ __device__ __forceinline__ void quartet_pairs(const FwdArgs& a, int64_t qq, int*
     *k = (int)(a.swap ? ob : ok);
 }
 
-// Stage C inner sum: sum_{u in [u0,u1)} E^ab_u X[p_u][cd] of one quartet and
-// one bra primitive (E term u at Eb[u * KB]).  Two alternating chains; the
-// split form returns its compensated float sum as a double (2 FP64 ops).
+// Stage C inner sum: acc + sum_{u in [u0,u1)} E^ab_u X[p_u][cd] of one
+// quartet and one bra primitive (E term u at Eb[u * KB]).  FP64: one chain
+// from the accumulator (no DADD); the split form adds its compensated float
+// sum to acc as a double (3 FP64 ops).
 template <bool SPLIT>
 __device__ __forceinline__ double bra_sum(const double* Eb, int KB, const double* sX, int u0, int u1,
-                                          const int16_t* s_bp, int ncd, int cd, int TQ, int q)
+                                          const int16_t* s_bp, int ncd, int cd, int TQ, int q, double acc)
 {
     if (!SPLIT) {
-        double va = 0.0, vb = 0.0;
-        int u = u0;
-        for (; u + 1 < u1; u += 2) {
-            va = fma(Eb[(size_t)u * KB], sX[(s_bp[u] * ncd + cd) * TQ + q], va);
-            vb = fma(Eb[(size_t)(u + 1) * KB], sX[(s_bp[u + 1] * ncd + cd) * TQ + q], vb);
-        }
-        if (u < u1) va = fma(Eb[(size_t)u * KB], sX[(s_bp[u] * ncd + cd) * TQ + q], va);
-        return va + vb;
+        double v = acc;
+        for (int u = u0; u < u1; ++u) v = fma(Eb[(size_t)u * KB], sX[(s_bp[u] * ncd + cd) * TQ + q], v);
+        return v;
     } else {
         const float2* E2 = reinterpret_cast<const float2*>(Eb);
         const float2* X2 = reinterpret_cast<const float2*>(sX);
@@ -287,7 +283,7 @@ __device__ __forceinline__ double bra_sum(const double* Eb, int KB, const double
             ff_mac(E2[(size_t)(u + 1) * KB], X2[(s_bp[u + 1] * ncd + cd) * TQ + q], Sb, cb);
         }
         if (u < u1) ff_mac(E2[(size_t)u * KB], X2[(s_bp[u] * ncd + cd) * TQ + q], Sa, ca);
-        return ((double)Sa + (double)Sb) + ((double)ca + (double)cb);
+        return acc + (((double)Sa + (double)Sb) + ((double)ca + (double)cb));
     }
 }
 
@@ -919,41 +915,21 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                 const int16_t* pqrow = s_pq + p * nhk;
                 const int t0 = s_kstart[cd], t1 = s_kstart[cd + 1];
                 // terms outer, ket primitives inner: one p+q lookup per term
-                // serves all KK primitives (E is stored slot-fastest).  Two
-                // terms and two primitives at a time feed four independent
-                // accumulator chains, which hides the FP64 (or TwoSum)
-                // latency with few warps per scheduler.
+                // serves all KK primitives (E is stored slot-fastest).  FP64:
+                // one accumulator chain, since the FP64 pipe keeps a dependent
+                // DFMA chain at its full rate with one warp per scheduler
+                // (measured: 1.06 TFLOP/s with one chain and 4 warps per SM),
+                // and a single chain needs no DADD to join partial sums.
+                // Split: two terms and two primitives at a time feed four
+                // chains, which hides the TwoSum latency.
                 if (!SPLIT) {
-                    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-                    int t = t0;
-                    for (; t + 1 < t1; t += 2) {
-                        const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NIs;
-                        const double* Rb = Rc + (size_t)pqrow[s_kq[t + 1]] * NIs;
-                        const double* Ea = Ek + t * KK;
-                        const double* Eb2 = Ea + KK;
-                        int k = 0;
-                        for (; k + 1 < KKt; k += 2) {
-                            v0 = fma(Ea[k], Ra[k], v0);
-                            v1 = fma(Ea[k + 1], Ra[k + 1], v1);
-                            v2 = fma(Eb2[k], Rb[k], v2);
-                            v3 = fma(Eb2[k + 1], Rb[k + 1], v3);
-                        }
-                        if (k < KKt) {
-                            v0 = fma(Ea[k], Ra[k], v0);
-                            v2 = fma(Eb2[k], Rb[k], v2);
-                        }
-                    }
-                    if (t < t1) {
+                    double v = 0.0;
+                    for (int t = t0; t < t1; ++t) {
                         const double* Ra = Rc + (size_t)pqrow[s_kq[t]] * NIs;
                         const double* Ea = Ek + t * KK;
-                        int k = 0;
-                        for (; k + 1 < KKt; k += 2) {
-                            v0 = fma(Ea[k], Ra[k], v0);
-                            v1 = fma(Ea[k + 1], Ra[k + 1], v1);
-                        }
-                        if (k < KKt) v0 = fma(Ea[k], Ra[k], v0);
+                        for (int k = 0; k < KKt; ++k) v = fma(Ea[k], Ra[k], v);
                     }
-                    sX[(p * ncd + cd) * TQ + q] = (v0 + v1) + (v2 + v3);
+                    sX[(p * ncd + cd) * TQ + q] = v;
                 } else {
                     float S[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
                     int t = t0;
@@ -1008,8 +984,8 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                         const double* Eb = a.e_smem ? sEb + q * a.sEbS + i
                                                     : (e_row ? sm + a.o_Ei
                                                              : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab + i);
-                        acc[s] += bra_sum<SPLIT>(Eb, e_row ? 1 : KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd,
-                                                 TQ, q);
+                        acc[s] = bra_sum<SPLIT>(Eb, e_row ? 1 : KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd,
+                                                TQ, q, acc[s]);
                     }
                 }
             } else {
@@ -1019,10 +995,12 @@ __device__ void tile_body(const FwdArgs& a, int64_t q0, int nqt, double* sm, dou
                     if (q >= nqt) continue;
                     const double* Eb = a.e_smem ? sEb + q * a.sEbS + i
                                                 : (e_row ? sm + a.o_Ei : a.bra_E + (size_t)s_q[4 * q] * KB * ct.Tab + i);
-                    const double v =
-                        bra_sum<SPLIT>(Eb, e_row ? 1 : KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ, q);
                     const int64_t o = out_index(a, a.order ? s_qq[q] : q0 + q, ab, cd);
-                    st_hint(a.out + o, (i == 0) ? v : ld_hint(a.out + o, stream) + v, stream);
+                    const double prev = (i == 0) ? 0.0 : ld_hint(a.out + o, stream);
+                    st_hint(a.out + o,
+                            bra_sum<SPLIT>(Eb, e_row ? 1 : KB, sX, s_bstart[ab], s_bstart[ab + 1], s_bp, ncd, cd, TQ,
+                                           q, prev),
+                            stream);
                 }
             }
             __syncthreads();

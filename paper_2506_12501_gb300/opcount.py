@@ -131,7 +131,7 @@ def sparse_flops(cls, Kbra: int, Kket: int, orient: str = "auto", allow_hrr: boo
     L = la + lb + lc + ld
     rows, cols, tb, tk, hs = _form(cls, hrr)
     ket = 2 * nh(la + lb) * tk                       # per primitive quartet
-    bra = 2 * cols * tb + rows * cols                # per bra primitive
+    bra = 2 * cols * tb                              # per bra primitive (each chain starts from the accumulator)
     return Kbra * Kket * (prim_quartet_flops(L) + ket) + Kbra * bra + 2 * hs
 
 
@@ -157,11 +157,11 @@ def sparse_flops3(cls3, Kx: int, Kket: int, pure: bool, swapped: bool, pure_term
     if not swapped:
         kb, kk = Kx, Kket
         ket = 2 * (nc(lx) if pure else nh(lx)) * tcd
-        bra = 2 * ncd * tx + nx * ncd
+        bra = 2 * ncd * tx
     else:
         kb, kk = Kket, Kx
         ket = 2 * nh(lc + ld) * tx
-        bra = 2 * nx * tcd + ncd * nx
+        bra = 2 * nx * tcd
     return kb * kk * (prim_quartet_flops(L) + ket) + kb * bra
 
 
