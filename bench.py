@@ -299,7 +299,8 @@ def synth_nc(l):
 
 def peaks_variant(eri):
     out = {}
-    for name, kind in (("dfma", eri.PEAK_DFMA), ("dmma", eri.PEAK_DMMA), ("ffma", eri.PEAK_FFMA)):
+    for name, kind in (("dfma", eri.PEAK_DFMA), ("dmma", eri.PEAK_DMMA), ("ffma", eri.PEAK_FFMA),
+                       ("dfma_one_chain_8_warps_per_sm", eri.PEAK_DFMA_ONE_CHAIN)):
         g, mhz = eri.eri_peak_probe(kind)
         out[name] = {"gflops": g, "sm_mhz": mhz}
     out["dfma_per_clk_per_sm"] = out["dfma"]["gflops"] * 1e9 / 2 / (out["dfma"]["sm_mhz"] * 1e6) / 152

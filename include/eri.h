@@ -441,6 +441,8 @@ int64_t eri_launch_count(void);
  * launch of 2 to 8 CTAs per SM runs independent chains (4 to 16 per thread)
  * for about 100 ms; *gflops (HOST, GFLOP/s, FMA = 2 flops) is the best, over
  * those shapes, of three timed launches each on `stream` (CUDA events).
+ * kind 3: DFMA with a single dependent chain per thread and one CTA of 256
+ * threads per SM (whether FP64 latency needs more chains or warps).
  * sm_mhz (HOST, may be NULL): the SM clock during the best shape's last
  * launch, from the cycle counter and the global timer.
  * Synchronises `stream`.  ERI_EINVAL for another kind or a NULL gflops.

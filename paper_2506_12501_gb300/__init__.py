@@ -33,7 +33,7 @@ from .binding import (  # noqa: F401
     eri_launch_count,
     eri_peak_probe,
     partition,
-    PEAK_DFMA, PEAK_DMMA, PEAK_FFMA,
+    PEAK_DFMA, PEAK_DMMA, PEAK_FFMA, PEAK_DFMA_ONE_CHAIN,
     PROF_FWD, PROF_GRAD, PROF_PAIR, PROF_PREPASS,
     error_string,
     lib,

@@ -384,7 +384,7 @@ def partition(costs, nranks: int):
     return owner, load
 
 
-PEAK_DFMA, PEAK_DMMA, PEAK_FFMA = 0, 1, 2
+PEAK_DFMA, PEAK_DMMA, PEAK_FFMA, PEAK_DFMA_ONE_CHAIN = 0, 1, 2, 3
 
 
 def eri_peak_probe(kind: int, stream=None) -> tuple:

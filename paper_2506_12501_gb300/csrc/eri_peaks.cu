@@ -104,6 +104,8 @@ static int probe_once(int kind, int chains, int per_sm, cudaStream_t st, double*
         count_launch();
         if (kind == 1)
             dmma_probe_kernel<<<grid, kProbeThreads, 0, st>>>(iters, sink, clk);
+        else if (kind == 3)
+            fma_probe_kernel<double, 1><<<grid, kProbeThreads, 0, st>>>(iters, 0.999999, 1e-7, sink, clk);
         else if (kind == 0 && chains == 4)
             fma_probe_kernel<double, 4><<<grid, kProbeThreads, 0, st>>>(iters, 0.999999, 1e-7, sink, clk);
         else if (kind == 0 && chains == 8)
@@ -167,8 +169,16 @@ static int probe_once(int kind, int chains, int per_sm, cudaStream_t st, double*
 
 extern "C" int eri_peak_probe(int kind, double* gflops, double* sm_mhz, void* stream)
 {
-    if (kind < 0 || kind > 2 || !gflops) return ERI_EINVAL;
+    if (kind < 0 || kind > 3 || !gflops) return ERI_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    if (kind == 3) {  // one dependent DFMA chain per thread, one CTA (8 warps) per SM
+        double g = 0.0, mhz = 0.0;
+        const int rc = probe_once(3, 1, 1, st, &g, &mhz);
+        if (rc != ERI_OK) return rc;
+        *gflops = g;
+        if (sm_mhz) *sm_mhz = mhz;
+        return ERI_OK;
+    }
     // the best over a few occupancies and chain counts (MMA: four
     // accumulators per warp, at two occupancies)
     const int shapes[][2] = {{4, 2}, {8, 2}, {16, 2}, {4, 4}, {8, 4}, {16, 4}, {8, 8}};

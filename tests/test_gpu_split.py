@@ -136,3 +136,35 @@ def test_recursion_form_accuracy_guard(cuda):
         assert eri.eri_last_form()[1] is True
     finally:
         eri.eri_set_forms(0)
+
+
+@pytest.mark.parametrize("cls", [(3, 3, 3, 3), (3, 3, 3, 2)])
+def test_split_packed_chains_mixed_contraction(cuda, cls):
+    """The split ket stage on packed FP32 pairs (tiles that accumulate in
+    memory: (ff|ff) and (ff|fd)) with contraction degrees 1 to 3 per shell,
+    so that one batch holds pairs of 1 to 9 primitives: sorted tiles whose
+    own ket count is below the batch's, odd and even counts (the zero partner
+    of an odd last primitive), against the oracle at the split bar.  The
+    tile shape reported afterwards is one of the two CTA widths."""
+    rng = np.random.default_rng(31)
+    shells, centres = [], []
+    for i in range(12):
+        l = cls[i % 4]
+        K = 1 + (i // 4) % 3
+        e = 10.0 ** rng.uniform(np.log10(0.05), np.log10(50.0), size=K)
+        w = rng.uniform(0.5, 1.0, size=K)
+        centres.append(rng.uniform(0.0, 4.0, size=3))
+        shells.append((i, l, list(e), list(w * synth.norm_coef(e, l))))
+    basis = synth.basis_from_shells(np.array(centres), shells)
+    by_l = {l: [i for i, s in enumerate(shells) if s[1] == l] for l in set(cls)}
+    pb = [(a, b) for a in by_l[cls[0]] for b in by_l[cls[1]]]
+    pk = [(c, d) for c in by_l[cls[2]] for d in by_l[cls[3]]]
+    bra = np.array([pb[i] for i in rng.choice(len(pb), 6, replace=False)], dtype=np.int32)
+    ket = np.array([pk[i] for i in rng.choice(len(pk), 6, replace=False)], dtype=np.int32)
+    q = np.array([(i, j) for i in range(len(bra)) for j in range(len(ket))][::3], dtype=np.int64)
+    ref = oracle_blocks(cls, basis, bra, ket, q, prec="d")
+    got = gpu_list(cls, basis, bra, ket, q, precision=eri.ERI_PREC_SPLIT)
+    assert_close(got, ref, atol=1e-10, what=f"split packed {cls}")
+    assert eri.eri_last_tile()["threads"] in (256, 512)
+    got64 = gpu_list(cls, basis, bra, ket, q)
+    assert_close(got64, ref, what=f"fp64 {cls}")
