@@ -153,6 +153,14 @@ __device__ __forceinline__ void r_recursion_warp(int L, const double* base, doub
     }
 }
 
+// One thread per primitive quartet.  The entries are rewritten four at a
+// time, every load of a group before any of its stores: the sources of an
+// entry have lower indices than the entry, so a group member that is the
+// source of another is read at its old (level n+1) value, and no entry
+// written earlier (a higher index) is a source of any later one.  The four
+// independent steps overlap their latencies, which a one-at-a-time loop
+// through shared memory (each load ordered after the previous store)
+// cannot.
 template <typename RPtr>
 __device__ __forceinline__ void r_recursion(int L, const double* base, double X, double Y, double Z,
                                             const RStep* __restrict__ st, RPtr R)
@@ -161,7 +169,22 @@ __device__ __forceinline__ void r_recursion(int L, const double* base, double X,
     for (int n = L - 1; n >= 0; --n) {
         const int N = L - n;
         const int top = (N + 1) * (N + 2) * (N + 3) / 6;  // Nh(N)
-        for (int e = top - 1; e >= 1; --e) {
+        int e = top - 1;
+        for (; e >= 4; e -= 4) {
+            RStep s[4];
+            double v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s[j] = st[e - j];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const double x = s[j].axis == 0 ? X : (s[j].axis == 1 ? Y : Z);
+                v[j] = x * R[s[j].src1];
+                if (s[j].coef) v[j] = fma(s[j].coefd, R[s[j].src2], v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) R[e - j] = v[j];
+        }
+        for (; e >= 1; --e) {
             const RStep s = st[e];
             const double x = s.axis == 0 ? X : (s.axis == 1 ? Y : Z);
             double v = x * R[s.src1];
