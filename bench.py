@@ -232,8 +232,8 @@ def kernel_source_sha():
 def profile_traffic():
     """DRAM bytes per fwd_kernel launch of the full sweep, from the committed
     ncu summary, if it was taken on the current kernel source (else None).
-    The summary holds the traffic of a small case (5000 quartets per class)
-    scaled to 1e5 quartets per class."""
+    The summary holds the one-pass DRAM counters of one full-size step
+    (81 launches, 1e5 quartets per class), averaged per launch."""
     path = os.path.join(ROOT, "profiles", "fwd_kernel_class_sweep.md")
     try:
         text = open(path).read()

@@ -167,7 +167,12 @@ int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis,
  * launch with the caller's bra as its kernel bra, ERI_GRAD_ONE_SWAPPED for
  * the single launch with the caller's ket as its kernel bra (whose channels
  * *bra_form then describes), else the second launch's form.  All give the same derivatives to
- * round-off; a cost model picks per call.  ERI_EINVAL before any call.
+ * round-off; a cost model picks per call, except that the first list-form
+ * batch of at least 65536 quartets of a class (per device, with every scheme
+ * allowed) times one launch against two on its first 32768 quartets, into
+ * scratch gradients, and keeps the faster scheme for the class (the model
+ * still picks the single launch's orientation and the forms).  ERI_EINVAL
+ * before any call.
  * eri_set_grad_forms -- restrict the planner (process-wide; for testing):
  * bits ERI_GRAD_X and ERI_GRAD_V allow those forms, bit ERI_GRAD_ONE the
  * single launch, bit ERI_GRAD_TWO two launches; a mask with neither of the

@@ -31,6 +31,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "eri_device.cuh"
@@ -211,6 +212,9 @@ static int g_last_grad_form[2] = {-1, -1};
 // bits: ERI_GRAD_X, ERI_GRAD_V (forms of a launch's own channels), 2: the
 // single launch, 3: two launches; a mask without bits 2 and 3 means two launches
 static std::atomic<int> g_grad_form_mask{0xF};
+// The scheme a call runs: 0, the cost model's pick; 1, one launch; 2, two
+// launches (set by the timed choice of eri_batch_grad for the call).
+static thread_local int g_grad_force = 0;
 
 // Derived-table entries per axis and value: (la+1)(lb+1)(la+lb+3).
 static int derived_entries(int la, int lb) { return (la + 1) * (lb + 1) * (la + lb + 3); }
@@ -978,7 +982,8 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
     // a single launch needs the pair tables of both sides raised and the E
     // products of both; otherwise the kernel bra's raised tables suffice
     const int mask = g_grad_form_mask.load();
-    const bool allow_one = (mask & 4) != 0, allow_two = (mask & 8) || !(mask & 12);
+    const bool allow_one = (mask & 4) != 0 && g_grad_force != 2,
+               allow_two = ((mask & 8) || !(mask & 12)) && g_grad_force != 1;
     const bool may_one = mode == 2 || (mode == 0 && allow_one);
     // the quartet indices refer to the caller's lists: validated by the first call only
     int mixed = 0;
@@ -1086,6 +1091,83 @@ static int launch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t*
 
 using namespace eri;
 
+// One adjoint call (arguments validated): the bra's channels, then, unless
+// that launch covered every channel, the ket's with the sides exchanged.
+static int run_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
+                    const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq, const double* W,
+                    double* grad_centres, double* grad_exps, cudaStream_t st)
+{
+    int err = ERI_OK;
+    GradOrder order;
+    g_last_grad_form[0] = g_last_grad_form[1] = -1;
+    int next = GRAD_DONE;
+    err = launch_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, grad_centres, grad_exps, 0, nbra,
+                      nket, &order, st, 0, &next);
+    if (err != ERI_OK || next == GRAD_DONE) return err;
+    return launch_grad(eri_class_t{cls.lc, cls.ld, cls.la, cls.lb}, basis, ket_pairs, nket, bra_pairs, nbra, quartets,
+                       nq, W, grad_centres, grad_exps, 1, nbra, nket, &order, st, next == GRAD_ONE_SWAPPED ? 2 : 1,
+                       nullptr);
+}
+
+// Timed choice between one launch and two, on the first large list-form
+// batch of a class (per device): each scheme runs twice on the batch's first
+// kGradTuneQuartets quartets, into scratch gradients (the weights read are
+// the caller's, in range, whatever they mean for the shorter list), and the
+// faster second run decides for the class.  The cost model still picks the
+// single launch's orientation and each launch's form.  Returns 1 (one
+// launch), 2 (two), or 0 (no decision: the model's pick).
+constexpr int64_t kGradTuneMin = 65536, kGradTuneQuartets = 32768;
+static std::map<std::tuple<int, int, int, int, int>, int> g_grad_scheme;
+static std::mutex g_grad_scheme_mu;
+
+static int timed_grad_scheme(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
+                             const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq,
+                             const double* W, cudaStream_t st)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const auto key = std::make_tuple(dev, cls.la, cls.lb, cls.lc, cls.ld);
+    {
+        std::lock_guard<std::mutex> lk(g_grad_scheme_mu);
+        auto it = g_grad_scheme.find(key);
+        if (it != g_grad_scheme.end()) return it->second;
+    }
+    int err = ERI_OK;
+    const size_t ng = 3 * (size_t)basis->natom + (size_t)basis->nprim;
+    double* scratch = (double*)aux_workspace(sizeof(double) * ng, &err);
+    if (!scratch) return 0;
+    const int64_t n = std::min(nq, kGradTuneQuartets);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 0;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 0;
+    }
+    float ms[3] = {0.f, 0.f, 0.f};
+    bool ok = true;
+    for (int scheme = 1; scheme <= 2 && ok; ++scheme) {
+        g_grad_force = scheme;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            ok &= cudaEventRecord(e0, st) == cudaSuccess;
+            ok &= run_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, n, W, scratch,
+                           scratch + 3 * basis->natom, st) == ERI_OK;
+            ok &= cudaEventRecord(e1, st) == cudaSuccess;
+            ok &= cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms[scheme], e0, e1) == cudaSuccess;
+        }
+    }
+    g_grad_force = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int pick = ms[1] <= ms[2] ? 1 : 2;
+    std::lock_guard<std::mutex> lk(g_grad_scheme_mu);
+    g_grad_scheme[key] = pick;
+    return pick;
+}
+
 extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const int32_t* bra_pairs, int64_t nbra,
                               const int32_t* ket_pairs, int64_t nket, const int64_t* quartets, int64_t nq,
                               const double* W, int64_t w_len, double* grad_centres, double* grad_exps, void* stream)
@@ -1097,16 +1179,15 @@ extern "C" int eri_batch_grad(eri_class_t cls, const eri_basis_t* basis, const i
     if (!W) return ERI_EINVAL;
     if (!grad_centres && !grad_exps) return ERI_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    // channels of the bra (a, b), then of the ket (c, d) with the sides exchanged
-    GradOrder order;
-    g_last_grad_form[0] = g_last_grad_form[1] = -1;
-    int next = GRAD_DONE;
-    err = launch_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, grad_centres, grad_exps, 0, nbra,
-                      nket, &order, st, 0, &next);
-    if (err != ERI_OK || next == GRAD_DONE) return err;
-    return launch_grad(eri_class_t{cls.lc, cls.ld, cls.la, cls.lb}, basis, ket_pairs, nket, bra_pairs, nbra, quartets,
-                       nq, W, grad_centres, grad_exps, 1, nbra, nket, &order, st, next == GRAD_ONE_SWAPPED ? 2 : 1,
-                       nullptr);
+    const int mask = g_grad_form_mask.load();
+    const bool both = (mask & 4) && ((mask & 8) || !(mask & 12));
+    int scheme = 0;
+    if (both && quartets && nqq >= kGradTuneMin)
+        scheme = timed_grad_scheme(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, st);
+    g_grad_force = scheme;
+    err = run_grad(cls, basis, bra_pairs, nbra, ket_pairs, nket, quartets, nq, W, grad_centres, grad_exps, st);
+    g_grad_force = 0;
+    return err;
 }
 
 extern "C" int eri_last_grad_forms(int32_t* bra_form, int32_t* ket_form)
