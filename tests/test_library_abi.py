@@ -86,3 +86,20 @@ def test_form_selectors_without_gpu():
     b, k = ctypes.c_int32(), ctypes.c_int32()
     r = L.eri_last_grad_forms(ctypes.byref(b), ctypes.byref(k))
     assert r == eri.ERI_EINVAL or (r == eri.ERI_OK and b.value in (0, 1) and k.value in (0, 1, 2, 4))
+
+
+def test_tile_query_and_probe_kinds_without_gpu():
+    """eri_last_tile answers ERI_EINVAL before the thread's first eri_batch
+    launch (or a shape with a valid width after one), with NULL outputs
+    allowed; eri_peak_probe rejects an unknown kind and a NULL rate before
+    any GPU work."""
+    import paper_2506_12501_gb300 as eri
+    L = eri.lib()
+    v = [ctypes.c_int32() for _ in range(4)]
+    r = L.eri_last_tile(*(ctypes.byref(x) for x in v))
+    assert r == eri.ERI_EINVAL or (r == eri.ERI_OK and v[0].value >= 1 and v[2].value in (256, 512))
+    assert L.eri_last_tile(None, None, None, None) in (eri.ERI_EINVAL, eri.ERI_OK)
+    g = ctypes.c_double()
+    assert L.eri_peak_probe(4, ctypes.byref(g), None, None) == eri.ERI_EINVAL
+    assert L.eri_peak_probe(-1, ctypes.byref(g), None, None) == eri.ERI_EINVAL
+    assert L.eri_peak_probe(3, None, None, None) == eri.ERI_EINVAL
